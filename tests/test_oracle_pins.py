@@ -1,0 +1,377 @@
+"""Pins of the CPU oracle against things other than itself: the paper's printed
+numbers, textbook constructions written independently here (Kronecker-product
+Hamiltonians, explicit symmetry projectors), closed forms (singlet, 4-ring,
+Bethe ansatz), invariants (Hermiticity, Sz conservation, union of sector
+spectra) and brute force."""
+import math
+
+import numpy as np
+import pytest
+
+import ed_inputs as ei
+import oracle
+from conftest import read_golden
+
+
+# ----------------------------------------------------------------------------
+# independent constructions used as pins (numpy only, no oracle code)
+# ----------------------------------------------------------------------------
+def kron_hamiltonian(n, op):
+    """Full 2^n matrix from Kronecker products of single-site matrices.
+    State index s has bit k = site k (site n-1 is the most significant factor)."""
+    def emb(a, site):
+        return np.kron(np.kron(np.eye(2 ** (n - 1 - site)), a), np.eye(2 ** site))
+    E = lambda a, c: np.outer(np.eye(2)[a], np.eye(2)[c])
+    H = np.zeros((2 ** n, 2 ** n), complex)
+    for t in range(len(op["sites"])):
+        i, j = op["sites"][t]
+        c = op["coeff"][t, 0] + 1j * op["coeff"][t, 1]
+        h = (op["local"][t, :, 0] + 1j * op["local"][t, :, 1]).reshape(4, 4)
+        for a in range(2):
+            for b in range(2):
+                for cc in range(2):
+                    for d in range(2):
+                        v = h[2 * a + b, 2 * cc + d]
+                        if v != 0:
+                            H += c * v * emb(E(a, cc), i) @ emb(E(b, d), j)
+    return H
+
+
+def act_all(n, perm, flip, states):
+    """g.s for an array of states, vectorised (bit perm[i] of g.s = bit i of s)."""
+    s = np.asarray(states, dtype=np.int64)
+    out = np.zeros_like(s)
+    for i in range(n):
+        out |= ((s >> i) & 1) << int(perm[i])
+    if flip:
+        out ^= (1 << n) - 1
+    return out
+
+
+def projected_basis(n, n_up, perms, chars, z):
+    """Explicit symmetry-adapted vectors |r^> = P|r> / |P|r>| with
+    P = |G|^-1 sum_g conj(chi(g)) U_g, for every orbit minimum r with P|r> != 0.
+    Returns (reps ascending, V with columns |r^> in the full 2^n space)."""
+    elems = [(p, 0, complex(c[0], c[1])) for p, c in zip(perms, chars)]
+    if z:
+        elems += [(p, 1, complex(c[0], c[1]) * z) for p, c in zip(perms, chars)]
+    allst = np.arange(2 ** n)
+    pc = np.array([bin(s).count("1") for s in allst])
+    sector = allst[pc == n_up] if n_up >= 0 else allst
+    images = np.stack([act_all(n, p, f, sector) for p, f, _ in elems])
+    orbit_min = images.min(axis=0)
+    reps, cols = [], []
+    for s, m in zip(sector, orbit_min):
+        if s != m:
+            continue
+        v = np.zeros(2 ** n, complex)
+        for p, f, ch in elems:
+            v[act_all(n, p, f, [s])[0]] += np.conj(ch)
+        v /= len(elems)
+        nv = np.linalg.norm(v)
+        if nv > 1e-9:
+            reps.append(s)
+            cols.append(v / nv)
+    V = np.array(cols).T if cols else np.zeros((2 ** n, 0), complex)
+    return np.array(reps, dtype=np.uint64), V
+
+
+def bethe_e0(n, iters=20000, tol=1e-15):
+    """Ground-state energy of the n-site periodic Heisenberg ring, J = 1, from
+    the Bethe ansatz (n even, M = n/2 magnons, quantum numbers
+    I_j = -(M-1)/2 .. (M-1)/2):  n atan(2 l_j) = pi I_j + sum_k atan(l_j - l_k),
+    E = n/4 - sum_j 2/(4 l_j^2 + 1)."""
+    m = n // 2
+    I = np.arange(m) - (m - 1) / 2.0
+    lam = 0.5 * np.tan(np.pi * I / n)
+    for _ in range(iters):
+        s = np.arctan(lam[:, None] - lam[None, :]).sum(axis=1)
+        new = 0.5 * np.tan((np.pi * I + s) / n)
+        if np.max(np.abs(new - lam)) < tol:
+            lam = new
+            break
+        lam = 0.5 * lam + 0.5 * new
+    return n / 4.0 - np.sum(2.0 / (4.0 * lam ** 2 + 1.0))
+
+
+def ring_sector(n, n_up, k=0, parity=None, z=0, op=None):
+    p, c = ei.ring_group(n, k, parity)
+    G = oracle.Group(n, p, c, z)
+    st, nm = oracle.enumerate_basis(G, n_up)
+    H = oracle.Operator(op if op is not None else ei.heisenberg_ring(n))
+    return G, H, st, nm
+
+
+# ----------------------------------------------------------------------------
+# the paper's printed numbers
+# ----------------------------------------------------------------------------
+@pytest.mark.parametrize("row", read_golden("table2_dims.txt"))
+def test_table2_dimensions(row):
+    n, dim = int(row[0]), int(row[1])
+    p, c = ei.ring_group(n, 0, parity=+1)
+    assert oracle.sector_dim(oracle.Group(n, p, c, +1), n // 2) == dim
+
+
+def test_fig1_four_spins():
+    want = {r[0]: int(r[1]) for r in read_golden("fig1_four_spins.txt")}
+    pt, ct = ei.trivial_group(4)
+    st, _ = oracle.enumerate_basis(oracle.Group(4, pt, ct), -1)
+    assert len(st) == want["full"]
+    p, c = ei.ring_group(4, 0)
+    st, _ = oracle.enumerate_basis(oracle.Group(4, p, c), -1)
+    assert len(st) == want["translations"]
+    # the six translation classes of Fig. 1: 0000, 0001, 0011, 0101, 0111, 1111
+    assert list(st) == [0b0000, 0b0001, 0b0011, 0b0101, 0b0111, 0b1111]
+    st, _ = oracle.enumerate_basis(oracle.Group(4, pt, ct), 2)
+    assert len(st) == want["u1_weight2"] == math.comb(4, 2)
+
+
+# ----------------------------------------------------------------------------
+# enumeration vs the character formula vs brute force
+# ----------------------------------------------------------------------------
+@pytest.mark.parametrize("n", [4, 6, 8, 10, 12])
+def test_enumeration_matches_character_formula_and_irrep_sum(n):
+    for n_up in range(0, n + 1):
+        total = 0
+        zs = (1, -1) if 2 * n_up == n else (0,)
+        for k in range(n):
+            for z in zs:
+                p, c = ei.ring_group(n, k)
+                G = oracle.Group(n, p, c, z)
+                st, nm = oracle.enumerate_basis(G, n_up)
+                assert len(st) == oracle.sector_dim(G, n_up)
+                assert np.all(np.diff(st.astype(np.int64)) > 0)
+                assert all(bin(int(s)).count("1") == n_up for s in st)
+                total += len(st)
+        # the one-dimensional irreps of an abelian group resolve the whole space
+        assert total == math.comb(n, n_up)
+
+
+def test_norms_are_stabilizer_orders_brute_force():
+    n = 10
+    p, c = ei.ring_group(n, 0, parity=+1)
+    G = oracle.Group(n, p, c, +1)
+    st, nm = oracle.enumerate_basis(G, 5)
+    elems = [(q, 0) for q in p] + [(q, 1) for q in p]
+    for s, m in zip(st, nm):
+        stab = sum(act_all(n, q, f, [int(s)])[0] == int(s) for q, f in elems)
+        assert m == stab
+        orbit = {int(act_all(n, q, f, [int(s)])[0]) for q, f in elems}
+        assert min(orbit) == int(s)
+        assert len(orbit) * stab == len(elems)  # orbit-stabilizer
+
+
+def test_norm_zero_states_are_excluded():
+    # k = pi on a 4-ring.  0000 is fixed by every translation and chi(T) = -1,
+    # so its character sum over the stabilizer vanishes: norm 0, not in the
+    # basis.  0101 is fixed by T^0 and T^2 only, chi(T^2) = +1: norm 2.
+    p, c = ei.ring_group(4, 2)
+    G = oracle.Group(4, p, c)
+    st, nm = oracle.enumerate_basis(G, -1)
+    assert 0 not in set(int(s) for s in st)
+    rep, chi, norm, ssum = oracle.state_info(G, 0)
+    assert norm == 0 and abs(ssum) < 1e-12
+    rep, chi, norm, ssum = oracle.state_info(G, 0b0101)
+    assert norm == 2 and abs(ssum - 2) < 1e-12
+
+
+# ----------------------------------------------------------------------------
+# the matrix elements against an explicit projector construction
+# ----------------------------------------------------------------------------
+@pytest.mark.parametrize("case", [
+    dict(n=8, n_up=4, k=0, parity=+1, z=+1),
+    dict(n=8, n_up=4, k=4, parity=-1, z=+1),
+    dict(n=8, n_up=4, k=4, parity=+1, z=-1),
+    dict(n=8, n_up=3, k=3, parity=None, z=0),
+    dict(n=10, n_up=5, k=1, parity=None, z=+1),
+    dict(n=9, n_up=4, k=2, parity=None, z=0),
+])
+def test_sector_matrix_equals_projected_full_hamiltonian(case):
+    n = case["n"]
+    p, c = ei.ring_group(n, case["k"], case["parity"])
+    rng = np.random.default_rng(7)
+    # a Hermitian, translation- and reflection-invariant operator with complex
+    # off-diagonal entries would break reflection; use Heisenberg + XXZ mix
+    op = ei.heisenberg_ring(n)
+    op2 = ei.xxz_ring(n, 0.7, 1.9)
+    for key in ("sites", "coeff", "local"):
+        op[key] = np.concatenate([op[key], op2[key]])
+    G = oracle.Group(n, p, c, case["z"])
+    st, nm = oracle.enumerate_basis(G, case["n_up"])
+    reps, V = projected_basis(n, case["n_up"], p, c, case["z"])
+    assert len(reps) > 0 and np.array_equal(st, reps)
+    np.testing.assert_allclose(V.conj().T @ V, np.eye(len(reps)), atol=1e-12)
+    Hs = V.conj().T @ kron_hamiltonian(n, op) @ V
+    Ho = oracle.dense_matrix(G, oracle.Operator(op), st, nm)
+    np.testing.assert_allclose(Ho, Hs, atol=1e-12, rtol=0)
+
+
+def test_torus_complex_sector_matrix_equals_projection():
+    # 3x2 torus, momentum (2pi/3, pi), J1-J2: complex characters, two generators
+    p, c = ei.torus_group(3, 2, 1, 1)
+    op = ei.j1j2_torus(3, 2, 1.0, 0.5)
+    G = oracle.Group(6, p, c, +1)
+    st, nm = oracle.enumerate_basis(G, 3)
+    reps, V = projected_basis(6, 3, p, c, +1)
+    assert np.array_equal(st, reps)
+    Hs = V.conj().T @ kron_hamiltonian(6, op) @ V
+    Ho = oracle.dense_matrix(G, oracle.Operator(op), st, nm)
+    np.testing.assert_allclose(Ho, Hs, atol=1e-12, rtol=0)
+
+
+def test_full_space_matches_kron_with_random_hermitian_terms():
+    n = 6
+    rng = np.random.default_rng(3)
+    bonds, locs = [], []
+    for _ in range(7):
+        i, j = rng.choice(n, 2, replace=False)
+        a = rng.normal(size=(4, 4)) + 1j * rng.normal(size=(4, 4))
+        locs.append(a + a.conj().T)
+        bonds.append((i, j))
+    op = ei.make_operator(bonds, rng.normal(size=len(bonds)), np.zeros((len(bonds), 4, 4)))
+    op["local"][:, :, 0] = np.array([l.real.reshape(16) for l in locs])
+    op["local"][:, :, 1] = np.array([l.imag.reshape(16) for l in locs])
+    pt, ct = ei.trivial_group(n)
+    G = oracle.Group(n, pt, ct)
+    st, nm = oracle.enumerate_basis(G, -1)
+    assert np.array_equal(st, np.arange(2 ** n, dtype=np.uint64)) and np.all(nm == 1)
+    Ho = oracle.dense_matrix(G, oracle.Operator(op), st, nm)
+    np.testing.assert_allclose(Ho, kron_hamiltonian(n, op), atol=1e-12, rtol=0)
+
+
+# ----------------------------------------------------------------------------
+# spectra
+# ----------------------------------------------------------------------------
+def test_union_of_sector_spectra_is_full_spectrum():
+    n = 10
+    full = np.linalg.eigvalsh(kron_hamiltonian(n, ei.heisenberg_ring(n)))
+    parts = []
+    for n_up in range(n + 1):
+        zs = (1, -1) if 2 * n_up == n else (0,)
+        for k in range(n):
+            for z in zs:
+                G, H, st, nm = ring_sector(n, n_up, k, None, z)
+                if len(st):
+                    M = oracle.dense_matrix(G, H, st, nm)
+                    assert np.abs(M - M.conj().T).max() < 1e-13
+                    parts.append(np.linalg.eigvalsh(M))
+    union = np.sort(np.concatenate(parts))
+    assert len(union) == 2 ** n
+    np.testing.assert_allclose(union, full, atol=1e-11)
+
+
+def test_reflection_sectors_resolve_momentum_sector():
+    n, n_up = 12, 6
+    for k in (0, 6):
+        G, H, st, nm = ring_sector(n, n_up, k, None, 0)
+        want = np.linalg.eigvalsh(oracle.dense_matrix(G, H, st, nm))
+        got = []
+        for par in (+1, -1):
+            Gp, Hp, sp_, np_ = ring_sector(n, n_up, k, par, 0)
+            if len(sp_):
+                got.append(np.linalg.eigvalsh(oracle.dense_matrix(Gp, Hp, sp_, np_)))
+        np.testing.assert_allclose(np.sort(np.concatenate(got)), want, atol=1e-11)
+
+
+def test_two_site_singlet():
+    op = ei.make_operator([(0, 1)], [1.0], ei.heisenberg_local())
+    pt, ct = ei.trivial_group(2)
+    G = oracle.Group(2, pt, ct)
+    st, nm = oracle.enumerate_basis(G, -1)
+    ev = np.linalg.eigvalsh(oracle.dense_matrix(G, oracle.Operator(op), st, nm))
+    np.testing.assert_allclose(ev, [-0.75, 0.25, 0.25, 0.25], atol=1e-15)
+
+
+def test_four_site_ring_ground_state():
+    G, H, st, nm = ring_sector(4, 2, 0, +1, +1)
+    ev = np.linalg.eigvalsh(oracle.dense_matrix(G, H, st, nm))
+    assert abs(ev[0] + 2.0) < 1e-14
+
+
+def test_bethe_solver_closed_forms():
+    assert abs(bethe_e0(2) + 1.5) < 1e-14          # 2 S0.S1 on the 2-ring
+    assert abs(bethe_e0(4) + 2.0) < 1e-12           # the 4-ring
+    # thermodynamic limit 1/4 - ln 2 (Hulthen) with the known -pi^2/(12 n^2)
+    # leading finite-size correction to the energy per site
+    n = 1000
+    e = bethe_e0(n) / n
+    assert abs(e - (0.25 - math.log(2)) + math.pi ** 2 / (12 * n * n)) < 1e-8
+
+
+@pytest.mark.parametrize("n", [8, 12, 16, 20])
+def test_ground_state_sector_matches_bethe_ansatz(n):
+    import scipy.sparse.linalg as sla
+    G, H, st, nm = ring_sector(n, n // 2, 0, +1, +1)
+    M = oracle.sparse_matrix(G, H, st, nm)
+    if M.shape[0] < 400:
+        e0 = np.linalg.eigvalsh(M.toarray())[0]
+    else:
+        e0 = sla.eigsh(M, k=1, which="SA", tol=1e-14)[0][0]
+    assert abs(e0 - bethe_e0(n)) < 1e-10
+
+
+def test_hermiticity_and_sz_conservation():
+    # complex sector: <u, H v> = <H u, v>
+    p, c = ei.ring_group(12, 5)
+    G = oracle.Group(12, p, c)
+    st, nm = oracle.enumerate_basis(G, 5)
+    H = oracle.Operator(ei.xxz_ring(12, 1.0, 1.5))
+    rng = np.random.default_rng(0)
+    u = rng.normal(size=len(st)) + 1j * rng.normal(size=len(st))
+    v = rng.normal(size=len(st)) + 1j * rng.normal(size=len(st))
+    lhs = np.vdot(u, oracle.matvec(G, H, st, nm, v))
+    rhs = np.vdot(oracle.matvec(G, H, st, nm, u), v)
+    assert abs(lhs - rhs) < 1e-10 * abs(lhs)
+    # Sz conservation on the full space: H commutes with the popcount operator
+    pt, ct = ei.trivial_group(8)
+    Gt = oracle.Group(8, pt, ct)
+    st, nm = oracle.enumerate_basis(Gt, -1)
+    M = oracle.dense_matrix(Gt, oracle.Operator(ei.heisenberg_ring(8)), st, nm)
+    Sz = np.diag([bin(int(s)).count("1") for s in st])
+    assert np.abs(M @ Sz - Sz @ M).max() == 0.0
+
+
+def test_oracle_lanczos_matches_dense():
+    G, H, st, nm = ring_sector(16, 8, 0, +1, +1)
+    M = oracle.dense_matrix(G, H, st, nm).real
+    x0 = ei.x_by_index(0, len(st))[:, 0]
+    _, _, e0 = oracle.lanczos(lambda v: M @ v, x0, 50)
+    assert abs(e0 - np.linalg.eigvalsh(M)[0]) < 1e-10
+
+
+# ----------------------------------------------------------------------------
+# rows evaluated from states alone (used at sizes where no basis is enumerated)
+# ----------------------------------------------------------------------------
+@pytest.mark.parametrize("cplx,nvec", [(False, 1), (True, 3)])
+def test_state_keyed_rows_match_indexed_matvec(cplx, nvec):
+    n, k = 12, (2 if cplx else 0)
+    p, c = ei.ring_group(n, k)
+    G = oracle.Group(n, p, c, +1)
+    st, nm = oracle.enumerate_basis(G, 6)
+    H = oracle.Operator(ei.heisenberg_ring(n))
+    x = ei.x_by_state(11, st, nvec, cplx)
+    y = oracle.matvec(G, H, st, nm, x)
+    y2, nnz = oracle.rows_statex(G, H, st, 11, nvec, cplx)
+    np.testing.assert_allclose(y2, y, atol=1e-13, rtol=0)
+    # nnz = distinct stored elements: off-diagonal terms + one diagonal
+    r, cc, _ = oracle.coo(G, H, st, nm)
+    offd = np.bincount(r[r != cc], minlength=len(st))
+    np.testing.assert_array_equal(nnz, offd + 1)
+
+
+def test_enumerate_slice_partitions_the_sector():
+    n, n_up = 14, 7
+    p, c = ei.ring_group(n, 0, +1)
+    G = oracle.Group(n, p, c, +1)
+    st, _ = oracle.enumerate_basis(G, n_up)
+    done, kept = oracle.enumerate_slice(G, n_up, (1 << n_up) - 1, math.comb(n, n_up))
+    assert done == math.comb(n, n_up) and kept == len(st)
+
+
+def test_input_generator_properties():
+    x = ei.x_by_index(0, 1 << 16)[:, 0]
+    assert x.min() >= -1 and x.max() < 1
+    assert abs(x.mean()) < 0.01 and abs(x.var() - 1 / 3) < 0.01
+    # the mixer is a bijection (distinct inputs give distinct outputs)
+    h = ei.hash64_01(np.arange(1 << 16, dtype=np.uint64))
+    assert len(np.unique(h)) == 1 << 16
