@@ -1,0 +1,419 @@
+"""Benchmark of the symmetry-adapted ED hot path on one GB300 (or N replicas).
+
+Workload (default): Heisenberg ring N=32, J=1, sector Sz=0, momentum 0,
+reflection +1, spin inversion +1 (group order 128, 4 707 969 representatives),
+x0 uniform in [-1, 1] from seed 0.
+
+One timed step = the whole hot path once: ed_basis_build (enumerate, filter,
+compact, prefix table) followed by ed_lanczos with 100 steps in the fp32-matvec
+mode (fp64 recurrence, fp64 refinement, fp64 Rayleigh quotient and residual).
+value = matrix rows processed by H.x per second over the step
+(dim x matvecs / step time).  The fp64-plain path (ed_lanczos fp64 mode) is
+timed the same way and reported beside it with |dE0| between the two.
+
+Multi-GPU: the path has one sector, which this build does not split across
+GPUs; with --gpus N every rank runs an independent replica (weak scaling,
+value = the sum over ranks), with a barrier and the max over ranks of the
+timed region.
+
+--impl reference times the CPU oracle (plain C, one core) on a bounded sample
+of the same rows and prints the same JSON line with "impl": "reference".
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import ed_inputs as ei  # noqa: E402
+
+METRIC = "H·x rows/s & nonzeros/s: FP32 batched vs FP64 plain on 1 GB300 at |dE0|<1e-10"
+UNIT = "rows/s"
+L2_BYTES = 129 * 1024 * 1024
+# INT32 ALU issue peak used for the roofline: 152 SMs x 64 lanes/clk x the
+# maximum SM clock (GB300 SM: 4 sub-partitions x 16 INT32 lanes).
+SMS = 152
+INT_LANES_PER_SM = 64
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.proc = None
+        self.gpu = gpu_index
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(gpu_index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for name, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+# ---------------------------------------------------------------------------
+# distributed plumbing (replicas only)
+# ---------------------------------------------------------------------------
+def dist_setup(n_gpus):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("gloo")
+    return rank, world, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(v, world):
+    if world == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(v, world):
+    if world == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------------------
+# oracle timing (cpu_baseline and the reference arm)
+# ---------------------------------------------------------------------------
+def oracle_rows(w, n_rows, seed=1):
+    """Row states for the oracle sample, found by the oracle itself: random
+    states of the sector's popcount mapped to their representatives."""
+    import oracle
+    G = oracle.Group(w["n_sites"], w["perms"], w["chars"], w["spin_inversion"])
+    rng = np.random.default_rng(seed)
+    rows = set()
+    while len(rows) < n_rows:
+        bits = rng.choice(w["n_sites"], w["n_up"], replace=False)
+        s = sum(1 << int(b) for b in bits)
+        rep, _, norm, _ = oracle.state_info(G, s)
+        if norm:
+            rows.add(rep)
+    return G, oracle.Operator(w["op"]), np.array(sorted(rows), np.uint64)
+
+
+def time_oracle_rows(G, H, rows):
+    import oracle
+    t0 = time.perf_counter()
+    _, nnz = oracle.rows_statex(G, H, rows, 0)
+    return time.perf_counter() - t0, nnz
+
+
+def cpu_baseline(w, budget_s=15.0):
+    G, H, rows = oracle_rows(w, 64)
+    dt, _ = time_oracle_rows(G, H, rows[:8])
+    per_row = max(dt / 8, 1e-6)
+    n = int(min(max(budget_s / per_row, 16), 20000))
+    G, H, rows = oracle_rows(w, n, seed=2)
+    dt, nnz = time_oracle_rows(G, H, rows)
+    return {"value": len(rows) / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{len(rows)} rows of the {w['name']} sector (one H.x row each, x keyed "
+                      f"by state, no basis enumeration), single-threaded C oracle, {dt:.1f} s",
+            "nnz_per_row": float(nnz.mean())}
+
+
+def run_reference(args, w):
+    rank, world, _ = dist_setup(args.gpus)
+    if rank != 0:
+        return
+    G, H, rows = oracle_rows(w, 64)
+    dt, _ = time_oracle_rows(G, H, rows[:8])
+    per_row = max(dt / 8, 1e-6)
+    rows_per_step = int(min(max(150.0 / (args.steps + args.warmup) / per_row, 8), 20000))
+    G, H, rows = oracle_rows(w, rows_per_step * (args.steps + args.warmup), seed=3)
+    chunks = np.array_split(rows, args.steps + args.warmup)
+    for c in chunks[: args.warmup]:
+        time_oracle_rows(G, H, c)
+    total, n_done = 0.0, 0
+    for c in chunks[args.warmup:]:
+        dt, _ = time_oracle_rows(G, H, c)
+        total += dt
+        n_done += len(c)
+    value = n_done / total
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": w["name"], "rows_per_step": rows_per_step},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"{rows_per_step} rows per step of the {w['name']} sector, "
+                                       "single-threaded C oracle (x keyed by state)"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# GPU measurement
+# ---------------------------------------------------------------------------
+def popcount64(t):
+    import torch
+    t = t - ((t >> 1) & 0x5555555555555555)
+    t = (t & 0x3333333333333333) + ((t >> 2) & 0x3333333333333333)
+    t = (t + (t >> 4)) & 0x0F0F0F0F0F0F0F0F
+    return ((t * 0x0101010101010101) >> 56) & 0xFF
+
+
+def generated_terms_per_row(states, n):
+    """Average off-diagonal terms H|r> generates per row for the Heisenberg ring
+    (one per antiparallel bond); every one of them costs a group search."""
+    mask = (1 << n) - 1
+    rot = ((states << 1) | (states >> (n - 1))) & mask
+    return float(popcount64((states ^ rot) & mask).double().mean())
+
+
+def run_matvec_only(args, w):
+    import torch
+    from paper_2308_16712_gb300 import ed
+    n = w["n_sites"]
+    op = w["op"]
+    O = ed.operator_create(n, op["sites"], op["coeff"], op["local"])
+    B = ed.basis_build(n, w["n_up"], w["spin_inversion"], w["perms"], w["chars"])
+    dim = ed.basis_size(B)
+    for dt in (torch.float32, torch.float64):
+        x = torch.from_numpy(ei.x_by_index(5, dim)[:, 0]).cuda().to(dt)
+        y = torch.empty_like(x)
+        for _ in range(args.steps):
+            ed.matvec(O, B, x, y, 1)
+    torch.cuda.synchronize()
+    print(json.dumps({"mode": "matvec", "workload": w["name"], "dim": dim, "launches": 2 * args.steps}))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="ring32")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--mode", default="job", choices=["job", "matvec"],
+                    help="job: the benchmark; matvec: only the basis build and --steps matvec "
+                         "launches per dtype (a short program for profiler captures)")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    w = ei.workload(args.workload)
+    if args.impl == "reference":
+        return run_reference(args, w)
+    if args.mode == "matvec":
+        return run_matvec_only(args, w)
+
+    import torch
+    from paper_2308_16712_gb300 import ed
+
+    rank, world, local = dist_setup(args.gpus)
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    n, n_up, z = w["n_sites"], w["n_up"], w["spin_inversion"]
+    op = w["op"]
+    steps = w["lanczos_steps"]
+    O = ed.operator_create(n, op["sites"], op["coeff"], op["local"])
+    B = ed.basis_build(n, n_up, z, w["perms"], w["chars"])
+    dim = ed.basis_size(B)
+    states, _ = ed.basis_states(B)
+    t_gen = generated_terms_per_row(states, n)
+    x0_host = torch.from_numpy(ei.x_by_index(0, dim)[:, 0]).pin_memory()
+    x0 = x0_host.to(dev)
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
+
+    def flush_l2():
+        flush.fill_(1.0)
+
+    def one_step(mode):
+        b = ed.basis_build(n, n_up, z, w["perms"], w["chars"])
+        r = ed.lanczos(O, b, x0, steps, mode)
+        del b
+        return r
+
+    def timed_steps(mode, k, warm):
+        for _ in range(warm):
+            one_step(mode)
+        torch.cuda.synchronize()
+        barrier(world)
+        total_ms, res, mv_ms, mv_n = 0.0, None, 0.0, 0
+        launches0 = ed.launch_count()
+        for _ in range(k):
+            flush_l2()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            res = one_step(mode)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            total_ms += e0.elapsed_time(e1)
+            mv_ms += res.matvec_ms
+            mv_n += res.matvecs
+        launches = ed.launch_count() - launches0
+        barrier(world)
+        return total_ms, res, mv_ms, mv_n, launches
+
+    sampler = ClockSampler(local) if rank == 0 else None
+    ms32, r32, mv32_ms, mv32_n, launches = timed_steps(ed.ED_LANCZOS_F32_MATVEC, args.steps, args.warmup)
+    clocks = sampler.stop() if sampler else None
+    ms64, r64, mv64_ms, mv64_n, _ = timed_steps(ed.ED_LANCZOS_F64, max(1, args.steps), 1)
+    ms32 = max_over_ranks(ms32, world)
+    ms64 = max_over_ranks(ms64, world)
+    per32 = ms32 / args.steps
+    per64 = ms64 / max(1, args.steps)
+    rows32 = dim * r32.matvecs / (per32 * 1e-3)
+    rows64 = dim * r64.matvecs / (per64 * 1e-3)
+    value = sum_over_ranks(rows32, world) if world > 1 else rows32
+
+    # single matvec launches (kernel level), L2 flushed between launches
+    def matvec_rate(dtype, nvec, reps=5):
+        xx = torch.from_numpy(ei.x_by_index(5, dim, nvec)).to(dev).to(dtype)
+        yy = torch.empty_like(xx)
+        ed.matvec(O, B, xx, yy, nvec)
+        tot = 0.0
+        for _ in range(reps):
+            flush_l2()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            ed.matvec(O, B, xx, yy, nvec)
+            b.record(stream)
+            torch.cuda.synchronize()
+            tot += a.elapsed_time(b)
+        return tot / reps
+
+    mv = {}
+    for name, dt, nv in [("f64", torch.float64, 1), ("f32", torch.float32, 1), ("f32_nvec8", torch.float32, 8)]:
+        ms = matvec_rate(dt, nv)
+        mv[name] = {"ms": ms, "rows_per_s": dim / (ms * 1e-3), "vector_rows_per_s": nv * dim / (ms * 1e-3)}
+
+    # roofline of the dominant kernel (the matvec): integer ALU bound
+    pk, pk_kind = peaks()
+    n_perm = len(w["perms"])
+    c_g = 39 if n <= 32 else 94  # INT32 ops per (term, permutation): Benes stages + flip + min
+    int_ops = dim * t_gen * n_perm * c_g
+    avg_ms = (mv32_ms / max(mv32_n, 1)) if mv32_n else mv["f32"]["ms"]
+    achieved = int_ops / (avg_ms * 1e-3) / 1e12
+    peak_int = SMS * INT_LANES_PER_SM * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline and world == 1:
+        cpu = cpu_baseline(w)
+    nnz_row = cpu["nnz_per_row"] if cpu else None
+
+    # end to end through the C ABI: pinned host x0 in, ground state and E0 out
+    host_out = torch.empty(dim, dtype=torch.float64).pin_memory()
+    vec = torch.empty(dim, dtype=torch.float64, device=dev)
+    e2e_ms = 0.0
+    for i in range(1 + args.steps):
+        flush_l2()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        xd = x0_host.to(dev, non_blocking=True)
+        b = ed.basis_build(n, n_up, z, w["perms"], w["chars"])
+        r = ed.lanczos(O, b, xd, steps, ed.ED_LANCZOS_F32_MATVEC, vec_out=vec)
+        host_out.copy_(vec, non_blocking=True)
+        torch.cuda.synchronize()
+        del b
+        if i:
+            e2e_ms += 1e3 * (time.perf_counter() - t0)
+    e2e_ms = max_over_ranks(e2e_ms / args.steps, world)
+    e2e_value = dim * r.matvecs / (e2e_ms * 1e-3)
+    if world > 1:
+        e2e_value = sum_over_ranks(e2e_value, world)
+
+    if rank != 0:
+        return
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": per32, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"{w['name']}: Heisenberg ring N={n}, J=1, Sz=0, k=0, p=+1, z=+1",
+                   "dim": dim, "group_order": n_perm * 2, "lanczos_steps": steps,
+                   "step": "basis build + Lanczos (fp32 matvec, fp64 recurrence, fp64 refinement)",
+                   "l2": "flushed between timed steps", "parallelism": f"replicas x{world}"},
+        "e0": r32.e0, "residual": r32.residual, "matvecs_per_step": r32.matvecs,
+        "fp64_plain": {"value": rows64, "ms_per_step": per64, "e0": r64.e0, "residual": r64.residual,
+                       "matvecs_per_step": r64.matvecs},
+        "dE0": abs(r32.e0 - r64.e0),
+        "speedup_fp32_vs_fp64": rows32 / rows64,
+        "nonzeros_per_s": value * nnz_row if nnz_row else None,
+        "nnz_per_row": nnz_row,
+        "generated_terms_per_row": t_gen,
+        "matvec_kernel": mv,
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_int, "unit": "TOP/s",
+                     "frac": achieved / peak_int, "traffic": None,
+                     "kernel": "k_matvec (fp32, 32-bit Benes group search)",
+                     "int_ops_per_launch": int_ops,
+                     "peak_basis": f"{SMS} SMs x {INT_LANES_PER_SM} INT32 lanes x "
+                                   f"{pk.get('sm_max_mhz', 2070.0):.0f} MHz ({pk_kind} clock)"},
+        "cpu_baseline": cpu,
+        "e2e": {"value": e2e_value, "unit": UNIT, "ms_per_step": e2e_ms,
+                "h2d_bytes_per_step": dim * 8, "d2h_bytes_per_step": dim * 8 + 8},
+        "gpu_launches": launches // max(args.steps, 1) * args.steps,
+        "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,212 @@
+/*
+ * ed.h -- C ABI of the GB300 symmetry-adapted exact-diagonalization hot path.
+ *
+ * The library implements the two operations the paper builds its exact
+ * diagonalization on, for spin-1/2 systems on one GPU:
+ *
+ *  - the basis of symmetry representatives (Sec. "States enumeration";
+ *    Background, Fig. 1: U(1) restriction and lattice symmetries), stored as
+ *    one ascending uint64 array with an integer orbit norm per element;
+ *  - the matrix-free matrix-vector product y_i = sum_j H_ij x_j over that
+ *    basis (Sec. "Matrix-vector product"), computed row by row ("pull"),
+ *    without atomics, by generating H|r> term by term, mapping every produced
+ *    state to its representative and finding that representative's index by
+ *    search in the sorted basis ("stateToIndex");
+ *
+ * plus the Krylov eigensolver that consumes it (Background: Lanczos).
+ *
+ * Conventions (used by every call):
+ *  - site i <-> bit i of a uint64 state, bit value 1 = spin up; at most 64 sites.
+ *  - a group element is a site permutation perm (site i goes to site perm[i]:
+ *    bit perm[i] of g.s equals bit i of s) with a character chi (complex, |chi|=1).
+ *    Spin inversion F (complement all n_sites bits) is added by the library as
+ *    a direct-product factor with character z = spin_inversion.
+ *  - representative rep(s) = min over the group of g.s (unsigned compare);
+ *    orbit norm n(s) = |Stab(s)| if chi == 1 on the stabilizer, else 0; the
+ *    basis holds the states with s == rep(s) and n(s) != 0, ascending.
+ *  - matrix element (pull form): for row r and each term of H|r> = sum_s h_s|s>
+ *    with r' = rep(s) = g*.s:  y_r += conj(h_s) chi(g*) sqrt(n(r')/n(r)) x_idx(r').
+ *  - vectors are device arrays laid out [dim][nvec] (nvec values of one basis
+ *    row are contiguous), 16-byte aligned; complex values are (re, im) pairs.
+ *
+ * Ownership: handles are created and destroyed by the library and are not
+ * modified after creation (they may be used from several streams at once).
+ * Device arrays passed in (x, y, queries, results) belong to the caller.
+ * Host arrays passed in are only read during the call.
+ *
+ * Errors: every call returns an ed_status.  Argument and shape errors are
+ * detected on the host before any launch.  A `stream` argument is a
+ * cudaStream_t (NULL = the legacy default stream); calls that take one enqueue
+ * their work on it and return without synchronising unless stated otherwise.
+ */
+#ifndef ED_H
+#define ED_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    ED_OK = 0,
+    ED_ERR_INVALID_ARG = 1,      /* null pointer, size out of range, misaligned array */
+    ED_ERR_NOT_A_GROUP = 2,      /* not closed, no identity, repeated element, not a permutation */
+    ED_ERR_BAD_CHARACTER = 3,    /* |chi| != 1 or chi(a b) != chi(a) chi(b) (tolerance 1e-9) */
+    ED_ERR_SYMMETRY_MISMATCH = 4,/* the operator does not commute with the group */
+    ED_ERR_OOM = 5,              /* device allocation failed */
+    ED_ERR_CUDA = 6,             /* a CUDA runtime call failed */
+    ED_ERR_INTERNAL = 7,         /* a device-side invariant check failed */
+    ED_ERR_NOT_CONVERGED = 8,    /* Lanczos residual above the requested tolerance */
+    ED_ERR_UNSUPPORTED = 9       /* valid request outside what this build implements */
+} ed_status;
+
+typedef enum {
+    ED_F64 = 0,  /* double                     */
+    ED_F32 = 1,  /* float                      */
+    ED_C128 = 2, /* complex double, (re, im)   */
+    ED_C64 = 3   /* complex float, (re, im)    */
+} ed_dtype;
+
+typedef struct ed_basis ed_basis;
+typedef struct ed_operator ed_operator;
+
+/* Human-readable name of a status code (static string). */
+const char *ed_status_string(ed_status status);
+
+/*
+ * ed_basis_build -- enumerate the representatives of one symmetry sector
+ * (Sec. "States enumeration": chunked filter of the bitstring range; the
+ * filter condition is the representative test and nonzero orbit norm above).
+ *
+ *   n_sites        1..64
+ *   n_up           number of up spins (U(1) sector, Background / Fig. 1), 0..n_sites;
+ *                  -1 = no U(1) restriction (then n_sites <= 40)
+ *   spin_inversion 0 (not used), +1 or -1 (its character z); nonzero requires
+ *                  2*n_up == n_sites or n_up == -1
+ *   n_elems        number of lattice group elements, 1..1024
+ *   perms          host, n_elems x n_sites int32, row g = permutation of element g
+ *   chars          host, n_elems x 2 double (re, im) = chi(g); must be a
+ *                  one-dimensional unitary representation of the permutation group
+ *   stream         cudaStream_t for the enumeration kernels
+ *   out            receives the new handle
+ *
+ * The call synchronises `stream` once (to size the output).  Errors:
+ * ED_ERR_INVALID_ARG, ED_ERR_NOT_A_GROUP, ED_ERR_BAD_CHARACTER, ED_ERR_OOM,
+ * ED_ERR_CUDA, ED_ERR_INTERNAL.
+ */
+ed_status ed_basis_build(int n_sites, int n_up, int spin_inversion, int n_elems,
+                         const int32_t *perms, const double *chars, void *stream,
+                         ed_basis **out);
+
+/* Number of representatives (the sector dimension). */
+ed_status ed_basis_size(const ed_basis *basis, uint64_t *dim);
+
+/* Borrowed device pointers to the ascending states (dim x uint64) and the
+ * orbit norms (dim x uint16).  Valid until ed_basis_destroy. */
+ed_status ed_basis_states(const ed_basis *basis, const uint64_t **d_states,
+                          const uint16_t **d_norms);
+
+/* 1 if every character (spin inversion included) is real, else 0: real
+ * sectors may use ED_F64 / ED_F32 vectors, complex ones need ED_C128 / ED_C64. */
+ed_status ed_basis_is_real(const ed_basis *basis, int *is_real);
+
+/*
+ * ed_basis_index -- "stateToIndex" (Sec. "Matrix-vector product"): position
+ * of each query state in the basis, or -1 if it is not a basis element.
+ *   d_query  device, n x uint64;  d_index  device, n x int64 (written).
+ */
+ed_status ed_basis_index(const ed_basis *basis, const uint64_t *d_query, int64_t *d_index,
+                         uint64_t n, void *stream);
+
+/* Release the basis and its device memory (synchronises the device). */
+void ed_basis_destroy(ed_basis *basis);
+
+/*
+ * ed_operator_create -- H = sum_t coeff_t * h_t acting on the site pair
+ * (sites[2t], sites[2t+1]) (the analytic Hamiltonian the matrix elements are
+ * generated from, Sec. "Matrix-vector product", getRow / getManyRows).
+ *
+ *   n_sites  1..64
+ *   n_terms  1..4096
+ *   coeff    host, n_terms x 2 double (re, im)
+ *   sites    host, n_terms x 2 int32, two distinct sites in [0, n_sites)
+ *   local    host, n_terms x 16 x 2 double: the 4x4 complex matrix h_t on
+ *            |s_i s_j>, row-major, row/column index 2*s_i + s_j
+ *
+ * H must be Hermitian for the matrix elements above to be those of H.
+ * Errors: ED_ERR_INVALID_ARG.
+ */
+ed_status ed_operator_create(int n_sites, int n_terms, const double *coeff,
+                             const int32_t *sites, const double *local, ed_operator **out);
+
+void ed_operator_destroy(ed_operator *op);
+
+/*
+ * ed_matvec -- y = H x over the basis (Sec. "Matrix-vector product",
+ * y_i = sum_j H_ij x_j), overwriting y.
+ *
+ *   d_x, d_y  device, dim x nvec of `dtype`, 16-byte aligned, not overlapping
+ *   nvec      1..16 vectors multiplied at once (one representative search per
+ *             matrix element serves all of them)
+ *   dtype     ED_F64 / ED_F32 (real sectors only) or ED_C128 / ED_C64;
+ *             the arithmetic is done in that precision
+ *
+ * No allocation and no host synchronisation.  Deterministic: the same inputs
+ * give bit-identical y.  Errors: ED_ERR_INVALID_ARG (including a complex
+ * sector with a real dtype, or operator/basis with different n_sites),
+ * ED_ERR_SYMMETRY_MISMATCH, ED_ERR_CUDA.
+ */
+ed_status ed_matvec(const ed_operator *op, const ed_basis *basis, const void *d_x, void *d_y,
+                    int nvec, ed_dtype dtype, void *stream);
+
+/* Lanczos precision modes. */
+typedef enum {
+    ED_LANCZOS_F64 = 0,        /* fp64 matvec, fp64 recurrence                     */
+    ED_LANCZOS_F32_MATVEC = 1, /* fp32 matvec, fp64 recurrence and fp64 refinement */
+    ED_LANCZOS_RECOMPUTE = 16  /* flag: form the Ritz vector by a second pass even
+                                  when the Krylov vectors would fit in memory      */
+} ed_lanczos_mode;
+
+typedef struct {
+    int steps;            /* Lanczos steps taken (stops early on an invariant subspace) */
+    int matvecs;          /* matrix-vector products performed, refinement included */
+    double ritz;          /* lowest Ritz value of the tridiagonal matrix */
+    double e0;            /* returned energy: fp64 Rayleigh quotient of the Ritz vector */
+    double residual;      /* |H psi - e0 psi| / |psi| in fp64 */
+    double matvec_ms;     /* device time spent in the matvec kernels, summed over
+                             all products (CUDA events on `stream` around each) */
+} ed_lanczos_info;
+
+/*
+ * ed_lanczos -- lowest eigenvalue of H in the sector by the Lanczos
+ * recurrence (Background: Krylov methods consume hundreds of matvecs).
+ *
+ *   d_x0      device start vector, dim values: double for real sectors,
+ *             (re, im) double pairs for complex ones; need not be normalised
+ *   steps     1..10000 Lanczos steps (no restart)
+ *   mode      ED_LANCZOS_F64 or ED_LANCZOS_F32_MATVEC, optionally OR-ed with
+ *             ED_LANCZOS_RECOMPUTE
+ *   e0_out    host, receives the energy (may be NULL)
+ *   d_vec_out device, dim values as d_x0, receives the normalised ground-state
+ *             approximation (may be NULL)
+ *   info      host, filled (may be NULL)
+ *
+ * The alpha/beta recurrence, dot products (compensated fp64 sums) and the
+ * tridiagonal eigensolve run in fp64 on the GPU.  The Ritz vector is formed
+ * from stored Krylov vectors when they fit in device memory, else by a second,
+ * bit-identical pass of the recurrence.  It is then refined in fp64: a few
+ * fp64 Lanczos steps started from it, whose lowest Ritz value is returned
+ * together with its residual.  Allocates its work vectors; synchronises
+ * `stream` before returning.
+ * Errors: ED_ERR_INVALID_ARG, ED_ERR_SYMMETRY_MISMATCH, ED_ERR_OOM, ED_ERR_CUDA.
+ */
+ed_status ed_lanczos(const ed_operator *op, const ed_basis *basis, const void *d_x0, int steps,
+                     int mode, double *e0_out, void *d_vec_out, ed_lanczos_info *info,
+                     void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ED_H */

@@ -1,0 +1,707 @@
+// ed_api.cu -- the C ABI: argument and group validation, Benes routing of the
+// site permutations, handle management and dispatch to the kernels.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <complex>
+#include <cstring>
+#include <map>
+#include <vector>
+
+#include "ed_kernels.cuh"
+
+using cplx = std::complex<double>;
+
+namespace {
+
+constexpr double kChiTol = 1e-9;
+
+#define ED_CUDA_TRY(expr)                                  \
+    do {                                                   \
+        cudaError_t _e = (expr);                           \
+        if (_e != cudaSuccess) {                           \
+            (void)cudaGetLastError();                      \
+            return _e == cudaErrorMemoryAllocation ? ED_ERR_OOM : ED_ERR_CUDA; \
+        }                                                  \
+    } while (0)
+
+// ---------------------------------------------------------------------------
+// Benes routing.  `sigma` maps local position a -> local destination sigma[a]
+// inside the sub-network [base, base + 2^lsub).  Every token (bit) is sent to
+// the lower or the upper half by the input stage such that the two tokens of
+// an input pair (a, a ^ d) and the two tokens bound for an output pair
+// (b, b ^ d) take different halves (2-colouring of even cycles), the halves
+// are routed recursively, and the output stage puts each token in place.
+// ---------------------------------------------------------------------------
+void benes_route(int lsub, int base, const std::vector<int> &sigma, int ltot,
+                 std::vector<uint64_t> &masks)
+{
+    const int m = 1 << lsub;
+    if (m == 2) {
+        if (sigma[0] == 1)
+            masks[ltot - 1] |= 1ULL << base;
+        return;
+    }
+    const int d = m / 2;
+    std::vector<int> inv(m), side(m, -1);
+    for (int a = 0; a < m; ++a)
+        inv[sigma[a]] = a;
+    for (int a0 = 0; a0 < m; ++a0) {
+        if (side[a0] >= 0)
+            continue;
+        int a = a0;
+        while (side[a] < 0) {
+            side[a] = 0;
+            const int ap = a ^ d;
+            side[ap] = 1;
+            a = inv[sigma[ap] ^ d];
+        }
+    }
+    const int level = lsub - 1;
+    const int in_stage = ltot - 1 - level, out_stage = ltot - 1 + level;
+    std::vector<int> lower(d), upper(d);
+    for (int a = 0; a < m; ++a) {
+        if (a < d && side[a] == 1)
+            masks[in_stage] |= 1ULL << (base + a);
+        (side[a] == 0 ? lower : upper)[a & (d - 1)] = sigma[a] & (d - 1);
+    }
+    for (int b = 0; b < d; ++b)
+        if (side[inv[b]] == 1)
+            masks[out_stage] |= 1ULL << (base + b);
+    benes_route(lsub - 1, base, lower, ltot, masks);
+    benes_route(lsub - 1, base + d, upper, ltot, masks);
+}
+
+// Masks (2*log2w - 1 stages) realising "bit i moves to perm[i]" on a w-bit word.
+std::vector<uint64_t> benes_masks(int log2w, int n, const int32_t *perm)
+{
+    const int w = 1 << log2w;
+    std::vector<int> sigma(w);
+    for (int i = 0; i < w; ++i)
+        sigma[i] = i < n ? perm[i] : i;
+    std::vector<uint64_t> masks(2 * log2w - 1, 0);
+    benes_route(log2w, 0, sigma, log2w, masks);
+    return masks;
+}
+
+// ---------------------------------------------------------------------------
+// group checks: each row a permutation, identity present, no repeats, closed
+// under composition (a.b)[i] = a[b[i]], chi a unitary homomorphism.
+// ---------------------------------------------------------------------------
+ed_status validate_group(int n, int ne, const int32_t *perms, const double *chars)
+{
+    std::map<std::vector<int32_t>, int> index;
+    bool has_identity = false;
+    for (int g = 0; g < ne; ++g) {
+        std::vector<int32_t> p(perms + (size_t)g * n, perms + (size_t)(g + 1) * n);
+        std::vector<char> seen(n, 0);
+        bool ident = true;
+        for (int i = 0; i < n; ++i) {
+            if (p[i] < 0 || p[i] >= n || seen[p[i]])
+                return ED_ERR_NOT_A_GROUP;
+            seen[p[i]] = 1;
+            ident = ident && p[i] == i;
+        }
+        has_identity = has_identity || ident;
+        if (!index.emplace(p, g).second)
+            return ED_ERR_NOT_A_GROUP;
+        const cplx c(chars[2 * g], chars[2 * g + 1]);
+        if (!std::isfinite(c.real()) || !std::isfinite(c.imag()) ||
+            std::abs(std::abs(c) - 1.0) > kChiTol)
+            return ED_ERR_BAD_CHARACTER;
+        if (ident && std::abs(c - 1.0) > kChiTol)
+            return ED_ERR_BAD_CHARACTER;
+    }
+    if (!has_identity)
+        return ED_ERR_NOT_A_GROUP;
+    std::vector<int32_t> comp(n);
+    for (int a = 0; a < ne; ++a) {
+        for (int b = 0; b < ne; ++b) {
+            for (int i = 0; i < n; ++i)
+                comp[i] = perms[(size_t)a * n + perms[(size_t)b * n + i]];
+            auto it = index.find(comp);
+            if (it == index.end())
+                return ED_ERR_NOT_A_GROUP;
+            const int c = it->second;
+            const cplx ca(chars[2 * a], chars[2 * a + 1]), cb(chars[2 * b], chars[2 * b + 1]);
+            const cplx cc(chars[2 * c], chars[2 * c + 1]);
+            if (std::abs(cc - ca * cb) > kChiTol)
+                return ED_ERR_BAD_CHARACTER;
+        }
+    }
+    return ED_OK;
+}
+
+uint64_t binomial(int n, int k)
+{
+    if (k < 0 || k > n)
+        return 0;
+    unsigned __int128 r = 1;
+    for (int i = 1; i <= k; ++i)
+        r = r * (unsigned)(n - k + i) / (unsigned)i;
+    return (uint64_t)r;
+}
+
+template <typename T>
+cudaError_t upload(T **dst, const T *src, size_t count)
+{
+    cudaError_t e = cudaMalloc((void **)dst, std::max<size_t>(count, 1) * sizeof(T));
+    if (e != cudaSuccess)
+        return e;
+    if (count)
+        e = cudaMemcpy(*dst, src, count * sizeof(T), cudaMemcpyHostToDevice);
+    return e;
+}
+
+void free_basis(ed_basis *b)
+{
+    if (!b)
+        return;
+    cudaFree(b->d_states);
+    cudaFree(b->d_norms);
+    cudaFree(b->d_tab);
+    cudaFree(b->d_masks32);
+    cudaFree(b->d_masks64);
+    cudaFree(b->d_chi);
+    cudaFree(b->d_chif);
+    cudaFree(b->d_chi_one);
+    delete b;
+}
+
+// Does the operator commute with every element of the (expanded) group?
+// Terms are summed per ordered site pair into 4x4 matrices; an element maps
+// the term on (i, j) to (perm[i], perm[j]) and, if it flips, conjugates the
+// matrix by X (x) X.
+bool operator_is_symmetric(const ed_operator *op, int n_perm, const int32_t *perms,
+                           int spin_inversion)
+{
+    using Key = std::pair<int, int>;
+    auto canon = [&](const int32_t *pm, bool flip) {
+        std::map<Key, std::vector<cplx>> out;
+        for (int t = 0; t < op->n_terms; ++t) {
+            int i = op->sites[2 * t], j = op->sites[2 * t + 1];
+            if (pm) {
+                i = pm[i];
+                j = pm[j];
+            }
+            const double *mm = op->mats.data() + (size_t)op->mat_of_term[t] * 32;
+            std::vector<cplx> h(16);
+            for (int r = 0; r < 4; ++r)
+                for (int c = 0; c < 4; ++c) {
+                    int rr = flip ? 3 - r : r, cc = flip ? 3 - c : c;
+                    h[rr * 4 + cc] = cplx(mm[2 * (r * 4 + c)], mm[2 * (r * 4 + c) + 1]);
+                }
+            if (i > j) {  // swap the tensor factors: index 2a+b -> 2b+a
+                std::vector<cplx> s(16);
+                auto sw = [](int x) { return ((x & 1) << 1) | (x >> 1); };
+                for (int r = 0; r < 4; ++r)
+                    for (int c = 0; c < 4; ++c)
+                        s[sw(r) * 4 + sw(c)] = h[r * 4 + c];
+                h = s;
+                std::swap(i, j);
+            }
+            auto &acc = out[Key(i, j)];
+            if (acc.empty())
+                acc.assign(16, cplx(0));
+            for (int e = 0; e < 16; ++e)
+                acc[e] += h[e];
+        }
+        return out;
+    };
+    const auto ref = canon(nullptr, false);
+    double scale = 0;
+    for (auto &kv : ref)
+        for (auto &v : kv.second)
+            scale = std::max(scale, std::abs(v));
+    const double tol = 1e-12 * std::max(1.0, scale);
+    auto same = [&](const std::map<Key, std::vector<cplx>> &m) {
+        auto val = [&](const std::map<Key, std::vector<cplx>> &x, const Key &k, int e) {
+            auto it = x.find(k);
+            return it == x.end() ? cplx(0) : it->second[e];
+        };
+        for (auto &kv : ref)
+            for (int e = 0; e < 16; ++e)
+                if (std::abs(val(m, kv.first, e) - kv.second[e]) > tol)
+                    return false;
+        for (auto &kv : m)
+            for (int e = 0; e < 16; ++e)
+                if (std::abs(val(ref, kv.first, e) - kv.second[e]) > tol)
+                    return false;
+        return true;
+    };
+    for (int g = 0; g < n_perm; ++g) {
+        const int32_t *pm = perms + (size_t)g * op->n_sites;
+        if (!same(canon(pm, false)))
+            return false;
+        if (spin_inversion && !same(canon(pm, true)))
+            return false;
+    }
+    return true;
+}
+
+
+// The host part of an operator: scaled, deduplicated matrices and the packed
+// term table.  Arguments must already be validated.
+ed_operator *build_operator_host(int n_sites, int n_terms, const double *coeff,
+                                 const int32_t *sites, const double *local)
+{
+    ed_operator *op = new ed_operator();
+    op->n_sites = n_sites;
+    op->n_terms = n_terms;
+    op->sites.assign(sites, sites + 2 * (size_t)n_terms);
+    // scaled matrices coeff_t * h_t, deduplicated
+    std::map<std::vector<double>, int> seen;
+    for (int t = 0; t < n_terms; ++t) {
+        const cplx c(coeff[2 * t], coeff[2 * t + 1]);
+        std::vector<double> m(32);
+        for (int e = 0; e < 16; ++e) {
+            const cplx v = c * cplx(local[(size_t)t * 32 + 2 * e], local[(size_t)t * 32 + 2 * e + 1]);
+            m[2 * e] = v.real();
+            m[2 * e + 1] = v.imag();
+            if (v.imag() != 0.0)
+                op->real = false;
+        }
+        auto it = seen.find(m);
+        int id;
+        if (it == seen.end()) {
+            id = (int)seen.size();
+            seen.emplace(m, id);
+            op->mats.insert(op->mats.end(), m.begin(), m.end());
+        } else {
+            id = it->second;
+        }
+        op->mat_of_term.push_back(id);
+    }
+    op->n_mats = (int)seen.size();
+    if (op->n_mats > 65535) {
+        delete op;
+        return nullptr;
+    }
+    std::vector<uint8_t> offmask((size_t)op->n_mats * 4, 0);
+    std::vector<double2> md((size_t)op->n_mats * 16);
+    std::vector<float2> mf((size_t)op->n_mats * 16);
+    for (int k = 0; k < op->n_mats; ++k) {
+        for (int e = 0; e < 16; ++e) {
+            const double re = op->mats[(size_t)k * 32 + 2 * e], im = op->mats[(size_t)k * 32 + 2 * e + 1];
+            md[(size_t)k * 16 + e] = make_double2(re, im);
+            mf[(size_t)k * 16 + e] = make_float2((float)re, (float)im);
+            const int r = e / 4, c = e % 4;
+            if (r != c && (re != 0.0 || im != 0.0))
+                offmask[(size_t)k * 4 + c] |= (uint8_t)(1u << r);
+        }
+    }
+    // the most off-diagonal elements one row can produce
+    int worst = 0;
+    for (int t = 0; t < n_terms; ++t) {
+        int best = 0;
+        for (int c = 0; c < 4; ++c)
+            best = std::max(best, __builtin_popcount(offmask[(size_t)op->mat_of_term[t] * 4 + c]));
+        worst += best;
+    }
+    op->max_offdiag = worst;
+    op->h_terms.resize(n_terms);
+    for (int t = 0; t < n_terms; ++t)
+        op->h_terms[t] = (uint32_t)sites[2 * t] | ((uint32_t)sites[2 * t + 1] << 8) |
+                         ((uint32_t)op->mat_of_term[t] << 16);
+    op->h_mats = std::move(md);
+    op->h_matsf = std::move(mf);
+    op->h_offmask = std::move(offmask);
+    return op;
+}
+
+edk::OpView op_view(const ed_operator *op)
+{
+    return edk::OpView{op->n_terms, op->n_mats, op->d_terms, op->d_mats, op->d_matsf,
+                       op->d_offmask};
+}
+
+}  // namespace
+
+namespace edk {
+
+static std::atomic<unsigned long long> g_launches{0};
+void count_launch(unsigned n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+
+// Operator/basis compatibility and the symmetry check (cached per basis).
+ed_status check_pair(const ed_operator *op, const ed_basis *b)
+{
+    if (!op || !b)
+        return ED_ERR_INVALID_ARG;
+    if (op->n_sites != b->n_sites)
+        return ED_ERR_INVALID_ARG;
+    if (op->checked.load() == b)
+        return ED_OK;
+    if (!operator_is_symmetric(op, b->n_perm, b->perms.data(), b->spin_inversion))
+        return ED_ERR_SYMMETRY_MISMATCH;
+    op->checked.store(b);
+    return ED_OK;
+}
+
+}  // namespace edk
+
+edk::GroupView ed_basis::group_view() const
+{
+    edk::GroupView g;
+    g.n_sites = n_sites;
+    g.n_perm = n_perm;
+    g.flip = spin_inversion != 0;
+    g.order = order;
+    g.full = n_sites >= 64 ? ~0ULL : ((1ULL << n_sites) - 1);
+    g.masks32 = d_masks32;
+    g.masks64 = d_masks64;
+    g.chi = d_chi;
+    g.chif = d_chif;
+    g.chi_one = d_chi_one;
+    return g;
+}
+
+edk::IndexView ed_basis::index_view() const
+{
+    return edk::IndexView{d_states, d_norms, dim, d_tab, tab_size, e_lo, e_hi, mbits};
+}
+
+// ---------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------
+extern "C" {
+
+const char *ed_status_string(ed_status s)
+{
+    switch (s) {
+    case ED_OK: return "ok";
+    case ED_ERR_INVALID_ARG: return "invalid argument";
+    case ED_ERR_NOT_A_GROUP: return "permutations do not form a group";
+    case ED_ERR_BAD_CHARACTER: return "characters are not a one-dimensional unitary representation";
+    case ED_ERR_SYMMETRY_MISMATCH: return "operator does not commute with the symmetry group";
+    case ED_ERR_OOM: return "device out of memory";
+    case ED_ERR_CUDA: return "CUDA runtime error";
+    case ED_ERR_INTERNAL: return "device-side invariant check failed";
+    case ED_ERR_NOT_CONVERGED: return "not converged";
+    case ED_ERR_UNSUPPORTED: return "unsupported by this build";
+    }
+    return "unknown status";
+}
+
+ed_status ed_basis_build(int n_sites, int n_up, int spin_inversion, int n_elems,
+                         const int32_t *perms, const double *chars, void *stream_, ed_basis **out)
+{
+    if (!out || !perms || !chars)
+        return ED_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (n_sites < 1 || n_sites > 64 || n_elems < 1 || n_elems > 1024)
+        return ED_ERR_INVALID_ARG;
+    if (n_up < -1 || n_up > n_sites || (n_up == -1 && n_sites > 40))
+        return ED_ERR_INVALID_ARG;
+    if (spin_inversion < -1 || spin_inversion > 1)
+        return ED_ERR_INVALID_ARG;
+    if (spin_inversion != 0 && n_up != -1 && 2 * n_up != n_sites)
+        return ED_ERR_INVALID_ARG;
+    ed_status st = validate_group(n_sites, n_elems, perms, chars);
+    if (st != ED_OK)
+        return st;
+    cudaStream_t stream = (cudaStream_t)stream_;
+
+    ed_basis *b = new ed_basis();
+    cudaGetDevice(&b->device);
+    b->n_sites = n_sites;
+    b->n_up = n_up;
+    b->spin_inversion = spin_inversion;
+    b->n_perm = n_elems;
+    b->order = n_elems * (spin_inversion ? 2 : 1);
+    b->perms.assign(perms, perms + (size_t)n_elems * n_sites);
+    b->chars.assign(chars, chars + 2 * (size_t)n_elems);
+
+    // expanded characters: plain elements, then flipped ones (times z)
+    std::vector<double2> chi(b->order);
+    std::vector<float2> chif(b->order);
+    std::vector<uint32_t> one((b->order + 31) / 32, 0);
+    b->trivial_chars = true;
+    b->real_chars = true;
+    for (int g = 0; g < b->order; ++g) {
+        const int p = g % n_elems;
+        cplx c(chars[2 * p], chars[2 * p + 1]);
+        if (g >= n_elems)
+            c *= (double)spin_inversion;
+        chi[g] = make_double2(c.real(), c.imag());
+        chif[g] = make_float2((float)c.real(), (float)c.imag());
+        const bool is_one = std::abs(c - 1.0) < kChiTol;
+        if (is_one)
+            one[g / 32] |= 1u << (g % 32);
+        b->trivial_chars = b->trivial_chars && is_one;
+        b->real_chars = b->real_chars && std::abs(c.imag()) < kChiTol;
+    }
+    // Benes masks for 32- and 64-bit words
+    std::vector<uint32_t> m32((size_t)n_elems * edk::kMaskStride, 0);
+    std::vector<uint64_t> m64((size_t)n_elems * edk::kMaskStride, 0);
+    for (int g = 0; g < n_elems; ++g) {
+        const int32_t *pm = perms + (size_t)g * n_sites;
+        if (n_sites <= 32) {
+            auto m = benes_masks(5, n_sites, pm);
+            for (int s = 0; s < 9; ++s)
+                m32[(size_t)g * edk::kMaskStride + s] = (uint32_t)m[s];
+        }
+        auto m = benes_masks(6, n_sites, pm);
+        for (int s = 0; s < 11; ++s)
+            m64[(size_t)g * edk::kMaskStride + s] = m[s];
+    }
+#define ED_B_TRY(expr)                           \
+    do {                                         \
+        cudaError_t _e = (expr);                 \
+        if (_e != cudaSuccess) {                 \
+            (void)cudaGetLastError();            \
+            free_basis(b);                       \
+            cudaFree(d_counts);                  \
+            cudaFree(d_offsets);                 \
+            cudaFree(d_tmp);                     \
+            cudaFree(d_binom);                   \
+            cudaFree(d_flag);                    \
+            return _e == cudaErrorMemoryAllocation ? ED_ERR_OOM : ED_ERR_CUDA; \
+        }                                        \
+    } while (0)
+    uint32_t *d_counts = nullptr;
+    uint64_t *d_offsets = nullptr, *d_tmp = nullptr, *d_binom = nullptr;
+    int *d_flag = nullptr;
+    ED_B_TRY(upload(&b->d_masks32, m32.data(), m32.size()));
+    ED_B_TRY(upload(&b->d_masks64, m64.data(), m64.size()));
+    ED_B_TRY(upload(&b->d_chi, chi.data(), chi.size()));
+    ED_B_TRY(upload(&b->d_chif, chif.data(), chif.size()));
+    ED_B_TRY(upload(&b->d_chi_one, one.data(), one.size()));
+
+    // enumeration plan
+    std::vector<uint64_t> binom(65 * 65);
+    for (int n = 0; n <= 64; ++n)
+        for (int k = 0; k <= 64; ++k)
+            binom[n * 65 + k] = binomial(n, k);
+    ED_B_TRY(upload(&d_binom, binom.data(), binom.size()));
+    edk::EnumPlan plan;
+    plan.n_sites = n_sites;
+    plan.n_up = n_up;
+    plan.total = n_up < 0 ? (1ULL << n_sites) : binomial(n_sites, n_up);
+    int sms = 148;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device);
+    const uint64_t threads = (uint64_t)sms * 2048 * 4;
+    plan.chunk = std::max<uint64_t>(16, (plan.total + threads - 1) / threads);
+    plan.n_chunks = (plan.total + plan.chunk - 1) / plan.chunk;
+    plan.binom = d_binom;
+    const edk::GroupView gv = b->group_view();
+
+    ED_B_TRY(cudaMalloc(&d_counts, plan.n_chunks * sizeof(uint32_t)));
+    ED_B_TRY(cudaMalloc(&d_offsets, (plan.n_chunks + 1) * sizeof(uint64_t)));
+    ED_B_TRY(cudaMalloc(&d_tmp, edk::scan_tmp_words(plan.n_chunks) * sizeof(uint64_t)));
+    ED_B_TRY(edk::launch_enum_count(plan, gv, d_counts, stream));
+    ED_B_TRY(edk::launch_scan(d_counts, plan.n_chunks, d_offsets, d_tmp, stream));
+    uint64_t dim = 0;
+    ED_B_TRY(cudaMemcpyAsync(&dim, d_offsets + plan.n_chunks, sizeof(uint64_t),
+                             cudaMemcpyDeviceToHost, stream));
+    ED_B_TRY(cudaStreamSynchronize(stream));
+    if (dim >= (1ULL << 32)) {
+        free_basis(b);
+        cudaFree(d_counts); cudaFree(d_offsets); cudaFree(d_tmp); cudaFree(d_binom);
+        return ED_ERR_UNSUPPORTED;
+    }
+    b->dim = dim;
+    ED_B_TRY(cudaMalloc(&b->d_states, std::max<uint64_t>(dim, 1) * sizeof(uint64_t)));
+    ED_B_TRY(cudaMalloc(&b->d_norms, std::max<uint64_t>(dim, 1) * sizeof(uint16_t)));
+    ED_B_TRY(edk::launch_enum_write(plan, gv, d_offsets, b->d_states, b->d_norms, stream));
+
+    // prefix table over the bit-length range of the basis
+    uint64_t ends[2] = {0, 0};
+    if (dim) {
+        ED_B_TRY(cudaMemcpyAsync(&ends[0], b->d_states, 8, cudaMemcpyDeviceToHost, stream));
+        ED_B_TRY(cudaMemcpyAsync(&ends[1], b->d_states + dim - 1, 8, cudaMemcpyDeviceToHost, stream));
+        ED_B_TRY(cudaStreamSynchronize(stream));
+    }
+    auto bitlen = [](uint64_t s) { return s ? 64 - __builtin_clzll(s) : 0; };
+    b->e_lo = bitlen(ends[0]);
+    b->e_hi = bitlen(ends[1]);
+    const int n_exp = b->e_hi - b->e_lo + 1;
+    int mb = 0;
+    while (mb < 26 && ((uint64_t)n_exp << (mb + 1)) * 4 <= std::max<uint64_t>(dim, 1))
+        ++mb;
+    b->mbits = mb;
+    b->tab_size = (uint64_t)n_exp << mb;
+    ED_B_TRY(cudaMalloc(&b->d_tab, (b->tab_size + 1) * sizeof(uint32_t)));
+    ED_B_TRY(edk::launch_prefix_table(b->index_view(), b->d_tab, stream));
+    ED_B_TRY(cudaMalloc(&d_flag, sizeof(int)));
+    ED_B_TRY(cudaMemsetAsync(d_flag, 0, sizeof(int), stream));
+    ED_B_TRY(edk::launch_check_sorted(b->d_states, dim, d_flag, stream));
+    int flag = 0;
+    ED_B_TRY(cudaMemcpyAsync(&flag, d_flag, sizeof(int), cudaMemcpyDeviceToHost, stream));
+    ED_B_TRY(cudaStreamSynchronize(stream));
+    cudaFree(d_counts);
+    cudaFree(d_offsets);
+    cudaFree(d_tmp);
+    cudaFree(d_binom);
+    cudaFree(d_flag);
+#undef ED_B_TRY
+    if (flag) {
+        free_basis(b);
+        return ED_ERR_INTERNAL;
+    }
+    *out = b;
+    return ED_OK;
+}
+
+ed_status ed_basis_size(const ed_basis *b, uint64_t *dim)
+{
+    if (!b || !dim)
+        return ED_ERR_INVALID_ARG;
+    *dim = b->dim;
+    return ED_OK;
+}
+
+ed_status ed_basis_states(const ed_basis *b, const uint64_t **s, const uint16_t **n)
+{
+    if (!b || !s || !n)
+        return ED_ERR_INVALID_ARG;
+    *s = b->d_states;
+    *n = b->d_norms;
+    return ED_OK;
+}
+
+ed_status ed_basis_is_real(const ed_basis *b, int *is_real)
+{
+    if (!b || !is_real)
+        return ED_ERR_INVALID_ARG;
+    *is_real = b->real_chars ? 1 : 0;
+    return ED_OK;
+}
+
+ed_status ed_basis_index(const ed_basis *b, const uint64_t *q, int64_t *idx, uint64_t n,
+                         void *stream)
+{
+    if (!b || (n && (!q || !idx)))
+        return ED_ERR_INVALID_ARG;
+    if (!n)
+        return ED_OK;
+    ED_CUDA_TRY(edk::launch_index(b->index_view(), q, idx, n, (cudaStream_t)stream));
+    return ED_OK;
+}
+
+void ed_basis_destroy(ed_basis *b)
+{
+    if (b)
+        cudaDeviceSynchronize();
+    free_basis(b);
+}
+
+ed_status ed_operator_create(int n_sites, int n_terms, const double *coeff, const int32_t *sites,
+                             const double *local, ed_operator **out)
+{
+    if (!out || !coeff || !sites || !local)
+        return ED_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (n_sites < 1 || n_sites > 64 || n_terms < 1 || n_terms > 4096)
+        return ED_ERR_INVALID_ARG;
+    for (int t = 0; t < n_terms; ++t) {
+        const int i = sites[2 * t], j = sites[2 * t + 1];
+        if (i < 0 || j < 0 || i >= n_sites || j >= n_sites || i == j)
+            return ED_ERR_INVALID_ARG;
+    }
+    for (size_t e = 0; e < (size_t)n_terms * 32; ++e)
+        if (!std::isfinite(local[e]))
+            return ED_ERR_INVALID_ARG;
+    ed_operator *op = build_operator_host(n_sites, n_terms, coeff, sites, local);
+    if (!op)
+        return ED_ERR_INVALID_ARG;
+    cudaError_t e = upload(&op->d_terms, op->h_terms.data(), op->h_terms.size());
+    if (e == cudaSuccess)
+        e = upload(&op->d_mats, op->h_mats.data(), op->h_mats.size());
+    if (e == cudaSuccess)
+        e = upload(&op->d_matsf, op->h_matsf.data(), op->h_matsf.size());
+    if (e == cudaSuccess)
+        e = upload(&op->d_offmask, op->h_offmask.data(), op->h_offmask.size());
+    if (e != cudaSuccess) {
+        (void)cudaGetLastError();
+        ed_operator_destroy(op);
+        return e == cudaErrorMemoryAllocation ? ED_ERR_OOM : ED_ERR_CUDA;
+    }
+    *out = op;
+    return ED_OK;
+}
+
+void ed_operator_destroy(ed_operator *op)
+{
+    if (!op)
+        return;
+    cudaDeviceSynchronize();
+    cudaFree(op->d_terms);
+    cudaFree(op->d_mats);
+    cudaFree(op->d_matsf);
+    cudaFree(op->d_offmask);
+    delete op;
+}
+
+ed_status ed_matvec(const ed_operator *op, const ed_basis *b, const void *x, void *y, int nvec,
+                    ed_dtype dtype, void *stream)
+{
+    if (!op || !b)
+        return ED_ERR_INVALID_ARG;
+    if (nvec < 1 || nvec > 16)
+        return ED_ERR_INVALID_ARG;
+    if (dtype != ED_F64 && dtype != ED_F32 && dtype != ED_C128 && dtype != ED_C64)
+        return ED_ERR_INVALID_ARG;
+    const bool cplx_dtype = dtype == ED_C128 || dtype == ED_C64;
+    if (!cplx_dtype && !(b->real_chars && op->real))
+        return ED_ERR_INVALID_ARG;
+    if (b->dim && (!x || !y))
+        return ED_ERR_INVALID_ARG;
+    if (((uintptr_t)x | (uintptr_t)y) & 15)
+        return ED_ERR_INVALID_ARG;
+    if (x == y && b->dim)
+        return ED_ERR_INVALID_ARG;
+    ed_status st = edk::check_pair(op, b);
+    if (st != ED_OK)
+        return st;
+    if (!b->dim)
+        return ED_OK;
+    ED_CUDA_TRY(edk::launch_matvec(op_view(op), b->group_view(), b->index_view(), !b->trivial_chars,
+                                   x, y, nvec, dtype, (cudaStream_t)stream));
+    return ED_OK;
+}
+
+// Diagnostics hook (not part of the public header): kernel launches issued by
+// the library since it was loaded.
+unsigned long long edx_launch_count(void) { return edk::g_launches.load(); }
+
+// Host-only test hook (not part of the public header): the Benes masks the
+// library computes for one permutation, 2*log2w - 1 words.
+int edx_benes_masks(int log2w, int n, const int32_t *perm, uint64_t *masks_out)
+{
+    if (log2w < 1 || log2w > 6 || n < 1 || n > (1 << log2w) || !perm || !masks_out)
+        return -1;
+    auto m = benes_masks(log2w, n, perm);
+    std::copy(m.begin(), m.end(), masks_out);
+    return (int)m.size();
+}
+
+// Host-only test hook: validate a term list and a permutation group and run the
+// operator symmetry check without touching the GPU.  Returns 1 if the operator
+// commutes with the group (spin inversion included when nonzero), 0 if not,
+// -1 on invalid terms.
+int edx_terms_commute(int n_sites, int n_terms, const double *coeff, const int32_t *sites,
+                      const double *local, int n_perm, const int32_t *perms, int spin_inversion)
+{
+    if (n_sites < 1 || n_sites > 64 || n_terms < 1 || !coeff || !sites || !local || !perms)
+        return -1;
+    for (int t = 0; t < n_terms; ++t) {
+        const int i = sites[2 * t], j = sites[2 * t + 1];
+        if (i < 0 || j < 0 || i >= n_sites || j >= n_sites || i == j)
+            return -1;
+    }
+    ed_operator *op = build_operator_host(n_sites, n_terms, coeff, sites, local);
+    if (!op)
+        return -1;
+    const int r = operator_is_symmetric(op, n_perm, perms, spin_inversion) ? 1 : 0;
+    delete op;
+    return r;
+}
+
+// Host-only test hook: the group validation of ed_basis_build as a status.
+int edx_validate_group(int n_sites, int n_elems, const int32_t *perms, const double *chars)
+{
+    return (int)validate_group(n_sites, n_elems, perms, chars);
+}
+
+}  // extern "C"

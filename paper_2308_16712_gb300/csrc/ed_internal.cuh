@@ -1,0 +1,243 @@
+// ed_internal.cuh -- device-side building blocks shared by the basis and matvec
+// kernels: the word-level Benes network that applies a site permutation, the
+// representative search over the symmetry group, the "stateToIndex" search in
+// the sorted basis (Sec. "Matrix-vector product"), and the handle layouts.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <atomic>
+#include <vector>
+
+#include "../../include/ed.h"
+
+namespace edk {
+
+// ---------------------------------------------------------------------------
+// Benes networks on a machine word.  A permutation of the 2^L bit positions of
+// a word is realised by 2L-1 "delta swap" stages with shifts
+// 2^(L-1), ..., 2, 1, 2, ..., 2^(L-1); stage i exchanges bits p and p + d(i)
+// wherever bit p of its mask is set.  Masks are stored padded to 12 words per
+// permutation so that they can be fetched as 16-byte vectors.
+// ---------------------------------------------------------------------------
+constexpr int kMaskStride = 12;
+
+template <typename W> struct WordInfo;
+template <> struct WordInfo<uint32_t> { static constexpr int kLog = 5; static constexpr int kBits = 32; };
+template <> struct WordInfo<uint64_t> { static constexpr int kLog = 6; static constexpr int kBits = 64; };
+
+__host__ __device__ constexpr int benes_shift(int log2w, int stage)
+{
+    return stage < log2w ? (1 << (log2w - 1 - stage)) : (1 << (stage - log2w + 1));
+}
+
+template <typename W, typename M>
+__device__ __forceinline__ W delta_swap(W x, M mask, int d)
+{
+    const W m = (W)mask;
+    W t = ((x >> d) ^ x) & m;
+    return x ^ t ^ (t << d);
+}
+
+// Apply one permutation, masks in shared memory (16-byte aligned, 12 words).
+__device__ __forceinline__ uint32_t benes_apply(uint32_t x, const uint32_t *m)
+{
+    const uint4 a = *reinterpret_cast<const uint4 *>(m);
+    const uint4 b = *reinterpret_cast<const uint4 *>(m + 4);
+    const uint32_t c = m[8];
+    x = delta_swap(x, a.x, 16);
+    x = delta_swap(x, a.y, 8);
+    x = delta_swap(x, a.z, 4);
+    x = delta_swap(x, a.w, 2);
+    x = delta_swap(x, b.x, 1);
+    x = delta_swap(x, b.y, 2);
+    x = delta_swap(x, b.z, 4);
+    x = delta_swap(x, b.w, 8);
+    x = delta_swap(x, c, 16);
+    return x;
+}
+
+__device__ __forceinline__ uint64_t benes_apply(uint64_t x, const uint64_t *m)
+{
+    const ulonglong2 a = *reinterpret_cast<const ulonglong2 *>(m);
+    const ulonglong2 b = *reinterpret_cast<const ulonglong2 *>(m + 2);
+    const ulonglong2 c = *reinterpret_cast<const ulonglong2 *>(m + 4);
+    const ulonglong2 e = *reinterpret_cast<const ulonglong2 *>(m + 6);
+    const ulonglong2 f = *reinterpret_cast<const ulonglong2 *>(m + 8);
+    const uint64_t g = m[10];
+    x = delta_swap(x, a.x, 32);
+    x = delta_swap(x, a.y, 16);
+    x = delta_swap(x, b.x, 8);
+    x = delta_swap(x, b.y, 4);
+    x = delta_swap(x, c.x, 2);
+    x = delta_swap(x, c.y, 1);
+    x = delta_swap(x, e.x, 2);
+    x = delta_swap(x, e.y, 4);
+    x = delta_swap(x, f.x, 8);
+    x = delta_swap(x, f.y, 16);
+    x = delta_swap(x, g, 32);
+    return x;
+}
+
+// ---------------------------------------------------------------------------
+// Device views of the handles (plain structs passed by value to kernels).
+// ---------------------------------------------------------------------------
+struct GroupView {
+    int n_sites;
+    int n_perm;        // lattice elements (the permutations)
+    int flip;          // 1 if spin inversion doubles the group
+    int order;         // n_perm * (1 + flip); expanded index: p (plain), p + n_perm (flipped)
+    uint64_t full;     // low n_sites bits set
+    const uint32_t *masks32;  // n_perm x kMaskStride (used when n_sites <= 32)
+    const uint64_t *masks64;  // n_perm x kMaskStride
+    const double2 *chi;       // order entries, expanded
+    const float2 *chif;       // same, single precision
+    const uint32_t *chi_one;  // bitset over the expanded order: chi == 1
+};
+
+struct IndexView {
+    const uint64_t *states;  // ascending basis
+    const uint16_t *norms;   // orbit norms
+    uint64_t dim;
+    const uint32_t *tab;     // prefix offsets, tab_size + 1 entries
+    uint64_t tab_size;
+    int e_lo, e_hi;          // bit-length range covered by the table
+    int mbits;               // mantissa bits of the table key
+};
+
+// Monotone bucket key of a state: (bit length - e_lo, next mbits bits below the
+// leading one).  Ascending states give non-decreasing keys.
+__host__ __device__ __forceinline__ uint64_t prefix_key(uint64_t s, int e_lo, int mbits)
+{
+#ifdef __CUDA_ARCH__
+    const int bl = 64 - __clzll((long long)s);
+#else
+    const int bl = s ? 64 - __builtin_clzll(s) : 0;
+#endif
+    uint64_t mant = 0;
+    if (mbits > 0 && bl >= 2)
+        mant = (s << (65 - bl)) >> (64 - mbits);
+    return ((uint64_t)(bl - e_lo) << mbits) | mant;
+}
+
+// "stateToIndex": position of s in the ascending basis or -1.
+__device__ __forceinline__ int64_t find_index(uint64_t s, const IndexView &ix)
+{
+    const int bl = 64 - __clzll((long long)s);
+    if (bl < ix.e_lo || bl > ix.e_hi)
+        return -1;
+    const uint64_t t = prefix_key(s, ix.e_lo, ix.mbits);
+    uint64_t lo = __ldg(ix.tab + t);
+    uint64_t hi = __ldg(ix.tab + t + 1);
+    const uint64_t end = hi;
+    while (lo < hi) {
+        const uint64_t mid = (lo + hi) >> 1;
+        if (__ldg(ix.states + mid) < s)
+            lo = mid + 1;
+        else
+            hi = mid;
+    }
+    return (lo < end && __ldg(ix.states + lo) == s) ? (int64_t)lo : -1;
+}
+
+__device__ __forceinline__ bool chi_is_one(const uint32_t *bits, int g)
+{
+    return (bits[g >> 5] >> (g & 31)) & 1u;
+}
+
+// ---------------------------------------------------------------------------
+// Representative search: best = min over the expanded group of g.s, gbest =
+// the expanded index of the first minimiser in visiting order.  The loop over
+// the group is uniform across the warp (every lane applies the same element at
+// the same time), so mask reads from shared memory are broadcasts.
+// ---------------------------------------------------------------------------
+template <typename W, bool kTrack>
+__device__ __forceinline__ void rep_search(W s, const W *sm_masks, int n_perm, int flip, W full,
+                                           W &best, int &gbest)
+{
+    best = ~W(0);
+    gbest = 0;
+    if (flip) {
+        for (int p = 0; p < n_perm; ++p) {
+            const W q = benes_apply(s, sm_masks + p * kMaskStride);
+            const W f = q ^ full;
+            if (kTrack) {
+                if (q < best) { best = q; gbest = p; }
+                if (f < best) { best = f; gbest = p + n_perm; }
+            } else {
+                best = min(best, min(q, f));
+            }
+        }
+    } else {
+        for (int p = 0; p < n_perm; ++p) {
+            const W q = benes_apply(s, sm_masks + p * kMaskStride);
+            if (kTrack) {
+                if (q < best) { best = q; gbest = p; }
+            } else {
+                best = min(best, q);
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// small complex helpers
+// ---------------------------------------------------------------------------
+template <typename T> struct Cplx { T re, im; };
+
+template <typename T>
+__device__ __forceinline__ Cplx<T> cmul(Cplx<T> a, Cplx<T> b)
+{
+    return {a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re};
+}
+
+}  // namespace edk
+
+// ---------------------------------------------------------------------------
+// Handle layouts (host side).
+// ---------------------------------------------------------------------------
+struct ed_basis {
+    int device = 0;
+    int n_sites = 0, n_up = 0, spin_inversion = 0;
+    int n_perm = 0, order = 0;
+    bool trivial_chars = false;  // every expanded character equals 1
+    bool real_chars = false;     // every expanded character is real
+    std::vector<int32_t> perms;  // n_perm x n_sites
+    std::vector<double> chars;   // n_perm x 2
+    uint64_t dim = 0;
+    // device arrays
+    uint64_t *d_states = nullptr;
+    uint16_t *d_norms = nullptr;
+    uint32_t *d_tab = nullptr;
+    uint32_t *d_masks32 = nullptr;
+    uint64_t *d_masks64 = nullptr;
+    double2 *d_chi = nullptr;
+    float2 *d_chif = nullptr;
+    uint32_t *d_chi_one = nullptr;
+    uint64_t tab_size = 0;
+    int e_lo = 0, e_hi = 0, mbits = 0;
+
+    edk::GroupView group_view() const;
+    edk::IndexView index_view() const;
+};
+
+struct ed_operator {
+    int n_sites = 0, n_terms = 0, n_mats = 0;
+    std::vector<int32_t> sites;       // n_terms x 2
+    std::vector<int32_t> mat_of_term; // n_terms
+    std::vector<double> mats;         // n_mats x 16 x 2: coeff * h, deduplicated
+    int max_offdiag = 0;              // max off-diagonal entries one row can produce
+    bool real = true;                 // every matrix entry real
+    // host copies of the device tables
+    std::vector<uint32_t> h_terms;
+    std::vector<double2> h_mats;
+    std::vector<float2> h_matsf;
+    std::vector<uint8_t> h_offmask;
+    // device tables
+    uint32_t *d_terms = nullptr;      // n_terms: i | j << 8 | mat << 16
+    double2 *d_mats = nullptr;        // n_mats x 16
+    float2 *d_matsf = nullptr;
+    uint8_t *d_offmask = nullptr;     // n_mats x 4: bit c' set if h[c'][c] != 0, c' != c
+    mutable std::atomic<const ed_basis *> checked{nullptr};  // last basis verified symmetric
+};

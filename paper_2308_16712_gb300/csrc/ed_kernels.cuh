@@ -1,0 +1,59 @@
+// ed_kernels.cuh -- launch wrappers exported by the kernel translation units to
+// the host API (ed_api.cu).  All functions enqueue on `stream` and return the
+// CUDA error of the launch.
+#pragma once
+
+#include "ed_internal.cuh"
+
+namespace edk {
+
+// Kernel launches issued by the library since it was loaded (diagnostics).
+void count_launch(unsigned n = 1);
+
+// ---- basis build (Sec. "States enumeration") --------------------------------
+struct EnumPlan {
+    int n_sites;
+    int n_up;            // -1: all 2^n_sites states
+    uint64_t total;      // states to visit
+    uint64_t chunk;      // states per thread
+    uint64_t n_chunks;
+    const uint64_t *binom;  // device (65 x 65) binomial table
+};
+
+// Pass 1: per-chunk representative counts.
+cudaError_t launch_enum_count(const EnumPlan &plan, const GroupView &g, uint32_t *counts,
+                              cudaStream_t stream);
+// Pass 2: write representatives and norms at offsets[chunk].
+cudaError_t launch_enum_write(const EnumPlan &plan, const GroupView &g, const uint64_t *offsets,
+                              uint64_t *states, uint16_t *norms, cudaStream_t stream);
+// Exclusive scan of n uint32 counts into n + 1 uint64 offsets (offsets[n] = total).
+// `tmp` must hold scan_tmp_words(n) uint64 words.
+size_t scan_tmp_words(uint64_t n);
+cudaError_t launch_scan(const uint32_t *counts, uint64_t n, uint64_t *offsets, uint64_t *tmp,
+                        cudaStream_t stream);
+// Prefix table over the ascending basis.
+cudaError_t launch_prefix_table(const IndexView &ix, uint32_t *tab, cudaStream_t stream);
+// Sets *flag to 1 if the basis is not strictly ascending.
+cudaError_t launch_check_sorted(const uint64_t *states, uint64_t dim, int *flag, cudaStream_t stream);
+
+// ---- state -> index -----------------------------------------------------------
+cudaError_t launch_index(const IndexView &ix, const uint64_t *query, int64_t *out, uint64_t n,
+                         cudaStream_t stream);
+
+// ---- matvec (Sec. "Matrix-vector product") --------------------------------------
+struct OpView {
+    int n_terms;
+    int n_mats;
+    const uint32_t *terms;   // i | j << 8 | mat << 16
+    const double2 *mats;     // n_mats x 16
+    const float2 *matsf;
+    const uint8_t *offmask;  // n_mats x 4
+};
+
+// Operator/basis compatibility check (n_sites, symmetry); cached per basis.
+ed_status check_pair(const ed_operator *op, const ed_basis *b);
+
+cudaError_t launch_matvec(const OpView &op, const GroupView &g, const IndexView &ix, bool track,
+                          const void *x, void *y, int nvec, ed_dtype dtype, cudaStream_t stream);
+
+}  // namespace edk

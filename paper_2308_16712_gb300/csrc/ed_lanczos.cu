@@ -1,0 +1,623 @@
+// ed_lanczos.cu -- the Krylov eigensolver that consumes the matvec (the paper's
+// Background: Lanczos needs hundreds of matrix-vector products).
+//
+// Recurrence (fp64 on the GPU):  v_0 = x0 / |x0|,
+//   w = H v_j,  alpha_j = Re <v_j, w>,  w -= alpha_j v_j + beta_j v_{j-1},
+//   beta_{j+1} = |w|,  v_{j+1} = w / beta_{j+1}.
+// Dot products and norms are compensated (Neumaier) sums over a fixed
+// partition, so a second pass reproduces alpha/beta bit for bit.  The lowest
+// eigenpair of the tridiagonal matrix comes from Sturm-count bisection and
+// inverse iteration in a single-thread kernel.  With ED_LANCZOS_F32_MATVEC the
+// matvec runs in fp32 (its input is the fp32 copy of v_j written by the
+// normalisation kernel) and the Ritz vector is refined by a few fp64 Lanczos
+// steps started from it.  The returned energy is the fp64 Rayleigh quotient of
+// the final vector, with its fp64 residual.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "ed_kernels.cuh"
+
+namespace edk {
+namespace {
+
+constexpr int kRedThreads = 256;
+constexpr int kRefineSteps = 6;
+
+// ---- compensated sums ------------------------------------------------------
+struct KSum {
+    double s, c;
+};
+
+__device__ __forceinline__ void ksum_add(KSum &k, double x)
+{
+    const double t = k.s + x;
+    if (fabs(k.s) >= fabs(x))
+        k.c += (k.s - t) + x;
+    else
+        k.c += (x - t) + k.s;
+    k.s = t;
+}
+
+__device__ __forceinline__ KSum ksum_merge(KSum a, KSum b)
+{
+    KSum r{a.s, a.c + b.c};
+    ksum_add(r, b.s);
+    return r;
+}
+
+// Block-wide merge of (s, c) pairs in a fixed tree order; result in thread 0.
+__device__ KSum block_ksum(KSum k)
+{
+    __shared__ double sm_s[kRedThreads / 32], sm_c[kRedThreads / 32];
+    for (int o = 16; o > 0; o >>= 1) {
+        KSum other{__shfl_down_sync(0xffffffffu, k.s, o), __shfl_down_sync(0xffffffffu, k.c, o)};
+        k = ksum_merge(k, other);
+    }
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) {
+        sm_s[wid] = k.s;
+        sm_c[wid] = k.c;
+    }
+    __syncthreads();
+    if (wid == 0) {
+        k = lane < kRedThreads / 32 ? KSum{sm_s[lane], sm_c[lane]} : KSum{0.0, 0.0};
+        for (int o = 16; o > 0; o >>= 1) {
+            KSum other{__shfl_down_sync(0xffffffffu, k.s, o), __shfl_down_sync(0xffffffffu, k.c, o)};
+            k = ksum_merge(k, other);
+        }
+    }
+    __syncthreads();
+    return k;
+}
+
+// Sum of the per-block partials (fixed order), every block computes the same value.
+__device__ double reduce_partials(const double2 *part, int nparts)
+{
+    KSum k{0.0, 0.0};
+    for (int i = threadIdx.x; i < nparts; i += blockDim.x)
+        k = ksum_merge(k, KSum{part[i].x, part[i].y});
+    k = block_ksum(k);
+    __shared__ double total;
+    if (threadIdx.x == 0)
+        total = k.s + k.c;
+    __syncthreads();
+    return total;
+}
+
+// ---- vector element access (real or complex, fp64 or fp32) -------------------
+template <bool kC> struct Vec;
+template <> struct Vec<false> {
+    using D = double;
+    using F = float;
+    __device__ static double dot(double a, double b) { return a * b; }
+    __device__ static double dotf(double a, float b) { return a * (double)b; }
+    __device__ static double norm2(double a) { return a * a; }
+    __device__ static double up(float a) { return (double)a; }
+    __device__ static float down(double a) { return (float)a; }
+    __device__ static double axpby(double w, double a, double v, double b, double p) { return w - a * v - b * p; }
+    __device__ static double scale(double w, double s) { return w * s; }
+    __device__ static double zero() { return 0.0; }
+    __device__ static double fma_acc(double acc, double y, double v) { return acc + y * v; }
+};
+template <> struct Vec<true> {
+    using D = double2;
+    using F = float2;
+    __device__ static double dot(double2 a, double2 b) { return a.x * b.x + a.y * b.y; }
+    __device__ static double dotf(double2 a, float2 b) { return a.x * (double)b.x + a.y * (double)b.y; }
+    __device__ static double norm2(double2 a) { return a.x * a.x + a.y * a.y; }
+    __device__ static double2 up(float2 a) { return make_double2(a.x, a.y); }
+    __device__ static float2 down(double2 a) { return make_float2((float)a.x, (float)a.y); }
+    __device__ static double2 axpby(double2 w, double a, double2 v, double b, double2 p)
+    {
+        return make_double2(w.x - a * v.x - b * p.x, w.y - a * v.y - b * p.y);
+    }
+    __device__ static double2 scale(double2 w, double s) { return make_double2(w.x * s, w.y * s); }
+    __device__ static double2 zero() { return make_double2(0.0, 0.0); }
+    __device__ static double2 fma_acc(double2 acc, double y, double2 v)
+    {
+        return make_double2(acc.x + y * v.x, acc.y + y * v.y);
+    }
+};
+
+// partial[b] = compensated sum over this block's slice of Re<a_i, b_i> (or |a_i|^2)
+template <bool kC, bool kF32>
+__global__ void __launch_bounds__(kRedThreads) k_dot_part(const typename Vec<kC>::D *a, const void *bv,
+                                                           uint64_t n, double2 *part)
+{
+    using VT = Vec<kC>;
+    KSum k{0.0, 0.0};
+    const uint64_t per = (n + gridDim.x - 1) / gridDim.x;
+    const uint64_t lo = min(n, blockIdx.x * per), hi = min(n, lo + per);
+    for (uint64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+        if constexpr (kF32)
+            ksum_add(k, VT::dotf(a[i], reinterpret_cast<const typename VT::F *>(bv)[i]));
+        else
+            ksum_add(k, VT::dot(a[i], reinterpret_cast<const typename VT::D *>(bv)[i]));
+    }
+    k = block_ksum(k);
+    if (threadIdx.x == 0)
+        part[blockIdx.x] = make_double2(k.s, k.c);
+}
+
+template <bool kC>
+__global__ void __launch_bounds__(kRedThreads) k_norm_part(const typename Vec<kC>::D *a, uint64_t n, double2 *part)
+{
+    using VT = Vec<kC>;
+    KSum k{0.0, 0.0};
+    const uint64_t per = (n + gridDim.x - 1) / gridDim.x;
+    const uint64_t lo = min(n, blockIdx.x * per), hi = min(n, lo + per);
+    for (uint64_t i = lo + threadIdx.x; i < hi; i += blockDim.x)
+        ksum_add(k, VT::norm2(a[i]));
+    k = block_ksum(k);
+    if (threadIdx.x == 0)
+        part[blockIdx.x] = make_double2(k.s, k.c);
+}
+
+// alpha_j from the dot partials; w = w_in - alpha v - beta_j vp; norm partials of w
+template <bool kC, bool kF32>
+__global__ void __launch_bounds__(kRedThreads) k_update(const void *w_in, typename Vec<kC>::D *w,
+                                                         const typename Vec<kC>::D *v,
+                                                         const typename Vec<kC>::D *vp, uint64_t n,
+                                                         const double2 *dot_part, int nparts,
+                                                         double *alpha, const double *beta_j,
+                                                         double2 *norm_part)
+{
+    using VT = Vec<kC>;
+    const double a = reduce_partials(dot_part, nparts);
+    if (blockIdx.x == 0 && threadIdx.x == 0)
+        *alpha = a;
+    const double b = vp ? *beta_j : 0.0;
+    KSum k{0.0, 0.0};
+    const uint64_t per = (n + gridDim.x - 1) / gridDim.x;
+    const uint64_t lo = min(n, blockIdx.x * per), hi = min(n, lo + per);
+    for (uint64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+        typename VT::D wi;
+        if constexpr (kF32)
+            wi = VT::up(reinterpret_cast<const typename VT::F *>(w_in)[i]);
+        else
+            wi = reinterpret_cast<const typename VT::D *>(w_in)[i];
+        const typename VT::D r = VT::axpby(wi, a, v[i], b, vp ? vp[i] : VT::zero());
+        w[i] = r;
+        ksum_add(k, VT::norm2(r));
+    }
+    k = block_ksum(k);
+    if (threadIdx.x == 0)
+        norm_part[blockIdx.x] = make_double2(k.s, k.c);
+}
+
+// beta = sqrt(sum of partials); v_out = w / beta (zero on breakdown); fp32 copy
+template <bool kC>
+__global__ void __launch_bounds__(kRedThreads) k_normalize(const typename Vec<kC>::D *w,
+                                                            typename Vec<kC>::D *v_out,
+                                                            typename Vec<kC>::F *x32, uint64_t n,
+                                                            const double2 *norm_part, int nparts,
+                                                            double *beta_out)
+{
+    using VT = Vec<kC>;
+    const double b = sqrt(fmax(reduce_partials(norm_part, nparts), 0.0));
+    if (blockIdx.x == 0 && threadIdx.x == 0)
+        *beta_out = b;
+    const double s = b > 0.0 ? 1.0 / b : 0.0;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (uint64_t)gridDim.x * blockDim.x) {
+        const typename VT::D r = VT::scale(w[i], s);
+        v_out[i] = r;
+        if (x32)
+            x32[i] = VT::down(r);
+    }
+}
+
+// acc += y[j] * v   (Ritz vector accumulation, second pass)
+template <bool kC>
+__global__ void k_axpy_coef(typename Vec<kC>::D *acc, const typename Vec<kC>::D *v, const double *y, int j,
+                            uint64_t n, int first)
+{
+    using VT = Vec<kC>;
+    const double c = y[j];
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (uint64_t)gridDim.x * blockDim.x)
+        acc[i] = VT::fma_acc(first ? VT::zero() : acc[i], c, v[i]);
+}
+
+// psi[i] = sum_j y[j] V[j][i] over stored Krylov vectors
+template <bool kC>
+__global__ void k_combine(typename Vec<kC>::D *psi, const typename Vec<kC>::D *V, const double *y,
+                          const int *m_eff, uint64_t n)
+{
+    using VT = Vec<kC>;
+    const int m = *m_eff;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (uint64_t)gridDim.x * blockDim.x) {
+        typename VT::D acc = VT::zero();
+        for (int j = 0; j < m; ++j)
+            acc = VT::fma_acc(acc, y[j], V[(uint64_t)j * n + i]);
+        psi[i] = acc;
+    }
+}
+
+// x_out = x_in / sqrt(sum of partials)
+template <bool kC>
+__global__ void k_scale_by_norm(const typename Vec<kC>::D *in, typename Vec<kC>::D *out,
+                                typename Vec<kC>::F *x32, uint64_t n, const double2 *part, int nparts)
+{
+    using VT = Vec<kC>;
+    const double nrm = sqrt(fmax(reduce_partials(part, nparts), 0.0));
+    const double s = nrm > 0.0 ? 1.0 / nrm : 0.0;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (uint64_t)gridDim.x * blockDim.x) {
+        const typename VT::D r = VT::scale(in[i], s);
+        out[i] = r;
+        if (x32)
+            x32[i] = VT::down(r);
+    }
+}
+
+// r = a - theta b with theta = <b,a>/<b,b> (from partials); partials of |r|^2
+template <bool kC>
+__global__ void __launch_bounds__(kRedThreads) k_residual(const typename Vec<kC>::D *hu,
+                                                           const typename Vec<kC>::D *u, uint64_t n,
+                                                           const double2 *num_part,
+                                                           const double2 *den_part, int nparts,
+                                                           double *theta_out, double2 *res_part)
+{
+    using VT = Vec<kC>;
+    const double num = reduce_partials(num_part, nparts);
+    const double den = reduce_partials(den_part, nparts);
+    const double th = num / den;
+    if (blockIdx.x == 0 && threadIdx.x == 0)
+        *theta_out = th;
+    KSum k{0.0, 0.0};
+    const uint64_t per = (n + gridDim.x - 1) / gridDim.x;
+    const uint64_t lo = min(n, blockIdx.x * per), hi = min(n, lo + per);
+    for (uint64_t i = lo + threadIdx.x; i < hi; i += blockDim.x)
+        ksum_add(k, VT::norm2(VT::axpby(hu[i], th, u[i], 0.0, VT::zero())));
+    k = block_ksum(k);
+    if (threadIdx.x == 0)
+        res_part[blockIdx.x] = make_double2(k.s, k.c);
+}
+
+__global__ void k_finish_residual(const double2 *res_part, const double2 *den_part, int nparts,
+                                  double *out)
+{
+    const double r = reduce_partials(res_part, nparts);
+    const double d = reduce_partials(den_part, nparts);
+    if (threadIdx.x == 0)
+        *out = sqrt(fmax(r, 0.0) / d);
+}
+
+// ---- tridiagonal eigensolver (one thread) ------------------------------------
+// Number of eigenvalues of T (diag a, offdiag b) below x (Sturm sequence).
+__device__ int sturm_count(const double *a, const double *b, int m, double x)
+{
+    int cnt = 0;
+    double d = 1.0;
+    for (int i = 0; i < m; ++i) {
+        const double bb = i ? b[i] * b[i] : 0.0;
+        d = (a[i] - x) - (i ? bb / d : 0.0);
+        if (d == 0.0)
+            d = -1e-300;
+        if (d < 0.0)
+            ++cnt;
+    }
+    return cnt;
+}
+
+// Lowest eigenvalue and eigenvector of the leading m_eff x m_eff block, where
+// m_eff stops at the first beta that vanishes (invariant subspace).
+// a[0..m), beta[0..m]: beta[j] couples v_{j-1} and v_j (beta[0] unused).
+__global__ void k_tridiag_lowest(const double *alpha, const double *beta, int m, double *y,
+                                 double *lambda_out, int *m_eff_out, double *work)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0)
+        return;
+    int me = m;
+    double scale = 0.0;
+    for (int i = 0; i < m; ++i)
+        scale = fmax(scale, fabs(alpha[i]) + fabs(beta[i + 1]));
+    for (int i = 1; i < m; ++i)
+        if (!(beta[i] > 1e-13 * fmax(scale, 1e-300))) {
+            me = i;
+            break;
+        }
+    // Gershgorin interval
+    double lo = 1e300, hi = -1e300;
+    for (int i = 0; i < me; ++i) {
+        const double r = (i ? fabs(beta[i]) : 0.0) + (i + 1 < me ? fabs(beta[i + 1]) : 0.0);
+        lo = fmin(lo, alpha[i] - r);
+        hi = fmax(hi, alpha[i] + r);
+    }
+    for (int it = 0; it < 200 && hi - lo > 0.0; ++it) {
+        const double mid = 0.5 * (lo + hi);
+        if (mid <= lo || mid >= hi)
+            break;
+        if (sturm_count(alpha, beta, me, mid) >= 1)
+            hi = mid;
+        else
+            lo = mid;
+    }
+    const double lam = 0.5 * (lo + hi);
+    // inverse iteration: (T - lam I) z = y, LU without pivoting with guarded pivots
+    double *dd = work;  // pivots
+    const double eps = 1e-15 * fmax(scale, 1e-300);
+    for (int i = 0; i < me; ++i)
+        y[i] = 1.0;
+    for (int iter = 0; iter < 4; ++iter) {
+        // forward elimination
+        double piv = alpha[0] - lam;
+        if (fabs(piv) < eps)
+            piv = eps;
+        dd[0] = piv;
+        for (int i = 1; i < me; ++i) {
+            const double l = beta[i] / dd[i - 1];
+            piv = (alpha[i] - lam) - l * beta[i];
+            if (fabs(piv) < eps)
+                piv = eps;
+            dd[i] = piv;
+            y[i] -= l * y[i - 1];
+        }
+        y[me - 1] /= dd[me - 1];
+        for (int i = me - 2; i >= 0; --i)
+            y[i] = (y[i] - beta[i + 1] * y[i + 1]) / dd[i];
+        double nrm = 0.0;
+        for (int i = 0; i < me; ++i)
+            nrm += y[i] * y[i];
+        nrm = sqrt(nrm);
+        for (int i = 0; i < me; ++i)
+            y[i] /= nrm;
+    }
+    for (int i = me; i < m; ++i)
+        y[i] = 0.0;
+    *lambda_out = lam;
+    *m_eff_out = me;
+}
+
+template <typename T>
+cudaError_t dalloc(T **p, size_t count)
+{
+    return cudaMalloc((void **)p, std::max<size_t>(count, 1) * sizeof(T));
+}
+
+// CUDA event pairs around every matvec launch; summed after the final sync.
+struct MatvecTimer {
+    std::vector<cudaEvent_t> ev;
+    ~MatvecTimer()
+    {
+        for (cudaEvent_t e : ev)
+            cudaEventDestroy(e);
+    }
+    cudaError_t mark(cudaStream_t st)
+    {
+        cudaEvent_t e;
+        cudaError_t r = cudaEventCreate(&e);
+        if (r != cudaSuccess)
+            return r;
+        ev.push_back(e);
+        return cudaEventRecord(e, st);
+    }
+    double total_ms() const
+    {
+        double t = 0.0;
+        for (size_t i = 0; i + 1 < ev.size(); i += 2) {
+            float ms = 0.f;
+            if (cudaEventElapsedTime(&ms, ev[i], ev[i + 1]) == cudaSuccess)
+                t += ms;
+        }
+        return t;
+    }
+};
+
+struct Scratch {
+    std::vector<void *> ptrs;
+    ~Scratch()
+    {
+        for (void *p : ptrs)
+            cudaFree(p);
+    }
+    template <typename T>
+    cudaError_t get(T **p, size_t count)
+    {
+        cudaError_t e = dalloc(p, count);
+        if (e == cudaSuccess)
+            ptrs.push_back((void *)*p);
+        return e;
+    }
+};
+
+#define ED_L_TRY(expr)                                                      \
+    do {                                                                    \
+        cudaError_t _e = (expr);                                            \
+        if (_e != cudaSuccess) {                                            \
+            (void)cudaGetLastError();                                       \
+            return _e == cudaErrorMemoryAllocation ? ED_ERR_OOM : ED_ERR_CUDA; \
+        }                                                                   \
+    } while (0)
+
+template <bool kC>
+ed_status run_lanczos(const ed_operator *op, const ed_basis *b, const void *x0, int steps,
+                      ed_lanczos_mode mode, bool recompute, double *e0_out, void *vec_out,
+                      ed_lanczos_info *info, cudaStream_t st)
+{
+    using D = typename Vec<kC>::D;
+    using F = typename Vec<kC>::F;
+    const uint64_t n = b->dim;
+    const bool f32 = mode == ED_LANCZOS_F32_MATVEC;
+    const ed_dtype dt64 = kC ? ED_C128 : ED_F64, dt32 = kC ? ED_C64 : ED_F32;
+    const OpView ov{op->n_terms, op->n_mats, op->d_terms, op->d_mats, op->d_matsf, op->d_offmask};
+    const GroupView gv = b->group_view();
+    const IndexView iv = b->index_view();
+    const bool track = !b->trivial_chars;
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int nparts = std::max(1, std::min<int>(sms * 4, (int)((n + kRedThreads - 1) / kRedThreads)));
+    const int vgrid = std::max(1, std::min<int>(sms * 8, (int)((n + kRedThreads - 1) / kRedThreads)));
+
+    // store the Krylov basis if it fits in half of the free memory
+    size_t free_b = 0, total_b = 0;
+    cudaMemGetInfo(&free_b, &total_b);
+    const size_t vec_bytes = n * sizeof(D);
+    const bool store = !recompute && (double)(steps + 1) * vec_bytes < 0.5 * (double)free_b;
+
+    Scratch S;
+    D *V = nullptr, *w = nullptr, *ring[2] = {nullptr, nullptr}, *psi = nullptr;
+    F *x32 = nullptr, *w32 = nullptr;
+    double *alpha = nullptr, *beta = nullptr, *y = nullptr, *work = nullptr, *scal = nullptr;
+    int *m_eff = nullptr;
+    double2 *part_a = nullptr, *part_b = nullptr, *part_c = nullptr;
+    if (store)
+        ED_L_TRY(S.get(&V, (size_t)(steps + 1) * n));
+    else {
+        ED_L_TRY(S.get(&ring[0], n));
+        ED_L_TRY(S.get(&ring[1], n));
+    }
+    ED_L_TRY(S.get(&w, n));
+    ED_L_TRY(S.get(&psi, n));
+    if (f32) {
+        ED_L_TRY(S.get(&x32, n));
+        ED_L_TRY(S.get(&w32, n));
+    }
+    const int mref = kRefineSteps;
+    const int mmax = std::max(steps, mref);
+    ED_L_TRY(S.get(&alpha, mmax + 1));
+    ED_L_TRY(S.get(&beta, mmax + 2));
+    ED_L_TRY(S.get(&y, mmax + 1));
+    ED_L_TRY(S.get(&work, 2 * (mmax + 1)));
+    ED_L_TRY(S.get(&scal, 8));
+    ED_L_TRY(S.get(&m_eff, 1));
+    ED_L_TRY(S.get(&part_a, nparts));
+    ED_L_TRY(S.get(&part_b, nparts));
+    ED_L_TRY(S.get(&part_c, nparts));
+    ED_L_TRY(cudaMemsetAsync(beta, 0, (mmax + 2) * sizeof(double), st));
+
+    int matvecs = 0;
+    MatvecTimer timer;
+    auto timed_matvec = [&](const void *in, void *out, ed_dtype dt) -> cudaError_t {
+        ++matvecs;
+        cudaError_t e = timer.mark(st);
+        if (e == cudaSuccess)
+            e = launch_matvec(ov, gv, iv, track, in, out, 1, dt, st);
+        if (e == cudaSuccess)
+            e = timer.mark(st);
+        return e;
+    };
+    auto H64 = [&](const D *in, D *out) -> cudaError_t { return timed_matvec(in, out, dt64); };
+
+    // One Lanczos run of m steps from `start` (unnormalised), fp64 or fp32 matvec.
+    // If Vs != nullptr, v_j is stored at Vs + j n; otherwise the ring buffers
+    // are used and, if acc_y != nullptr, psi += acc_y[j] v_j is accumulated.
+    auto run = [&](const D *start, int m, bool use_f32, D *Vs, const double *acc_y) -> cudaError_t {
+        cudaError_t e;
+        D *v0 = Vs ? Vs : ring[0];
+        k_norm_part<kC><<<nparts, kRedThreads, 0, st>>>(start, n, part_a); count_launch();
+        k_scale_by_norm<kC><<<vgrid, kRedThreads, 0, st>>>(start, v0, use_f32 ? x32 : nullptr, n, part_a, nparts); count_launch();
+        D *vp = nullptr, *v = v0;
+        for (int j = 0; j < m; ++j) {
+            if (acc_y) {
+                k_axpy_coef<kC><<<vgrid, kRedThreads, 0, st>>>(psi, v, acc_y, j, n, j == 0); count_launch();
+            }
+            if (use_f32) {
+                e = timed_matvec(x32, w32, dt32);
+                if (e != cudaSuccess)
+                    return e;
+                k_dot_part<kC, true><<<nparts, kRedThreads, 0, st>>>(v, w32, n, part_a); count_launch();
+                k_update<kC, true><<<nparts, kRedThreads, 0, st>>>(w32, w, v, vp, n, part_a, nparts,
+                                                                    alpha + j, beta + j, part_b); count_launch();
+            } else {
+                if ((e = H64(v, w)) != cudaSuccess)
+                    return e;
+                k_dot_part<kC, false><<<nparts, kRedThreads, 0, st>>>(v, w, n, part_a); count_launch();
+                k_update<kC, false><<<nparts, kRedThreads, 0, st>>>(w, w, v, vp, n, part_a, nparts,
+                                                                     alpha + j, beta + j, part_b); count_launch();
+            }
+            D *vn = Vs ? Vs + (uint64_t)(j + 1) * n : (vp ? vp : ring[1]);
+            k_normalize<kC><<<vgrid, kRedThreads, 0, st>>>(w, vn, use_f32 ? x32 : nullptr, n, part_b,
+                                                           nparts, beta + j + 1); count_launch();
+            vp = v;
+            v = vn;
+        }
+        return cudaGetLastError();
+    };
+
+    // main pass
+    ED_L_TRY(run((const D *)x0, steps, f32, store ? V : nullptr, nullptr));
+    ED_L_TRY(cudaMemsetAsync(y, 0, (mmax + 1) * sizeof(double), st));
+    k_tridiag_lowest<<<1, 1, 0, st>>>(alpha, beta, steps, y, scal + 0, m_eff, work); count_launch();
+    if (store) {
+        k_combine<kC><<<vgrid, kRedThreads, 0, st>>>(psi, V, y, m_eff, n); count_launch();
+    } else {
+        ED_L_TRY(run((const D *)x0, steps, f32, nullptr, y));  // bit-identical second pass
+    }
+    ED_L_TRY(cudaGetLastError());
+    double ritz = 0.0;
+    int me = 0;
+    ED_L_TRY(cudaMemcpyAsync(&ritz, scal + 0, sizeof(double), cudaMemcpyDeviceToHost, st));
+    ED_L_TRY(cudaMemcpyAsync(&me, m_eff, sizeof(int), cudaMemcpyDeviceToHost, st));
+
+    // fp64 refinement from the fp32-matvec Ritz vector: a short fp64 Lanczos run
+    D *u = psi;
+    if (f32) {
+        D *Vr = nullptr;
+        ED_L_TRY(S.get(&Vr, (size_t)(mref + 1) * n));
+        ED_L_TRY(cudaMemsetAsync(beta, 0, (mmax + 2) * sizeof(double), st));
+        ED_L_TRY(run(psi, mref, false, Vr, nullptr));
+        ED_L_TRY(cudaMemsetAsync(y, 0, (mmax + 1) * sizeof(double), st));
+        k_tridiag_lowest<<<1, 1, 0, st>>>(alpha, beta, mref, y, scal + 1, m_eff, work); count_launch();
+        k_combine<kC><<<vgrid, kRedThreads, 0, st>>>(psi, Vr, y, m_eff, n); count_launch();
+        ED_L_TRY(cudaGetLastError());
+    }
+    // fp64 Rayleigh quotient and residual of the final vector u
+    ED_L_TRY(H64(u, w));
+    k_dot_part<kC, false><<<nparts, kRedThreads, 0, st>>>(u, w, n, part_a); count_launch();
+    k_norm_part<kC><<<nparts, kRedThreads, 0, st>>>(u, n, part_b); count_launch();
+    k_residual<kC><<<nparts, kRedThreads, 0, st>>>(w, u, n, part_a, part_b, nparts, scal + 2, part_c); count_launch();
+    k_finish_residual<<<1, kRedThreads, 0, st>>>(part_c, part_b, nparts, scal + 3); count_launch();
+    if (vec_out)
+        k_scale_by_norm<kC><<<vgrid, kRedThreads, 0, st>>>(u, (D *)vec_out, nullptr, n, part_b, nparts); count_launch();
+    ED_L_TRY(cudaGetLastError());
+    double res[2] = {0.0, 0.0};
+    ED_L_TRY(cudaMemcpyAsync(res, scal + 2, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
+    ED_L_TRY(cudaStreamSynchronize(st));
+    if (e0_out)
+        *e0_out = res[0];
+    if (info) {
+        info->steps = me;
+        info->matvecs = matvecs;
+        info->ritz = ritz;
+        info->e0 = res[0];
+        info->residual = res[1];
+        info->matvec_ms = timer.total_ms();
+    }
+    return ED_OK;
+}
+
+}  // namespace
+}  // namespace edk
+
+extern "C" ed_status ed_lanczos(const ed_operator *op, const ed_basis *b, const void *x0, int steps,
+                                int mode_flags, double *e0_out, void *vec_out,
+                                ed_lanczos_info *info, void *stream)
+{
+    if (!op || !b || steps < 1 || steps > 10000)
+        return ED_ERR_INVALID_ARG;
+    const int base = mode_flags & ~ED_LANCZOS_RECOMPUTE;
+    if (base != ED_LANCZOS_F64 && base != ED_LANCZOS_F32_MATVEC)
+        return ED_ERR_INVALID_ARG;
+    const ed_lanczos_mode mode = (ed_lanczos_mode)base;
+    const bool recompute = (mode_flags & ED_LANCZOS_RECOMPUTE) != 0;
+    if (b->dim == 0 || !x0)
+        return ED_ERR_INVALID_ARG;
+    if (((uintptr_t)x0 | (uintptr_t)vec_out) & 15)
+        return ED_ERR_INVALID_ARG;
+    const ed_status st = edk::check_pair(op, b);
+    if (st != ED_OK)
+        return st;
+    const bool cplx = !(b->real_chars && op->real);
+    if (cplx)
+        return edk::run_lanczos<true>(op, b, x0, steps, mode, recompute, e0_out, vec_out, info,
+                                      (cudaStream_t)stream);
+    return edk::run_lanczos<false>(op, b, x0, steps, mode, recompute, e0_out, vec_out, info,
+                                   (cudaStream_t)stream);
+}

@@ -1,0 +1,275 @@
+// ed_matvec_impl.cuh -- the pull-style symmetry-adapted matvec kernel
+// (Sec. "Matrix-vector product": y_i = sum_j H_ij x_j with getRow and
+// stateToIndex), instantiated per precision in the ed_matvec_*.cu units.
+//
+// Work decomposition.  The grid is persistent; every warp owns a contiguous
+// block of rows and hands rows to its lanes on demand (ballot + popc), so a
+// lane that finishes a row takes the next one without waiting for the others.
+// A lane owns its row r: it loads r and n(r), forms the diagonal term, and then
+// walks the off-diagonal terms of H|r> one at a time.  All 32 lanes run the
+// representative search of their current term in lockstep over the same group
+// element (the mask reads are shared-memory broadcasts), then each lane looks
+// the representative up in the sorted basis, gathers x at that index and
+// accumulates in registers, in a fixed order: the result is deterministic and
+// needs no atomics.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <algorithm>
+
+#include "ed_kernels.cuh"
+
+namespace edk {
+
+constexpr int kMvThreads = 256;
+
+struct MatvecArgs {
+    OpView op;
+    GroupView g;
+    IndexView ix;
+    const void *x;
+    void *y;
+    int nvec;
+};
+
+template <typename T, bool kC> struct ValT { using type = T; };
+template <typename T> struct ValT<T, true> { using type = Cplx<T>; };
+
+template <typename T> __device__ __forceinline__ Cplx<T> conjc(Cplx<T> a) { return {a.re, -a.im}; }
+
+template <typename T> __device__ __forceinline__ Cplx<T> load_c(const double2 *p);
+template <> __device__ __forceinline__ Cplx<double> load_c<double>(const double2 *p) { return {p->x, p->y}; }
+template <typename T> __device__ __forceinline__ Cplx<T> load_cf(const float2 *p);
+template <> __device__ __forceinline__ Cplx<float> load_cf<float>(const float2 *p) { return {p->x, p->y}; }
+
+__host__ __device__ inline size_t align16(size_t v) { return (v + 15) & ~size_t(15); }
+
+template <typename W, typename T, bool kTrack>
+__host__ __device__ inline void matvec_smem_layout(const GroupView &g, const OpView &op, size_t off[5])
+{
+    off[0] = 0;                                                            // masks
+    off[1] = align16(off[0] + (size_t)g.n_perm * kMaskStride * sizeof(W)); // chi
+    off[2] = align16(off[1] + (kTrack ? (size_t)g.order * sizeof(Cplx<T>) : 0)); // terms
+    off[3] = align16(off[2] + (size_t)op.n_terms * sizeof(uint32_t));     // mats
+    off[4] = align16(off[3] + (size_t)op.n_mats * 16 * sizeof(Cplx<T>));  // offmask
+}
+
+template <typename W, typename T, bool kTrack>
+__host__ __device__ inline size_t matvec_smem_bytes(const GroupView &g, const OpView &op)
+{
+    size_t off[5];
+    matvec_smem_layout<W, T, kTrack>(g, op, off);
+    return align16(off[4] + (size_t)op.n_mats * 4);
+}
+
+template <typename W, typename T, bool kC, bool kTrack, int NV>
+__global__ void __launch_bounds__(kMvThreads) k_matvec(const MatvecArgs a)
+{
+    using V = typename ValT<T, kC>::type;
+    extern __shared__ __align__(16) unsigned char smem[];
+    size_t off[5];
+    matvec_smem_layout<W, T, kTrack>(a.g, a.op, off);
+    W *sm_masks = reinterpret_cast<W *>(smem + off[0]);
+    Cplx<T> *sm_chi = reinterpret_cast<Cplx<T> *>(smem + off[1]);
+    uint32_t *sm_terms = reinterpret_cast<uint32_t *>(smem + off[2]);
+    Cplx<T> *sm_mats = reinterpret_cast<Cplx<T> *>(smem + off[3]);
+    uint8_t *sm_off = smem + off[4];
+
+    {
+        const W *gm = sizeof(W) == 4 ? reinterpret_cast<const W *>(a.g.masks32)
+                                     : reinterpret_cast<const W *>(a.g.masks64);
+        for (int e = threadIdx.x; e < a.g.n_perm * kMaskStride; e += blockDim.x)
+            sm_masks[e] = gm[e];
+        if (kTrack) {
+            for (int e = threadIdx.x; e < a.g.order; e += blockDim.x) {
+                if constexpr (sizeof(T) == 8)
+                    sm_chi[e] = load_c<T>(a.g.chi + e);
+                else
+                    sm_chi[e] = load_cf<T>(a.g.chif + e);
+            }
+        }
+        for (int e = threadIdx.x; e < a.op.n_terms; e += blockDim.x)
+            sm_terms[e] = a.op.terms[e];
+        for (int e = threadIdx.x; e < a.op.n_mats * 16; e += blockDim.x) {
+            if constexpr (sizeof(T) == 8)
+                sm_mats[e] = load_c<T>(a.op.mats + e);
+            else
+                sm_mats[e] = load_cf<T>(a.op.matsf + e);
+        }
+        for (int e = threadIdx.x; e < a.op.n_mats * 4; e += blockDim.x)
+            sm_off[e] = a.op.offmask[e];
+    }
+    __syncthreads();
+
+    const V *__restrict__ x = reinterpret_cast<const V *>(a.x);
+    V *__restrict__ y = reinterpret_cast<V *>(a.y);
+    const int nvec = a.nvec;
+    const int n_terms = a.op.n_terms;
+    const uint64_t dim = a.ix.dim;
+    const W full = (W)a.g.full;
+    const unsigned kAll = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const unsigned lanes_below = (1u << lane) - 1u;
+    const uint64_t gw = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    const uint64_t per = (dim + nw - 1) / nw;
+    const uint64_t row_begin = min(dim, gw * per);
+    const uint64_t row_end = min(dim, row_begin + per);
+    uint64_t next = row_begin;  // warp-uniform
+
+    bool has = false;
+    uint64_t row = 0;
+    W r = 0;
+    T nr = 1;
+    int t = -1, col = 0, si = 0, sj = 0, mid = 0, amp = 0;
+    uint32_t cmask = 0;
+    W cur = 0;
+    V acc[NV];
+
+    // next off-diagonal term of H|r>: sets cur (the produced state) and amp
+    auto advance = [&]() -> bool {
+        while (cmask == 0) {
+            if (++t >= n_terms)
+                return false;
+            const uint32_t td = sm_terms[t];
+            si = td & 0xff;
+            sj = (td >> 8) & 0xff;
+            mid = td >> 16;
+            col = (int)(((r >> si) & 1) << 1 | ((r >> sj) & 1));
+            cmask = sm_off[mid * 4 + col];
+        }
+        const int cp = __ffs(cmask) - 1;
+        cmask &= cmask - 1;
+        cur = (r & ~((W(1) << si) | (W(1) << sj))) | (W(cp >> 1) << si) | (W(cp & 1) << sj);
+        amp = mid * 16 + cp * 4 + col;
+        return true;
+    };
+    auto store_row = [&]() {
+#pragma unroll
+        for (int v = 0; v < NV; ++v)
+            if (v < nvec)
+                y[row * nvec + v] = acc[v];
+    };
+
+    while (true) {
+        while (true) {
+            const unsigned need = __ballot_sync(kAll, !has);
+            if (need == 0 || next >= row_end)
+                break;
+            const uint64_t mine = next + __popc(need & lanes_below);
+            next += __popc(need);
+            if (!has && mine < row_end) {
+                row = mine;
+                r = (W)__ldg(a.ix.states + row);
+                nr = (T)__ldg(a.ix.norms + row);
+                Cplx<T> d = {T(0), T(0)};
+                for (int q = 0; q < n_terms; ++q) {
+                    const uint32_t td = sm_terms[q];
+                    const int c = (int)(((r >> (td & 0xff)) & 1) << 1 | ((r >> ((td >> 8) & 0xff)) & 1));
+                    const Cplx<T> h = sm_mats[(td >> 16) * 16 + c * 5];
+                    d.re += h.re;
+                    d.im += h.im;
+                }
+#pragma unroll
+                for (int v = 0; v < NV; ++v) {
+                    if (v < nvec) {
+                        const V xv = x[row * nvec + v];
+                        if constexpr (kC)
+                            acc[v] = cmul(conjc(d), xv);
+                        else
+                            acc[v] = d.re * xv;
+                    }
+                }
+                t = -1;
+                cmask = 0;
+                if (advance())
+                    has = true;
+                else
+                    store_row();
+            }
+        }
+        if (__ballot_sync(kAll, has) == 0)
+            break;
+
+        W best;
+        int gbest;
+        rep_search<W, kTrack>(has ? cur : W(0), sm_masks, a.g.n_perm, a.g.flip, full, best, gbest);
+
+        if (has) {
+            const int64_t j = find_index((uint64_t)best, a.ix);
+            if (j >= 0) {
+                const T ratio = sqrt((T)__ldg(a.ix.norms + j) / nr);
+                const Cplx<T> h = sm_mats[amp];
+                Cplx<T> coef = {h.re * ratio, -h.im * ratio};  // conj(h) sqrt(n'/n)
+                if (kTrack)
+                    coef = cmul(coef, sm_chi[gbest]);
+#pragma unroll
+                for (int v = 0; v < NV; ++v) {
+                    if (v < nvec) {
+                        const V xv = x[(uint64_t)j * nvec + v];
+                        if constexpr (kC) {
+                            const Cplx<T> p = cmul(coef, xv);
+                            acc[v].re += p.re;
+                            acc[v].im += p.im;
+                        } else {
+                            acc[v] += coef.re * xv;
+                        }
+                    }
+                }
+            }
+            if (!advance()) {
+                store_row();
+                has = false;
+            }
+        }
+    }
+}
+
+template <typename W, typename T, bool kC, bool kTrack, int NV>
+cudaError_t matvec_launch(const MatvecArgs &a, cudaStream_t stream)
+{
+    auto kern = k_matvec<W, T, kC, kTrack, NV>;
+    const size_t smem = matvec_smem_bytes<W, T, kTrack>(a.g, a.op);
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess)
+        return e;
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kMvThreads, smem);
+    if (e != cudaSuccess)
+        return e;
+    const uint64_t warps_needed = (a.ix.dim + 31) / 32;
+    const uint64_t blocks_needed = (warps_needed * 32 + kMvThreads - 1) / kMvThreads;
+    const int grid = (int)std::min<uint64_t>(blocks_needed, (uint64_t)sms * std::max(per_sm, 1));
+    kern<<<std::max(grid, 1), kMvThreads, smem, stream>>>(a); count_launch();
+    return cudaGetLastError();
+}
+
+template <typename T, bool kC>
+cudaError_t matvec_dispatch_prec(const MatvecArgs &a, bool track, cudaStream_t stream)
+{
+    const bool w32 = a.g.n_sites <= 32;
+#define ED_MV_NV(W, TR)                                                           \
+    do {                                                                          \
+        if (a.nvec == 1) return matvec_launch<W, T, kC, TR, 1>(a, stream);        \
+        if (a.nvec <= 4) return matvec_launch<W, T, kC, TR, 4>(a, stream);        \
+        if (a.nvec <= 8) return matvec_launch<W, T, kC, TR, 8>(a, stream);        \
+        return matvec_launch<W, T, kC, TR, 16>(a, stream);                        \
+    } while (0)
+    if (w32) {
+        if (track) ED_MV_NV(uint32_t, true);
+        ED_MV_NV(uint32_t, false);
+    }
+    if (track) ED_MV_NV(uint64_t, true);
+    ED_MV_NV(uint64_t, false);
+#undef ED_MV_NV
+}
+
+cudaError_t matvec_f64(const MatvecArgs &a, bool track, cudaStream_t s);
+cudaError_t matvec_f32(const MatvecArgs &a, bool track, cudaStream_t s);
+cudaError_t matvec_c128(const MatvecArgs &a, bool track, cudaStream_t s);
+cudaError_t matvec_c64(const MatvecArgs &a, bool track, cudaStream_t s);
+
+}  // namespace edk

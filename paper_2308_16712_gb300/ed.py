@@ -1,0 +1,234 @@
+"""Thin ctypes binding of libed.so (include/ed.h), one Python function per C entry
+point with the same name minus the ``ed_`` prefix.  Argument marshalling only:
+every step of the computation runs in the library's CUDA kernels.
+
+Device arrays are torch CUDA tensors (PyTorch provides device memory and
+streams); the default stream argument is torch's current stream.  There is no
+CPU fallback: importing this module without the built library raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libed.so")
+
+ED_OK = 0
+ED_F64, ED_F32, ED_C128, ED_C64 = 0, 1, 2, 3
+ED_LANCZOS_F64, ED_LANCZOS_F32_MATVEC, ED_LANCZOS_RECOMPUTE = 0, 1, 16
+
+STATUS_NAMES = {
+    0: "ED_OK", 1: "ED_ERR_INVALID_ARG", 2: "ED_ERR_NOT_A_GROUP", 3: "ED_ERR_BAD_CHARACTER",
+    4: "ED_ERR_SYMMETRY_MISMATCH", 5: "ED_ERR_OOM", 6: "ED_ERR_CUDA", 7: "ED_ERR_INTERNAL",
+    8: "ED_ERR_NOT_CONVERGED", 9: "ED_ERR_UNSUPPORTED",
+}
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"{LIB_PATH} is missing: build it with paper_2308_16712_gb300.build.build() "
+                      "(there is no fallback implementation)")
+
+_lib = ctypes.CDLL(LIB_PATH)
+_P = ctypes.c_void_p
+_i32, _u64, _i64, _d = ctypes.c_int, ctypes.c_uint64, ctypes.c_int64, ctypes.c_double
+
+
+class LanczosInfo(ctypes.Structure):
+    _fields_ = [("steps", ctypes.c_int), ("matvecs", ctypes.c_int), ("ritz", ctypes.c_double),
+                ("e0", ctypes.c_double), ("residual", ctypes.c_double),
+                ("matvec_ms", ctypes.c_double)]
+
+
+_SIGS = {
+    "ed_status_string": (ctypes.c_char_p, [_i32]),
+    "ed_basis_build": (_i32, [_i32, _i32, _i32, _i32, _P, _P, _P, ctypes.POINTER(_P)]),
+    "ed_basis_size": (_i32, [_P, ctypes.POINTER(_u64)]),
+    "ed_basis_states": (_i32, [_P, ctypes.POINTER(_P), ctypes.POINTER(_P)]),
+    "ed_basis_is_real": (_i32, [_P, ctypes.POINTER(_i32)]),
+    "ed_basis_index": (_i32, [_P, _P, _P, _u64, _P]),
+    "ed_basis_destroy": (None, [_P]),
+    "ed_operator_create": (_i32, [_i32, _i32, _P, _P, _P, ctypes.POINTER(_P)]),
+    "ed_operator_destroy": (None, [_P]),
+    "ed_matvec": (_i32, [_P, _P, _P, _P, _i32, _i32, _P]),
+    "ed_lanczos": (_i32, [_P, _P, _P, _i32, _i32, ctypes.POINTER(_d), _P,
+                          ctypes.POINTER(LanczosInfo), _P]),
+    "edx_launch_count": (ctypes.c_ulonglong, []),
+}
+for _name, (_res, _args) in _SIGS.items():
+    if hasattr(_lib, _name):
+        _f = getattr(_lib, _name)
+        _f.restype = _res
+        _f.argtypes = _args
+
+
+class EDError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        super().__init__(f"{where}: {STATUS_NAMES.get(status, status)} "
+                         f"({_lib.ed_status_string(status).decode()})")
+
+
+def _check(st: int, where: str):
+    if st != ED_OK:
+        raise EDError(st, where)
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _host(a, dtype):
+    return np.ascontiguousarray(np.asarray(a, dtype=dtype))
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class _DevArray:
+    """__cuda_array_interface__ wrapper so torch can view library-owned memory."""
+
+    def __init__(self, ptr: int, n: int, typestr: str, owner):
+        self.__cuda_array_interface__ = {"shape": (n,), "typestr": typestr,
+                                         "data": (ptr, True), "version": 3, "strides": None}
+        self._owner = owner
+
+
+class Basis:
+    """Owns an ed_basis handle."""
+
+    def __init__(self, handle: ctypes.c_void_p, n_sites: int):
+        self.handle = handle
+        self.n_sites = n_sites
+
+    def __del__(self):
+        if getattr(self, "handle", None):
+            _lib.ed_basis_destroy(self.handle)
+            self.handle = None
+
+
+class Operator:
+    """Owns an ed_operator handle."""
+
+    def __init__(self, handle: ctypes.c_void_p, n_sites: int):
+        self.handle = handle
+        self.n_sites = n_sites
+
+    def __del__(self):
+        if getattr(self, "handle", None):
+            _lib.ed_operator_destroy(self.handle)
+            self.handle = None
+
+
+def status_string(status: int) -> str:
+    return _lib.ed_status_string(status).decode()
+
+
+def basis_build(n_sites: int, n_up: int, spin_inversion: int, perms, chars, stream=None) -> Basis:
+    perms = _host(perms, np.int32).reshape(-1, n_sites)
+    chars = _host(chars, np.float64).reshape(-1, 2)
+    if len(perms) != len(chars):
+        raise ValueError("perms and chars disagree on the group order")
+    out = ctypes.c_void_p()
+    _check(_lib.ed_basis_build(n_sites, n_up, spin_inversion, len(perms),
+                               perms.ctypes.data_as(_P), chars.ctypes.data_as(_P), _stream(stream),
+                               ctypes.byref(out)), "ed_basis_build")
+    return Basis(out, n_sites)
+
+
+def basis_size(basis: Basis) -> int:
+    d = ctypes.c_uint64()
+    _check(_lib.ed_basis_size(basis.handle, ctypes.byref(d)), "ed_basis_size")
+    return d.value
+
+
+def basis_is_real(basis: Basis) -> bool:
+    r = ctypes.c_int()
+    _check(_lib.ed_basis_is_real(basis.handle, ctypes.byref(r)), "ed_basis_is_real")
+    return bool(r.value)
+
+
+def basis_states(basis: Basis):
+    """(states, norms) as torch CUDA tensor views (int64 holding the uint64 bits,
+    int16 holding the uint16 norms); valid while `basis` lives."""
+    import torch
+    s, n = ctypes.c_void_p(), ctypes.c_void_p()
+    _check(_lib.ed_basis_states(basis.handle, ctypes.byref(s), ctypes.byref(n)), "ed_basis_states")
+    dim = basis_size(basis)
+    if dim == 0:
+        dev = torch.device("cuda")
+        return torch.empty(0, dtype=torch.int64, device=dev), torch.empty(0, dtype=torch.int16, device=dev)
+    st = torch.as_tensor(_DevArray(s.value, dim, "<i8", basis), device="cuda")
+    nm = torch.as_tensor(_DevArray(n.value, dim, "<i2", basis), device="cuda")
+    return st, nm
+
+
+def basis_index(basis: Basis, query, out=None, stream=None):
+    """stateToIndex for an int64 CUDA tensor of states; returns int64 indices (-1 = absent)."""
+    import torch
+    q = query.contiguous()
+    if out is None:
+        out = torch.empty(q.numel(), dtype=torch.int64, device=q.device)
+    _check(_lib.ed_basis_index(basis.handle, _ptr(q), _ptr(out), q.numel(), _stream(stream)),
+           "ed_basis_index")
+    return out
+
+
+def operator_create(n_sites: int, sites, coeff, local) -> Operator:
+    sites = _host(sites, np.int32).reshape(-1, 2)
+    coeff = _host(coeff, np.float64).reshape(-1, 2)
+    local = _host(local, np.float64).reshape(-1, 16, 2)
+    out = ctypes.c_void_p()
+    _check(_lib.ed_operator_create(n_sites, len(sites), coeff.ctypes.data_as(_P),
+                                   sites.ctypes.data_as(_P), local.ctypes.data_as(_P),
+                                   ctypes.byref(out)), "ed_operator_create")
+    return Operator(out, n_sites)
+
+
+_DTYPE_CODE = {"float64": ED_F64, "float32": ED_F32, "complex128": ED_C128, "complex64": ED_C64}
+
+
+def matvec(op: Operator, basis: Basis, x, y, nvec: int = 1, stream=None):
+    """y = H x (torch CUDA tensors of shape (dim,) or (dim, nvec), same dtype)."""
+    if x.dtype != y.dtype:
+        raise ValueError("x and y must share a dtype")
+    code = _DTYPE_CODE[str(x.dtype).replace("torch.", "")]
+    if not (x.is_contiguous() and y.is_contiguous()):
+        raise ValueError("x and y must be contiguous")
+    _check(_lib.ed_matvec(op.handle, basis.handle, _ptr(x), _ptr(y), nvec, code, _stream(stream)),
+           "ed_matvec")
+    return y
+
+
+def launch_count() -> int:
+    """Kernel launches the library has issued since it was loaded (diagnostics)."""
+    return int(_lib.edx_launch_count())
+
+
+@dataclass
+class LanczosResult:
+    e0: float
+    steps: int
+    matvecs: int
+    ritz: float
+    residual: float
+    matvec_ms: float
+
+
+def lanczos(op: Operator, basis: Basis, x0, steps: int, mode: int = ED_LANCZOS_F64, vec_out=None,
+            stream=None) -> LanczosResult:
+    e0 = ctypes.c_double()
+    info = LanczosInfo()
+    _check(_lib.ed_lanczos(op.handle, basis.handle, _ptr(x0), steps, mode, ctypes.byref(e0),
+                           _ptr(vec_out) if vec_out is not None else None, ctypes.byref(info),
+                           _stream(stream)), "ed_lanczos")
+    return LanczosResult(e0.value, info.steps, info.matvecs, info.ritz, info.residual,
+                         info.matvec_ms)
