@@ -245,6 +245,29 @@ def run_matvec_only(args, w):
     print(json.dumps({"mode": "matvec", "workload": w["name"], "dim": dim, "launches": 2 * args.steps}))
 
 
+def search_ops_per_term(n, n_perm, flip, fact, rot_L, n_cos, kinds):
+    """INT32 operations of one representative search as the kernel runs it
+    (instruction-level count of the algorithm, not a measurement):
+    32-bit words: Benes stage = 2 shifts + 2 three-input logic ops (9 stages);
+    rotation of the doubled word = 1 funnel shift (+1 mask op when n < 32);
+    spin-inversion candidate = 1 logic op; running minimum = 1 op per candidate.
+    64-bit words: each of those costs two 32-bit operations; the 64-bit
+    minimum costs 4 (2 compares, 2 selects); one incremental rotation costs 6."""
+    cand = 2 if flip else 1
+    if n <= 32:
+        benes, rev = 36, (1 if n == 32 else 2)
+        per_rot = (1 if n == 32 else 2) + cand * 1 + (1 if flip else 0)
+        per_perm = benes + cand * 1 + (1 if flip else 0)
+    else:
+        benes, rev = 84, 4
+        per_rot = 6 + cand * 4 + (2 if flip else 0)
+        per_perm = benes + cand * 4 + (2 if flip else 0)
+    if not fact:
+        return n_perm * per_perm
+    head = sum({0: 0, 1: rev, 2: benes}[int(k)] for k in kinds)
+    return head + n_cos * rot_L * per_rot
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -350,8 +373,10 @@ def main():
     # roofline of the dominant kernel (the matvec): integer ALU bound
     pk, pk_kind = peaks()
     n_perm = len(w["perms"])
-    c_g = 39 if n <= 32 else 94  # INT32 ops per (term, permutation): Benes stages + flip + min
-    int_ops = dim * t_gen * n_perm * c_g
+    fact, rot_L, rot_d, n_cos = ed.basis_factored(B)
+    kinds = [0, 1] if (fact and n_cos == 2) else [0] + [2] * (n_cos - 1)
+    ops_term = search_ops_per_term(n, n_perm, z != 0, fact, rot_L, n_cos, kinds)
+    int_ops = dim * t_gen * ops_term
     avg_ms = (mv32_ms / max(mv32_n, 1)) if mv32_n else mv["f32"]["ms"]
     achieved = int_ops / (avg_ms * 1e-3) / 1e12
     peak_int = SMS * INT_LANES_PER_SM * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
@@ -402,8 +427,9 @@ def main():
         "matvec_kernel": mv,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_int, "unit": "TOP/s",
                      "frac": achieved / peak_int, "traffic": None,
-                     "kernel": "k_matvec (fp32, 32-bit Benes group search)",
-                     "int_ops_per_launch": int_ops,
+                     "kernel": "k_matvec (fp32, " + ("rotation x coset" if fact else "Benes")
+                               + f" group search, {'32' if n <= 32 else '64'}-bit words)",
+                     "int_ops_per_launch": int_ops, "int_ops_per_term": ops_term,
                      "peak_basis": f"{SMS} SMs x {INT_LANES_PER_SM} INT32 lanes x "
                                    f"{pk.get('sm_max_mhz', 2070.0):.0f} MHz ({pk_kind} clock)"},
         "cpu_baseline": cpu,

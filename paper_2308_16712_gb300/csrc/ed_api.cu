@@ -154,10 +154,100 @@ cudaError_t upload(T **dst, const T *src, size_t count)
     return e;
 }
 
+// Factored form of the lattice group: the largest cyclic subgroup acting as a
+// rotation of the n-bit word (site i -> i + d mod n, smallest such d) and one
+// representative per coset {rho^b h}, preferring the identity, then the bit
+// reversal (site i -> n - 1 - i), else any element (applied by a Benes network).
+struct Factorization {
+    int L = 1, d = 0;
+    std::vector<int> rep;       // user element index of each coset representative
+    std::vector<uint8_t> kind;  // 0 identity, 1 reversal, 2 Benes
+    std::vector<int> elem;      // (c * L + b) -> user element index of rho^b h_c
+};
+
+bool factorize(int n, int ne, const int32_t *perms, Factorization &F)
+{
+    std::map<std::vector<int32_t>, int> index;
+    for (int g = 0; g < ne; ++g)
+        index.emplace(std::vector<int32_t>(perms + (size_t)g * n, perms + (size_t)(g + 1) * n), g);
+    int d = 0;
+    for (int cand = 1; cand < n && !d; ++cand) {
+        if (n % cand)
+            continue;
+        std::vector<int32_t> rot(n);
+        for (int i = 0; i < n; ++i)
+            rot[i] = (i + cand) % n;
+        if (index.count(rot))
+            d = cand;
+    }
+    if (!d || d >= 32)
+        return false;
+    const int L = n / d;
+    if (ne % L)
+        return false;
+    F.L = L;
+    F.d = d;
+    std::vector<int> coset_of(ne, -1);
+    std::vector<int32_t> q(n), ident(n), rev(n);
+    for (int i = 0; i < n; ++i) {
+        ident[i] = i;
+        rev[i] = n - 1 - i;
+    }
+    for (int g = 0; g < ne; ++g) {
+        if (coset_of[g] >= 0)
+            continue;
+        const int c = (int)F.rep.size();
+        std::vector<int> members(L);
+        for (int b = 0; b < L; ++b) {
+            for (int i = 0; i < n; ++i)
+                q[i] = (perms[(size_t)g * n + i] + b * d) % n;
+            auto it = index.find(q);
+            if (it == index.end())
+                return false;
+            members[b] = it->second;
+            coset_of[it->second] = c;
+        }
+        // representative: identity, else reversal, else g itself
+        int rep = g, kind = 2;
+        for (int m : members) {
+            std::vector<int32_t> p(perms + (size_t)m * n, perms + (size_t)(m + 1) * n);
+            if (p == ident) {
+                rep = m;
+                kind = 0;
+                break;
+            }
+            if (p == rev && kind == 2) {
+                rep = m;
+                kind = 1;
+            }
+        }
+        F.rep.push_back(rep);
+        F.kind.push_back((uint8_t)kind);
+    }
+    const int nc = (int)F.rep.size();
+    F.elem.assign((size_t)nc * L, -1);
+    for (int c = 0; c < nc; ++c) {
+        for (int b = 0; b < L; ++b) {
+            for (int i = 0; i < n; ++i)
+                q[i] = (perms[(size_t)F.rep[c] * n + i] + b * d) % n;
+            F.elem[(size_t)c * L + b] = index.at(q);
+        }
+    }
+    return nc * L == ne;
+}
+
+bool g_force_generic = false;
+
 void free_basis(ed_basis *b)
 {
     if (!b)
         return;
+    cudaFree(b->d_cos_kind);
+    cudaFree(b->d_cos_masks32);
+    cudaFree(b->d_cos_masks64);
+    cudaFree(b->d_fchi);
+    cudaFree(b->d_fchif);
+    cudaFree(b->d_fchi_one);
     cudaFree(b->d_states);
     cudaFree(b->d_norms);
     cudaFree(b->d_tab);
@@ -353,6 +443,16 @@ edk::GroupView ed_basis::group_view() const
     g.chi = d_chi;
     g.chif = d_chif;
     g.chi_one = d_chi_one;
+    g.fact = fact && !g_force_generic;
+    g.rot_L = rot_L;
+    g.rot_d = rot_d;
+    g.n_cos = n_cos;
+    g.cos_kind = d_cos_kind;
+    g.cos_masks32 = d_cos_masks32;
+    g.cos_masks64 = d_cos_masks64;
+    g.fchi = d_fchi;
+    g.fchif = d_fchif;
+    g.fchi_one = d_fchi_one;
     return g;
 }
 
@@ -467,6 +567,46 @@ ed_status ed_basis_build(int n_sites, int n_up, int spin_inversion, int n_elems,
     ED_B_TRY(upload(&b->d_chi, chi.data(), chi.size()));
     ED_B_TRY(upload(&b->d_chif, chif.data(), chif.size()));
     ED_B_TRY(upload(&b->d_chi_one, one.data(), one.size()));
+    {
+        Factorization F;
+        if (factorize(n_sites, n_elems, perms, F)) {
+            const int nc = (int)F.rep.size();
+            std::vector<uint32_t> cm32((size_t)nc * edk::kMaskStride, 0);
+            std::vector<uint64_t> cm64((size_t)nc * edk::kMaskStride, 0);
+            for (int c = 0; c < nc; ++c) {
+                const int32_t *pm = perms + (size_t)F.rep[c] * n_sites;
+                if (n_sites <= 32) {
+                    auto m = benes_masks(5, n_sites, pm);
+                    for (int st2 = 0; st2 < 9; ++st2)
+                        cm32[(size_t)c * edk::kMaskStride + st2] = (uint32_t)m[st2];
+                }
+                auto m = benes_masks(6, n_sites, pm);
+                for (int st2 = 0; st2 < 11; ++st2)
+                    cm64[(size_t)c * edk::kMaskStride + st2] = m[st2];
+            }
+            std::vector<double2> fchi(b->order);
+            std::vector<float2> fchif(b->order);
+            std::vector<uint32_t> fone((b->order + 31) / 32, 0);
+            for (int g = 0; g < b->order; ++g) {
+                const int fi = g % n_elems;            // factored index within one flip half
+                const int src = F.elem[fi] + (g >= n_elems ? n_elems : 0);  // expanded index
+                fchi[g] = chi[src];
+                fchif[g] = chif[src];
+                if ((one[src / 32] >> (src % 32)) & 1u)
+                    fone[g / 32] |= 1u << (g % 32);
+            }
+            ED_B_TRY(upload(&b->d_cos_kind, F.kind.data(), F.kind.size()));
+            ED_B_TRY(upload(&b->d_cos_masks32, cm32.data(), cm32.size()));
+            ED_B_TRY(upload(&b->d_cos_masks64, cm64.data(), cm64.size()));
+            ED_B_TRY(upload(&b->d_fchi, fchi.data(), fchi.size()));
+            ED_B_TRY(upload(&b->d_fchif, fchif.data(), fchif.size()));
+            ED_B_TRY(upload(&b->d_fchi_one, fone.data(), fone.size()));
+            b->fact = true;
+            b->rot_L = F.L;
+            b->rot_d = F.d;
+            b->n_cos = nc;
+        }
+    }
 
     // enumeration plan
     std::vector<uint64_t> binom(65 * 65);
@@ -659,6 +799,39 @@ ed_status ed_matvec(const ed_operator *op, const ed_basis *b, const void *x, voi
     ED_CUDA_TRY(edk::launch_matvec(op_view(op), b->group_view(), b->index_view(), !b->trivial_chars,
                                    x, y, nvec, dtype, (cudaStream_t)stream));
     return ED_OK;
+}
+
+// Test hook (not part of the public header): 1 = use the generic Benes search
+// for every group even when the factored form is available (both paths are
+// then exercised by the same parity tests).  Affects later launches.
+void edx_force_generic(int on) { g_force_generic = on != 0; }
+
+// Host-only test hook: the factored form the library finds for a permutation
+// group (returns the number of cosets, 0 if there is none); kinds_out gets one
+// byte per coset (0 identity, 1 reversal, 2 Benes), at most ne entries.
+int edx_factorize(int n, int ne, const int32_t *perms, int *rot_L, int *rot_d, uint8_t *kinds_out)
+{
+    if (n < 1 || n > 64 || ne < 1 || !perms)
+        return -1;
+    Factorization F;
+    if (!factorize(n, ne, perms, F))
+        return 0;
+    if (rot_L) *rot_L = F.L;
+    if (rot_d) *rot_d = F.d;
+    if (kinds_out)
+        std::copy(F.kind.begin(), F.kind.end(), kinds_out);
+    return (int)F.rep.size();
+}
+
+// Diagnostics hook: whether a basis uses the factored search, and its shape.
+int edx_basis_factored(const ed_basis *b, int *rot_L, int *rot_d, int *n_cos)
+{
+    if (!b)
+        return -1;
+    if (rot_L) *rot_L = b->rot_L;
+    if (rot_d) *rot_d = b->rot_d;
+    if (n_cos) *n_cos = b->n_cos;
+    return b->fact ? 1 : 0;
 }
 
 // Diagnostics hook (not part of the public header): kernel launches issued by

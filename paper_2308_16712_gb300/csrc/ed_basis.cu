@@ -69,21 +69,59 @@ __device__ __forceinline__ int rep_norm(W s, const W *sm_masks, const uint32_t *
     return ok ? stab : 0;
 }
 
-template <typename W, bool kU1, bool kWrite>
+// Same test over the factored group (rotation subgroup x coset representatives).
+template <typename W>
+__device__ __forceinline__ int rep_norm_fact(W s, const uint8_t *kinds, const W *masks,
+                                             const uint32_t *one, const GroupView &g, W full)
+{
+    int stab = 0;
+    bool ok = true, rep = true;
+    for_each_image<W>(s, kinds, masks, g.n_cos, g.rot_L, g.rot_d, g.n_sites, g.n_perm, g.flip, full,
+                      [&](W q, int gi) {
+                          if (q < s) {
+                              rep = false;
+                              return true;
+                          }
+                          if (q == s) {
+                              ++stab;
+                              ok = ok && chi_is_one(one, gi);
+                          }
+                          return false;
+                      });
+    return (rep && ok) ? stab : 0;
+}
+
+__host__ __device__ inline size_t enum_smem_bytes(const GroupView &g, size_t wbytes, bool fact)
+{
+    const int nm = fact ? g.n_cos : g.n_perm;
+    return (size_t)nm * kMaskStride * wbytes + ((g.order + 31) / 32) * 4 + ((nm + 15) / 16) * 16;
+}
+
+template <typename W, bool kU1, bool kWrite, bool kFact>
 __global__ void __launch_bounds__(kEnumThreads) k_enumerate(EnumPlan plan, GroupView g,
                                                             uint32_t *counts,
                                                             const uint64_t *offsets,
                                                             uint64_t *states, uint16_t *norms)
 {
     extern __shared__ __align__(16) unsigned char smem[];
+    const int nm = kFact ? g.n_cos : g.n_perm;
     W *sm_masks = reinterpret_cast<W *>(smem);
-    uint32_t *sm_one = reinterpret_cast<uint32_t *>(smem + (size_t)g.n_perm * kMaskStride * sizeof(W));
-    const W *gm = sizeof(W) == 4 ? reinterpret_cast<const W *>(g.masks32)
-                                 : reinterpret_cast<const W *>(g.masks64);
-    for (int e = threadIdx.x; e < g.n_perm * kMaskStride; e += blockDim.x)
+    uint32_t *sm_one = reinterpret_cast<uint32_t *>(smem + (size_t)nm * kMaskStride * sizeof(W));
+    uint8_t *sm_kind = reinterpret_cast<uint8_t *>(sm_one + (g.order + 31) / 32);
+    const W *gm;
+    if (kFact)
+        gm = sizeof(W) == 4 ? reinterpret_cast<const W *>(g.cos_masks32)
+                            : reinterpret_cast<const W *>(g.cos_masks64);
+    else
+        gm = sizeof(W) == 4 ? reinterpret_cast<const W *>(g.masks32)
+                            : reinterpret_cast<const W *>(g.masks64);
+    for (int e = threadIdx.x; e < nm * kMaskStride; e += blockDim.x)
         sm_masks[e] = gm[e];
     for (int e = threadIdx.x; e < (g.order + 31) / 32; e += blockDim.x)
-        sm_one[e] = g.chi_one[e];
+        sm_one[e] = kFact ? g.fchi_one[e] : g.chi_one[e];
+    if (kFact)
+        for (int e = threadIdx.x; e < g.n_cos; e += blockDim.x)
+            sm_kind[e] = g.cos_kind[e];
     __syncthreads();
     const W full = (W)g.full;
     for (uint64_t c = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; c < plan.n_chunks;
@@ -94,11 +132,12 @@ __global__ void __launch_bounds__(kEnumThreads) k_enumerate(EnumPlan plan, Group
         uint32_t kept = 0;
         uint64_t out = kWrite ? offsets[c] : 0;
         for (uint64_t q = 0; q < cnt; ++q) {
-            const int nm = rep_norm<W>((W)s, sm_masks, sm_one, g.n_perm, g.flip, full);
-            if (nm) {
+            const int nrm = kFact ? rep_norm_fact<W>((W)s, sm_kind, sm_masks, sm_one, g, full)
+                                  : rep_norm<W>((W)s, sm_masks, sm_one, g.n_perm, g.flip, full);
+            if (nrm) {
                 if (kWrite) {
                     states[out] = s;
-                    norms[out] = (uint16_t)nm;
+                    norms[out] = (uint16_t)nrm;
                     ++out;
                 }
                 ++kept;
@@ -111,13 +150,13 @@ __global__ void __launch_bounds__(kEnumThreads) k_enumerate(EnumPlan plan, Group
     }
 }
 
-template <typename W, bool kU1, bool kWrite>
+template <typename W, bool kU1, bool kWrite, bool kFact>
 cudaError_t enum_launch(const EnumPlan &plan, const GroupView &g, uint32_t *counts,
                         const uint64_t *offsets, uint64_t *states, uint16_t *norms,
                         cudaStream_t stream)
 {
-    auto kern = k_enumerate<W, kU1, kWrite>;
-    const size_t smem = (size_t)g.n_perm * kMaskStride * sizeof(W) + ((g.order + 31) / 32) * 4;
+    auto kern = k_enumerate<W, kU1, kWrite, kFact>;
+    const size_t smem = enum_smem_bytes(g, sizeof(W), kFact);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess)
         return e;
@@ -139,12 +178,18 @@ cudaError_t enum_dispatch(const EnumPlan &plan, const GroupView &g, uint32_t *co
                           cudaStream_t stream)
 {
     const bool u1 = plan.n_up >= 0;
+#define ED_ENUM(W, U1)                                                                           \
+    return g.fact ? enum_launch<W, U1, kWrite, true>(plan, g, counts, offsets, states, norms, stream) \
+                  : enum_launch<W, U1, kWrite, false>(plan, g, counts, offsets, states, norms, stream)
     if (plan.n_sites <= 32) {
-        return u1 ? enum_launch<uint32_t, true, kWrite>(plan, g, counts, offsets, states, norms, stream)
-                  : enum_launch<uint32_t, false, kWrite>(plan, g, counts, offsets, states, norms, stream);
+        if (u1)
+            ED_ENUM(uint32_t, true);
+        ED_ENUM(uint32_t, false);
     }
-    return u1 ? enum_launch<uint64_t, true, kWrite>(plan, g, counts, offsets, states, norms, stream)
-              : enum_launch<uint64_t, false, kWrite>(plan, g, counts, offsets, states, norms, stream);
+    if (u1)
+        ED_ENUM(uint64_t, true);
+    ED_ENUM(uint64_t, false);
+#undef ED_ENUM
 }
 
 // ---------------------------------------------------------------------------

@@ -94,6 +94,17 @@ struct GroupView {
     const double2 *chi;       // order entries, expanded
     const float2 *chif;       // same, single precision
     const uint32_t *chi_one;  // bitset over the expanded order: chi == 1
+    // Factored form G = { rho^b h_c F^f }: rho = rotation of the n_sites-bit word
+    // by rot_d bits (order rot_L), h_c = coset representatives applied first.
+    // Expanded factored index: c * rot_L + b (+ n_perm if flipped).
+    int fact;                 // 1 if the factored form is available
+    int rot_L, rot_d, n_cos;
+    const uint8_t *cos_kind;  // n_cos: 0 identity, 1 bit reversal, 2 Benes network
+    const uint32_t *cos_masks32;  // n_cos x kMaskStride
+    const uint64_t *cos_masks64;  // n_cos x kMaskStride
+    const double2 *fchi;      // order entries, factored index
+    const float2 *fchif;
+    const uint32_t *fchi_one;
 };
 
 struct IndexView {
@@ -182,6 +193,110 @@ __device__ __forceinline__ void rep_search(W s, const W *sm_masks, int n_perm, i
 }
 
 // ---------------------------------------------------------------------------
+// Representative search over the factored group.  For every coset
+// representative h (identity, bit reversal of the n-bit word, or a Benes
+// network) the image h.s is rotated through all rot_L positions; each rotated
+// word q and its complement q ^ full (spin inversion) are candidates.  The
+// coset loop and the rotation loop are uniform across the warp.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t reverse_bits(uint32_t s, int n) { return __brev(s) >> (32 - n); }
+__device__ __forceinline__ uint64_t reverse_bits(uint64_t s, int n) { return __brevll(s) >> (64 - n); }
+
+template <typename W>
+__device__ __forceinline__ W coset_image(W s, int kind, const W *masks, int n)
+{
+    if (kind == 0)
+        return s;
+    if (kind == 1)
+        return reverse_bits(s, n);
+    return benes_apply(s, masks);
+}
+
+// Visits every candidate of the factored group: f(candidate, factored index).
+// 32-bit words: rotation by k of the n-bit word is one funnel shift of the
+// doubled word (h | h << n).
+template <typename F>
+__device__ __forceinline__ void for_each_image32(uint32_t s, const uint8_t *kinds, const uint32_t *masks,
+                                                 int n_cos, int L, int d, int n, int n_perm, int flip,
+                                                 uint32_t full, F &&f)
+{
+    for (int c = 0; c < n_cos; ++c) {
+        const uint32_t h = coset_image(s, (int)kinds[c], masks + c * kMaskStride, n);
+        const uint32_t lo = n == 32 ? h : (h | (h << n));
+        const uint32_t hi = n == 32 ? h : (h >> (32 - n));
+        const int base = c * L;
+        if (n == 32) {
+            for (int b = 0; b < L; ++b) {
+                const uint32_t q = __funnelshift_l(h, h, b * d);
+                if (f(q, base + b))
+                    return;
+                if (flip && f(~q, base + b + n_perm))
+                    return;
+            }
+        } else {
+            for (int b = 0; b < L; ++b) {
+                const uint32_t q = __funnelshift_rc(lo, hi, n - b * d) & full;
+                if (f(q, base + b))
+                    return;
+                if (flip && f(q ^ full, base + b + n_perm))
+                    return;
+            }
+        }
+    }
+}
+
+// 64-bit words: the rotation is applied incrementally, rho = rotate by d.
+template <typename F>
+__device__ __forceinline__ void for_each_image64(uint64_t s, const uint8_t *kinds, const uint64_t *masks,
+                                                 int n_cos, int L, int d, int n, int n_perm, int flip,
+                                                 uint64_t full, F &&f)
+{
+    for (int c = 0; c < n_cos; ++c) {
+        uint64_t q = coset_image(s, (int)kinds[c], masks + c * kMaskStride, n);
+        const int base = c * L;
+        for (int b = 0; b < L; ++b) {
+            if (f(q, base + b))
+                return;
+            if (flip && f(q ^ full, base + b + n_perm))
+                return;
+            q = ((q << d) | (q >> (n - d))) & full;
+        }
+    }
+}
+
+template <typename W, typename F>
+__device__ __forceinline__ void for_each_image(W s, const uint8_t *kinds, const W *masks, int n_cos, int L,
+                                               int d, int n, int n_perm, int flip, W full, F &&f)
+{
+    if constexpr (sizeof(W) == 4)
+        for_each_image32(s, kinds, masks, n_cos, L, d, n, n_perm, flip, full, f);
+    else
+        for_each_image64(s, kinds, masks, n_cos, L, d, n, n_perm, flip, full, f);
+}
+
+template <typename W, bool kTrack>
+__device__ __forceinline__ void rep_search_fact(W s, const uint8_t *kinds, const W *masks, int n_cos, int L,
+                                                int d, int n, int n_perm, int flip, W full, W &best,
+                                                int &gbest)
+{
+    W bst = ~W(0);
+    int gb = 0;
+    for_each_image<W>(s, kinds, masks, n_cos, L, d, n, n_perm, flip, full, [&](W q, int g) {
+        if (kTrack) {
+            if (q < bst) {
+                bst = q;
+                gb = g;
+            }
+        } else {
+            bst = min(bst, q);
+        }
+        return false;
+    });
+    best = bst;
+    gbest = gb;
+}
+
+// ---------------------------------------------------------------------------
 // small complex helpers
 // ---------------------------------------------------------------------------
 template <typename T> struct Cplx { T re, im; };
@@ -215,6 +330,15 @@ struct ed_basis {
     double2 *d_chi = nullptr;
     float2 *d_chif = nullptr;
     uint32_t *d_chi_one = nullptr;
+    // factored form (see GroupView)
+    bool fact = false;
+    int rot_L = 1, rot_d = 0, n_cos = 0;
+    uint8_t *d_cos_kind = nullptr;
+    uint32_t *d_cos_masks32 = nullptr;
+    uint64_t *d_cos_masks64 = nullptr;
+    double2 *d_fchi = nullptr;
+    float2 *d_fchif = nullptr;
+    uint32_t *d_fchi_one = nullptr;
     uint64_t tab_size = 0;
     int e_lo = 0, e_hi = 0, mbits = 0;
 

@@ -45,48 +45,62 @@ template <> __device__ __forceinline__ Cplx<float> load_cf<float>(const float2 *
 
 __host__ __device__ inline size_t align16(size_t v) { return (v + 15) & ~size_t(15); }
 
-template <typename W, typename T, bool kTrack>
-__host__ __device__ inline void matvec_smem_layout(const GroupView &g, const OpView &op, size_t off[5])
+template <typename W, typename T, bool kTrack, bool kFact>
+__host__ __device__ inline void matvec_smem_layout(const GroupView &g, const OpView &op, size_t off[6])
 {
+    const int nm = kFact ? g.n_cos : g.n_perm;
     off[0] = 0;                                                            // masks
-    off[1] = align16(off[0] + (size_t)g.n_perm * kMaskStride * sizeof(W)); // chi
+    off[1] = align16(off[0] + (size_t)nm * kMaskStride * sizeof(W));       // chi
     off[2] = align16(off[1] + (kTrack ? (size_t)g.order * sizeof(Cplx<T>) : 0)); // terms
     off[3] = align16(off[2] + (size_t)op.n_terms * sizeof(uint32_t));     // mats
     off[4] = align16(off[3] + (size_t)op.n_mats * 16 * sizeof(Cplx<T>));  // offmask
+    off[5] = align16(off[4] + (size_t)op.n_mats * 4);                     // coset kinds
 }
 
-template <typename W, typename T, bool kTrack>
+template <typename W, typename T, bool kTrack, bool kFact>
 __host__ __device__ inline size_t matvec_smem_bytes(const GroupView &g, const OpView &op)
 {
-    size_t off[5];
-    matvec_smem_layout<W, T, kTrack>(g, op, off);
-    return align16(off[4] + (size_t)op.n_mats * 4);
+    size_t off[6];
+    matvec_smem_layout<W, T, kTrack, kFact>(g, op, off);
+    return align16(off[5] + (kFact ? (size_t)g.n_cos : 0));
 }
 
-template <typename W, typename T, bool kC, bool kTrack, int NV>
+template <typename W, typename T, bool kC, bool kTrack, bool kFact, int NV>
 __global__ void __launch_bounds__(kMvThreads) k_matvec(const MatvecArgs a)
 {
     using V = typename ValT<T, kC>::type;
     extern __shared__ __align__(16) unsigned char smem[];
-    size_t off[5];
-    matvec_smem_layout<W, T, kTrack>(a.g, a.op, off);
+    size_t off[6];
+    matvec_smem_layout<W, T, kTrack, kFact>(a.g, a.op, off);
     W *sm_masks = reinterpret_cast<W *>(smem + off[0]);
     Cplx<T> *sm_chi = reinterpret_cast<Cplx<T> *>(smem + off[1]);
     uint32_t *sm_terms = reinterpret_cast<uint32_t *>(smem + off[2]);
     Cplx<T> *sm_mats = reinterpret_cast<Cplx<T> *>(smem + off[3]);
     uint8_t *sm_off = smem + off[4];
+    uint8_t *sm_kind = smem + off[5];
 
     {
-        const W *gm = sizeof(W) == 4 ? reinterpret_cast<const W *>(a.g.masks32)
-                                     : reinterpret_cast<const W *>(a.g.masks64);
-        for (int e = threadIdx.x; e < a.g.n_perm * kMaskStride; e += blockDim.x)
+        const int nm = kFact ? a.g.n_cos : a.g.n_perm;
+        const W *gm;
+        if (kFact)
+            gm = sizeof(W) == 4 ? reinterpret_cast<const W *>(a.g.cos_masks32)
+                                : reinterpret_cast<const W *>(a.g.cos_masks64);
+        else
+            gm = sizeof(W) == 4 ? reinterpret_cast<const W *>(a.g.masks32)
+                                : reinterpret_cast<const W *>(a.g.masks64);
+        for (int e = threadIdx.x; e < nm * kMaskStride; e += blockDim.x)
             sm_masks[e] = gm[e];
+        if (kFact)
+            for (int e = threadIdx.x; e < a.g.n_cos; e += blockDim.x)
+                sm_kind[e] = a.g.cos_kind[e];
         if (kTrack) {
+            const double2 *cd = kFact ? a.g.fchi : a.g.chi;
+            const float2 *cf = kFact ? a.g.fchif : a.g.chif;
             for (int e = threadIdx.x; e < a.g.order; e += blockDim.x) {
                 if constexpr (sizeof(T) == 8)
-                    sm_chi[e] = load_c<T>(a.g.chi + e);
+                    sm_chi[e] = load_c<T>(cd + e);
                 else
-                    sm_chi[e] = load_cf<T>(a.g.chif + e);
+                    sm_chi[e] = load_cf<T>(cf + e);
             }
         }
         for (int e = threadIdx.x; e < a.op.n_terms; e += blockDim.x)
@@ -194,7 +208,11 @@ __global__ void __launch_bounds__(kMvThreads) k_matvec(const MatvecArgs a)
 
         W best;
         int gbest;
-        rep_search<W, kTrack>(has ? cur : W(0), sm_masks, a.g.n_perm, a.g.flip, full, best, gbest);
+        if (kFact)
+            rep_search_fact<W, kTrack>(has ? cur : W(0), sm_kind, sm_masks, a.g.n_cos, a.g.rot_L,
+                                       a.g.rot_d, a.g.n_sites, a.g.n_perm, a.g.flip, full, best, gbest);
+        else
+            rep_search<W, kTrack>(has ? cur : W(0), sm_masks, a.g.n_perm, a.g.flip, full, best, gbest);
 
         if (has) {
             const int64_t j = find_index((uint64_t)best, a.ix);
@@ -226,11 +244,11 @@ __global__ void __launch_bounds__(kMvThreads) k_matvec(const MatvecArgs a)
     }
 }
 
-template <typename W, typename T, bool kC, bool kTrack, int NV>
+template <typename W, typename T, bool kC, bool kTrack, bool kFact, int NV>
 cudaError_t matvec_launch(const MatvecArgs &a, cudaStream_t stream)
 {
-    auto kern = k_matvec<W, T, kC, kTrack, NV>;
-    const size_t smem = matvec_smem_bytes<W, T, kTrack>(a.g, a.op);
+    auto kern = k_matvec<W, T, kC, kTrack, kFact, NV>;
+    const size_t smem = matvec_smem_bytes<W, T, kTrack, kFact>(a.g, a.op);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess)
         return e;
@@ -251,19 +269,26 @@ template <typename T, bool kC>
 cudaError_t matvec_dispatch_prec(const MatvecArgs &a, bool track, cudaStream_t stream)
 {
     const bool w32 = a.g.n_sites <= 32;
-#define ED_MV_NV(W, TR)                                                           \
+    const bool fact = a.g.fact != 0;
+#define ED_MV_NV(W, TR, FA)                                                       \
     do {                                                                          \
-        if (a.nvec == 1) return matvec_launch<W, T, kC, TR, 1>(a, stream);        \
-        if (a.nvec <= 4) return matvec_launch<W, T, kC, TR, 4>(a, stream);        \
-        if (a.nvec <= 8) return matvec_launch<W, T, kC, TR, 8>(a, stream);        \
-        return matvec_launch<W, T, kC, TR, 16>(a, stream);                        \
+        if (a.nvec == 1) return matvec_launch<W, T, kC, TR, FA, 1>(a, stream);    \
+        if (a.nvec <= 4) return matvec_launch<W, T, kC, TR, FA, 4>(a, stream);    \
+        if (a.nvec <= 8) return matvec_launch<W, T, kC, TR, FA, 8>(a, stream);    \
+        return matvec_launch<W, T, kC, TR, FA, 16>(a, stream);                    \
+    } while (0)
+#define ED_MV_FA(W, TR)                  \
+    do {                                 \
+        if (fact) ED_MV_NV(W, TR, true); \
+        ED_MV_NV(W, TR, false);          \
     } while (0)
     if (w32) {
-        if (track) ED_MV_NV(uint32_t, true);
-        ED_MV_NV(uint32_t, false);
+        if (track) ED_MV_FA(uint32_t, true);
+        ED_MV_FA(uint32_t, false);
     }
-    if (track) ED_MV_NV(uint64_t, true);
-    ED_MV_NV(uint64_t, false);
+    if (track) ED_MV_FA(uint64_t, true);
+    ED_MV_FA(uint64_t, false);
+#undef ED_MV_FA
 #undef ED_MV_NV
 }
 

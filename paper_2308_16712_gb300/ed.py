@@ -56,6 +56,8 @@ _SIGS = {
     "ed_lanczos": (_i32, [_P, _P, _P, _i32, _i32, ctypes.POINTER(_d), _P,
                           ctypes.POINTER(LanczosInfo), _P]),
     "edx_launch_count": (ctypes.c_ulonglong, []),
+    "edx_force_generic": (None, [_i32]),
+    "edx_basis_factored": (_i32, [_P, ctypes.POINTER(_i32), ctypes.POINTER(_i32), ctypes.POINTER(_i32)]),
 }
 for _name, (_res, _args) in _SIGS.items():
     if hasattr(_lib, _name):
@@ -98,7 +100,7 @@ class _DevArray:
 
     def __init__(self, ptr: int, n: int, typestr: str, owner):
         self.__cuda_array_interface__ = {"shape": (n,), "typestr": typestr,
-                                         "data": (ptr, True), "version": 3, "strides": None}
+                                         "data": (ptr, False), "version": 3, "strides": None}
         self._owner = owner
 
 
@@ -211,6 +213,19 @@ def matvec(op: Operator, basis: Basis, x, y, nvec: int = 1, stream=None):
 def launch_count() -> int:
     """Kernel launches the library has issued since it was loaded (diagnostics)."""
     return int(_lib.edx_launch_count())
+
+
+def force_generic(on: bool) -> None:
+    """Testing aid: use the generic Benes group search even where the factored
+    (rotation x coset) search applies.  Affects later launches and builds."""
+    _lib.edx_force_generic(1 if on else 0)
+
+
+def basis_factored(basis: Basis):
+    """(uses factored search, rotation order L, rotation step d, cosets)."""
+    L, d, c = _i32(), _i32(), _i32()
+    f = _lib.edx_basis_factored(basis.handle, ctypes.byref(L), ctypes.byref(d), ctypes.byref(c))
+    return bool(f == 1), L.value, d.value, c.value
 
 
 @dataclass

@@ -194,3 +194,29 @@ def test_argument_errors_before_any_launch(lib):
     sites[0] = [3, 3]
     assert lib.ed_operator_create(8, 1, co.ctypes.data_as(P), sites.ctypes.data_as(P),
                                   loc.ctypes.data_as(P), ctypes.byref(out)) == 1
+
+
+# ----------------------------------------------------------------------------
+# factored form of lattice groups (rotation subgroup x coset representatives)
+# ----------------------------------------------------------------------------
+def factorize(lib, perms):
+    perms = np.ascontiguousarray(np.asarray(perms, np.int32))
+    L, d = ctypes.c_int(), ctypes.c_int()
+    kinds = np.zeros(len(perms), np.uint8)
+    nc = lib.edx_factorize(perms.shape[1], perms.shape[0], perms.ctypes.data_as(ctypes.c_void_p),
+                           ctypes.byref(L), ctypes.byref(d), kinds.ctypes.data_as(ctypes.c_void_p))
+    return nc, L.value, d.value, list(kinds[:max(nc, 0)])
+
+
+def test_factorization_of_lattice_groups(lib):
+    assert factorize(lib, ei.ring_group(32, 0, +1)[0]) == (2, 32, 1, [0, 1])
+    assert factorize(lib, ei.ring_group(40, 0, +1)[0]) == (2, 40, 1, [0, 1])
+    assert factorize(lib, ei.ring_group(28, 3)[0]) == (1, 28, 1, [0])
+    nc, L, d, kinds = factorize(lib, ei.torus_group(6, 6)[0])
+    assert (nc, L, d) == (6, 6, 6) and kinds[0] == 0 and all(k == 2 for k in kinds[1:])
+    assert factorize(lib, ei.trivial_group(10)[0])[0] == 0
+    # the factored elements cover the group exactly once (checked through the
+    # rotation closure: cosets x L = |G|)
+    for p in (ei.ring_group(12, 0, -1)[0], ei.torus_group(3, 4)[0], ei.torus_group(4, 4)[0]):
+        nc, L, d, _ = factorize(lib, p)
+        assert nc * L == len(p)

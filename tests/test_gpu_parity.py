@@ -46,9 +46,23 @@ def make(case, with_oracle=True):
     return build_pair(n, n_up, z, p, c, opf(), with_oracle)
 
 
+@pytest.fixture(params=["factored", "generic"], autouse=True)
+def search_mode(request):
+    """Run every parity test with the factored (rotation x coset) group search
+    and again with the generic Benes search over every element."""
+    torch, ed = gpu()
+    ed.force_generic(request.param == "generic")
+    yield request.param
+    ed.force_generic(False)
+
+
 @pytest.mark.parametrize("case", SECTORS, ids=[s[0] for s in SECTORS])
-def test_basis_bit_exact(case):
+def test_basis_bit_exact(case, search_mode):
     S = make(case)
+    torch, ed = gpu()
+    fact, L, d, nc = ed.basis_factored(S["B"])
+    if case[0].startswith(("ring", "torus")) and search_mode == "factored":
+        assert fact and nc * L == len(case[4]()[0])
     st, nm = gpu_basis_numpy(S["B"])
     assert S["dim"] == len(S["st"]) == oracle.sector_dim(S["G"], case[2])
     assert np.array_equal(st, S["st"])
