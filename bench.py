@@ -246,26 +246,28 @@ def run_matvec_only(args, w):
 
 
 def search_ops_per_term(n, n_perm, flip, fact, rot_L, n_cos, kinds):
-    """INT32 operations of one representative search as the kernel runs it
-    (instruction-level count of the algorithm, not a measurement):
+    """INT32 operations of one representative search (real characters, so no
+    minimiser is tracked) as the kernel runs it -- an instruction-level count of
+    the algorithm, not a measurement.
     32-bit words: Benes stage = 2 shifts + 2 three-input logic ops (9 stages);
     rotation of the doubled word = 1 funnel shift (+1 mask op when n < 32);
-    spin-inversion candidate = 1 logic op; running minimum = 1 op per candidate.
-    64-bit words: each of those costs two 32-bit operations; the 64-bit
-    minimum costs 4 (2 compares, 2 selects); one incremental rotation costs 6."""
-    cand = 2 if flip else 1
+    running min = 1 op per candidate; with spin inversion the factored search
+    keeps a running max as well (1 op) and needs no per-candidate complement,
+    the generic one complements (1 op) and takes a second min (1 op).
+    64-bit words: shifts, logic ops, min and max cost two 32-bit operations
+    each (4 for a 64-bit min or max); an incremental rotation costs 6."""
     if n <= 32:
         benes, rev = 36, (1 if n == 32 else 2)
-        per_rot = (1 if n == 32 else 2) + cand * 1 + (1 if flip else 0)
-        per_perm = benes + cand * 1 + (1 if flip else 0)
+        per_rot = (1 if n == 32 else 2) + (2 if flip else 1)
+        per_perm = benes + (3 if flip else 1)
     else:
         benes, rev = 84, 4
-        per_rot = 6 + cand * 4 + (2 if flip else 0)
-        per_perm = benes + cand * 4 + (2 if flip else 0)
+        per_rot = 6 + (8 if flip else 4)
+        per_perm = benes + (2 + 8 if flip else 4)
     if not fact:
         return n_perm * per_perm
     head = sum({0: 0, 1: rev, 2: benes}[int(k)] for k in kinds)
-    return head + n_cos * rot_L * per_rot
+    return head + n_cos * rot_L * per_rot + (1 if flip else 0)
 
 
 def main():

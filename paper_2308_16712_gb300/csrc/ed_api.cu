@@ -390,10 +390,26 @@ ed_operator *build_operator_host(int n_sites, int n_terms, const double *coeff,
         worst += best;
     }
     op->max_offdiag = worst;
-    op->h_terms.resize(n_terms);
-    for (int t = 0; t < n_terms; ++t)
-        op->h_terms[t] = (uint32_t)sites[2 * t] | ((uint32_t)sites[2 * t + 1] << 8) |
-                         ((uint32_t)op->mat_of_term[t] << 16);
+    // rotation families: terms grouped by (matrix, (j - i) mod n); a site that
+    // occurs twice in one group opens another family of the same kind
+    std::map<std::pair<int, int>, std::vector<size_t>> open_fams;
+    for (int t = 0; t < n_terms; ++t) {
+        const int i = sites[2 * t], j = sites[2 * t + 1];
+        const int delta = ((j - i) % n_sites + n_sites) % n_sites;
+        auto &list = open_fams[{op->mat_of_term[t], delta}];
+        bool placed = false;
+        for (size_t f : list) {
+            if (!((op->h_fams[f].mask >> i) & 1ULL)) {
+                op->h_fams[f].mask |= 1ULL << i;
+                placed = true;
+                break;
+            }
+        }
+        if (!placed) {
+            list.push_back(op->h_fams.size());
+            op->h_fams.push_back(edk::OpFamily{1ULL << i, (uint32_t)op->mat_of_term[t], (uint32_t)delta});
+        }
+    }
     op->h_mats = std::move(md);
     op->h_matsf = std::move(mf);
     op->h_offmask = std::move(offmask);
@@ -402,13 +418,15 @@ ed_operator *build_operator_host(int n_sites, int n_terms, const double *coeff,
 
 edk::OpView op_view(const ed_operator *op)
 {
-    return edk::OpView{op->n_terms, op->n_mats, op->d_terms, op->d_mats, op->d_matsf,
+    return edk::OpView{(int)op->h_fams.size(), op->n_mats, op->d_fams, op->d_mats, op->d_matsf,
                        op->d_offmask};
 }
 
 }  // namespace
 
 namespace edk {
+
+OpView make_op_view(const ed_operator *op) { return op_view(op); }
 
 static std::atomic<unsigned long long> g_launches{0};
 void count_launch(unsigned n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
@@ -745,7 +763,7 @@ ed_status ed_operator_create(int n_sites, int n_terms, const double *coeff, cons
     ed_operator *op = build_operator_host(n_sites, n_terms, coeff, sites, local);
     if (!op)
         return ED_ERR_INVALID_ARG;
-    cudaError_t e = upload(&op->d_terms, op->h_terms.data(), op->h_terms.size());
+    cudaError_t e = upload(&op->d_fams, op->h_fams.data(), op->h_fams.size());
     if (e == cudaSuccess)
         e = upload(&op->d_mats, op->h_mats.data(), op->h_mats.size());
     if (e == cudaSuccess)
@@ -766,7 +784,7 @@ void ed_operator_destroy(ed_operator *op)
     if (!op)
         return;
     cudaDeviceSynchronize();
-    cudaFree(op->d_terms);
+    cudaFree(op->d_fams);
     cudaFree(op->d_mats);
     cudaFree(op->d_matsf);
     cudaFree(op->d_offmask);
@@ -867,6 +885,26 @@ int edx_terms_commute(int n_sites, int n_terms, const double *coeff, const int32
     if (!op)
         return -1;
     const int r = operator_is_symmetric(op, n_perm, perms, spin_inversion) ? 1 : 0;
+    delete op;
+    return r;
+}
+
+// Host-only test hook: number of rotation families the term list splits into
+// (-1 on invalid terms).
+int edx_operator_families(int n_sites, int n_terms, const double *coeff, const int32_t *sites,
+                          const double *local)
+{
+    if (n_sites < 1 || n_sites > 64 || n_terms < 1 || !coeff || !sites || !local)
+        return -1;
+    for (int t = 0; t < n_terms; ++t) {
+        const int i = sites[2 * t], j = sites[2 * t + 1];
+        if (i < 0 || j < 0 || i >= n_sites || j >= n_sites || i == j)
+            return -1;
+    }
+    ed_operator *op = build_operator_host(n_sites, n_terms, coeff, sites, local);
+    if (!op)
+        return -1;
+    const int r = (int)op->h_fams.size();
     delete op;
     return r;
 }

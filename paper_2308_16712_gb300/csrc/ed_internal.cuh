@@ -301,6 +301,17 @@ __device__ __forceinline__ void rep_search_fact(W s, const uint8_t *kinds, const
 // ---------------------------------------------------------------------------
 template <typename T> struct Cplx { T re, im; };
 
+// A "rotation family" of two-site terms: every site i in `mask` is coupled to
+// site (i + delta) mod n_sites by the same 4x4 matrix `mat`.  Any term list is
+// a union of such families (group the terms by matrix and by site offset), so
+// a row's local configurations on all bonds of a family come from one word
+// rotation and a few logic operations.
+struct OpFamily {
+    uint64_t mask;
+    uint32_t mat;
+    uint32_t delta;
+};
+
 template <typename T>
 __device__ __forceinline__ Cplx<T> cmul(Cplx<T> a, Cplx<T> b)
 {
@@ -354,12 +365,12 @@ struct ed_operator {
     int max_offdiag = 0;              // max off-diagonal entries one row can produce
     bool real = true;                 // every matrix entry real
     // host copies of the device tables
-    std::vector<uint32_t> h_terms;
+    std::vector<edk::OpFamily> h_fams;
     std::vector<double2> h_mats;
     std::vector<float2> h_matsf;
     std::vector<uint8_t> h_offmask;
     // device tables
-    uint32_t *d_terms = nullptr;      // n_terms: i | j << 8 | mat << 16
+    edk::OpFamily *d_fams = nullptr;  // rotation families of the terms
     double2 *d_mats = nullptr;        // n_mats x 16
     float2 *d_matsf = nullptr;
     uint8_t *d_offmask = nullptr;     // n_mats x 4: bit c' set if h[c'][c] != 0, c' != c

@@ -42,16 +42,17 @@ cudaError_t launch_index(const IndexView &ix, const uint64_t *query, int64_t *ou
 
 // ---- matvec (Sec. "Matrix-vector product") --------------------------------------
 struct OpView {
-    int n_terms;
+    int n_fam;
     int n_mats;
-    const uint32_t *terms;   // i | j << 8 | mat << 16
-    const double2 *mats;     // n_mats x 16
+    const OpFamily *fams;    // rotation families
+    const double2 *mats;     // n_mats x 16, coeff * h
     const float2 *matsf;
-    const uint8_t *offmask;  // n_mats x 4
+    const uint8_t *offmask;  // n_mats x 4: bit c' set if h[c'][c] != 0, c' != c
 };
 
 // Operator/basis compatibility check (n_sites, symmetry); cached per basis.
 ed_status check_pair(const ed_operator *op, const ed_basis *b);
+OpView make_op_view(const ed_operator *op);
 
 cudaError_t launch_matvec(const OpView &op, const GroupView &g, const IndexView &ix, bool track,
                           const void *x, void *y, int nvec, ed_dtype dtype, cudaStream_t stream);

@@ -445,7 +445,7 @@ ed_status run_lanczos(const ed_operator *op, const ed_basis *b, const void *x0, 
     const uint64_t n = b->dim;
     const bool f32 = mode == ED_LANCZOS_F32_MATVEC;
     const ed_dtype dt64 = kC ? ED_C128 : ED_F64, dt32 = kC ? ED_C64 : ED_F32;
-    const OpView ov{op->n_terms, op->n_mats, op->d_terms, op->d_mats, op->d_matsf, op->d_offmask};
+    const OpView ov = make_op_view(op);
     const GroupView gv = b->group_view();
     const IndexView iv = b->index_view();
     const bool track = !b->trivial_chars;

@@ -5,8 +5,10 @@
 // Work decomposition.  The grid is persistent; every warp owns a contiguous
 // block of rows and hands rows to its lanes on demand (ballot + popc), so a
 // lane that finishes a row takes the next one without waiting for the others.
-// A lane owns its row r: it loads r and n(r), forms the diagonal term, and then
-// walks the off-diagonal terms of H|r> one at a time.  All 32 lanes run the
+// A lane owns its row r: it loads r and n(r), forms the diagonal from the
+// local configurations of every bond family (one word rotation and four
+// popcounts per family), and then walks the off-diagonal terms of H|r> one at a
+// time (bit by bit through the family masks).  All 32 lanes run the
 // representative search of their current term in lockstep over the same group
 // element (the mask reads are shared-memory broadcasts), then each lane looks
 // the representative up in the sorted basis, gathers x at that index and
@@ -45,24 +47,94 @@ template <> __device__ __forceinline__ Cplx<float> load_cf<float>(const float2 *
 
 __host__ __device__ inline size_t align16(size_t v) { return (v + 15) & ~size_t(15); }
 
+// Shared-memory layout: masks | chi | families | matrices | offmask | coset kinds | sqrt tables
 template <typename W, typename T, bool kTrack, bool kFact>
-__host__ __device__ inline void matvec_smem_layout(const GroupView &g, const OpView &op, size_t off[6])
+__host__ __device__ inline void matvec_smem_layout(const GroupView &g, const OpView &op, size_t off[8])
 {
     const int nm = kFact ? g.n_cos : g.n_perm;
-    off[0] = 0;                                                            // masks
-    off[1] = align16(off[0] + (size_t)nm * kMaskStride * sizeof(W));       // chi
-    off[2] = align16(off[1] + (kTrack ? (size_t)g.order * sizeof(Cplx<T>) : 0)); // terms
-    off[3] = align16(off[2] + (size_t)op.n_terms * sizeof(uint32_t));     // mats
-    off[4] = align16(off[3] + (size_t)op.n_mats * 16 * sizeof(Cplx<T>));  // offmask
-    off[5] = align16(off[4] + (size_t)op.n_mats * 4);                     // coset kinds
+    off[0] = 0;
+    off[1] = align16(off[0] + (size_t)nm * kMaskStride * sizeof(W));
+    off[2] = align16(off[1] + (kTrack ? (size_t)g.order * sizeof(Cplx<T>) : 0));
+    off[3] = align16(off[2] + (size_t)op.n_fam * sizeof(OpFamily));
+    off[4] = align16(off[3] + (size_t)op.n_mats * 16 * sizeof(Cplx<T>));
+    off[5] = align16(off[4] + (size_t)op.n_mats * 4);
+    off[6] = align16(off[5] + (kFact ? (size_t)g.n_cos : 0));
+    off[7] = align16(off[6] + 2 * (size_t)(g.order + 1) * sizeof(T));
 }
 
 template <typename W, typename T, bool kTrack, bool kFact>
 __host__ __device__ inline size_t matvec_smem_bytes(const GroupView &g, const OpView &op)
 {
-    size_t off[6];
+    size_t off[8];
     matvec_smem_layout<W, T, kTrack, kFact>(g, op, off);
-    return align16(off[5] + (kFact ? (size_t)g.n_cos : 0));
+    return off[7];
+}
+
+// bit i of the result = bit (i + delta) mod n of s  (0 < delta < n)
+__device__ __forceinline__ uint32_t rot_down(uint32_t s, int delta, int n, uint32_t full)
+{
+    if (n == 32)
+        return __funnelshift_r(s, s, delta);
+    return ((s >> delta) | (s << (n - delta))) & full;
+}
+__device__ __forceinline__ uint64_t rot_down(uint64_t s, int delta, int n, uint64_t full)
+{
+    return ((s >> delta) | (s << (n - delta))) & full;
+}
+
+__device__ __forceinline__ int lowest_bit(uint32_t v) { return __ffs(v) - 1; }
+__device__ __forceinline__ int lowest_bit(uint64_t v) { return __ffsll((long long)v) - 1; }
+__device__ __forceinline__ int popc(uint32_t v) { return __popc(v); }
+__device__ __forceinline__ int popc(uint64_t v) { return __popcll((long long)v); }
+
+// Sites i of the family (mask M) whose bond (i, i+delta) is in local
+// configuration c = 2 s_i + s_{i+delta}; t = rot_down(s, delta).
+template <typename W>
+__device__ __forceinline__ W config_mask(W s, W t, W M, int c)
+{
+    const W a = (c & 2) ? s : ~s;
+    const W b = (c & 1) ? t : ~t;
+    return a & b & M;
+}
+
+// Minimum over the factored group without tracking the minimiser: for every
+// coset image h, the running min and max over its rotations; the spin-flipped
+// candidates q ^ full have their minimum at full ^ max(q).
+template <typename W>
+__device__ __forceinline__ W rep_min_fact(W s, const uint8_t *kinds, const W *masks, int n_cos, int L,
+                                          int d, int n, int flip, W full)
+{
+    W mn = ~W(0), mx = 0;
+    for (int c = 0; c < n_cos; ++c) {
+        const W h = coset_image(s, (int)kinds[c], masks + c * kMaskStride, n);
+        if constexpr (sizeof(W) == 4) {
+            if (n == 32) {
+#pragma unroll 8
+                for (int b = 0; b < L; ++b) {
+                    const uint32_t q = __funnelshift_l(h, h, b * d);
+                    mn = min(mn, q);
+                    mx = max(mx, q);
+                }
+            } else {
+                const uint32_t lo = h | (h << n), hi = h >> (32 - n);
+#pragma unroll 8
+                for (int b = 0; b < L; ++b) {
+                    const uint32_t q = __funnelshift_rc(lo, hi, n - b * d) & full;
+                    mn = min(mn, q);
+                    mx = max(mx, q);
+                }
+            }
+        } else {
+            W q = h;
+#pragma unroll 4
+            for (int b = 0; b < L; ++b) {
+                mn = min(mn, q);
+                mx = max(mx, q);
+                q = ((q << d) | (q >> (n - d))) & full;
+            }
+        }
+    }
+    return flip ? min(mn, (W)(mx ^ full)) : mn;
 }
 
 template <typename W, typename T, bool kC, bool kTrack, bool kFact, int NV>
@@ -70,14 +142,16 @@ __global__ void __launch_bounds__(kMvThreads) k_matvec(const MatvecArgs a)
 {
     using V = typename ValT<T, kC>::type;
     extern __shared__ __align__(16) unsigned char smem[];
-    size_t off[6];
+    size_t off[8];
     matvec_smem_layout<W, T, kTrack, kFact>(a.g, a.op, off);
     W *sm_masks = reinterpret_cast<W *>(smem + off[0]);
     Cplx<T> *sm_chi = reinterpret_cast<Cplx<T> *>(smem + off[1]);
-    uint32_t *sm_terms = reinterpret_cast<uint32_t *>(smem + off[2]);
+    OpFamily *sm_fam = reinterpret_cast<OpFamily *>(smem + off[2]);
     Cplx<T> *sm_mats = reinterpret_cast<Cplx<T> *>(smem + off[3]);
     uint8_t *sm_off = smem + off[4];
     uint8_t *sm_kind = smem + off[5];
+    T *sm_sq = reinterpret_cast<T *>(smem + off[6]);     // sqrt(k), k = 0..order
+    T *sm_isq = sm_sq + (a.g.order + 1);                  // 1/sqrt(k)
 
     {
         const int nm = kFact ? a.g.n_cos : a.g.n_perm;
@@ -103,8 +177,8 @@ __global__ void __launch_bounds__(kMvThreads) k_matvec(const MatvecArgs a)
                     sm_chi[e] = load_cf<T>(cf + e);
             }
         }
-        for (int e = threadIdx.x; e < a.op.n_terms; e += blockDim.x)
-            sm_terms[e] = a.op.terms[e];
+        for (int e = threadIdx.x; e < a.op.n_fam; e += blockDim.x)
+            sm_fam[e] = a.op.fams[e];
         for (int e = threadIdx.x; e < a.op.n_mats * 16; e += blockDim.x) {
             if constexpr (sizeof(T) == 8)
                 sm_mats[e] = load_c<T>(a.op.mats + e);
@@ -113,13 +187,18 @@ __global__ void __launch_bounds__(kMvThreads) k_matvec(const MatvecArgs a)
         }
         for (int e = threadIdx.x; e < a.op.n_mats * 4; e += blockDim.x)
             sm_off[e] = a.op.offmask[e];
+        for (int e = threadIdx.x; e <= a.g.order; e += blockDim.x) {
+            sm_sq[e] = sqrt((T)e);
+            sm_isq[e] = e ? T(1) / sqrt((T)e) : T(0);
+        }
     }
     __syncthreads();
 
     const V *__restrict__ x = reinterpret_cast<const V *>(a.x);
     V *__restrict__ y = reinterpret_cast<V *>(a.y);
     const int nvec = a.nvec;
-    const int n_terms = a.op.n_terms;
+    const int n_fam = a.op.n_fam;
+    const int n = a.g.n_sites;
     const uint64_t dim = a.ix.dim;
     const W full = (W)a.g.full;
     const unsigned kAll = 0xffffffffu;
@@ -134,30 +213,43 @@ __global__ void __launch_bounds__(kMvThreads) k_matvec(const MatvecArgs a)
 
     bool has = false;
     uint64_t row = 0;
-    W r = 0;
-    T nr = 1;
-    int t = -1, col = 0, si = 0, sj = 0, mid = 0, amp = 0;
-    uint32_t cmask = 0;
-    W cur = 0;
+    W r = 0, t = 0, fmask = 0, bits = 0, cur = 0;
+    T rinv = 1;
+    int f = 0, c = 0, i = 0, fdelta = 0, fmat = 0, amp = 0;
+    uint32_t cpm = 0;
     V acc[NV];
 
-    // next off-diagonal term of H|r>: sets cur (the produced state) and amp
+    // next off-diagonal term of H|r> in (family, configuration, site, target) order
     auto advance = [&]() -> bool {
-        while (cmask == 0) {
-            if (++t >= n_terms)
-                return false;
-            const uint32_t td = sm_terms[t];
-            si = td & 0xff;
-            sj = (td >> 8) & 0xff;
-            mid = td >> 16;
-            col = (int)(((r >> si) & 1) << 1 | ((r >> sj) & 1));
-            cmask = sm_off[mid * 4 + col];
+        while (true) {
+            if (cpm) {
+                const int cp = __ffs(cpm) - 1;
+                cpm &= cpm - 1;
+                const int fl = c ^ cp;
+                int j = i + fdelta;
+                j -= j >= n ? n : 0;
+                cur = r ^ (W((fl >> 1) & 1) << i) ^ (W(fl & 1) << j);
+                amp = fmat * 16 + cp * 4 + c;
+                return true;
+            }
+            if (bits) {
+                i = lowest_bit(bits);
+                bits &= bits - 1;
+                cpm = sm_off[fmat * 4 + c];
+                continue;
+            }
+            if (++c == 4) {
+                c = 0;
+                if (++f >= n_fam)
+                    return false;
+                const OpFamily fm = sm_fam[f];
+                fmask = (W)fm.mask;
+                fmat = (int)fm.mat;
+                fdelta = (int)fm.delta;
+                t = rot_down(r, fdelta, n, full);
+            }
+            bits = sm_off[fmat * 4 + c] ? config_mask(r, t, fmask, c) : W(0);
         }
-        const int cp = __ffs(cmask) - 1;
-        cmask &= cmask - 1;
-        cur = (r & ~((W(1) << si) | (W(1) << sj))) | (W(cp >> 1) << si) | (W(cp & 1) << sj);
-        amp = mid * 16 + cp * 4 + col;
-        return true;
     };
     auto store_row = [&]() {
 #pragma unroll
@@ -176,14 +268,19 @@ __global__ void __launch_bounds__(kMvThreads) k_matvec(const MatvecArgs a)
             if (!has && mine < row_end) {
                 row = mine;
                 r = (W)__ldg(a.ix.states + row);
-                nr = (T)__ldg(a.ix.norms + row);
+                rinv = sm_isq[__ldg(a.ix.norms + row)];
+                // diagonal: sum over families and configurations
                 Cplx<T> d = {T(0), T(0)};
-                for (int q = 0; q < n_terms; ++q) {
-                    const uint32_t td = sm_terms[q];
-                    const int c = (int)(((r >> (td & 0xff)) & 1) << 1 | ((r >> ((td >> 8) & 0xff)) & 1));
-                    const Cplx<T> h = sm_mats[(td >> 16) * 16 + c * 5];
-                    d.re += h.re;
-                    d.im += h.im;
+                for (int q = 0; q < n_fam; ++q) {
+                    const OpFamily fm = sm_fam[q];
+                    const W tq = rot_down(r, (int)fm.delta, n, full);
+#pragma unroll
+                    for (int cc = 0; cc < 4; ++cc) {
+                        const int cnt = popc(config_mask(r, tq, (W)fm.mask, cc));
+                        const Cplx<T> h = sm_mats[fm.mat * 16 + cc * 5];
+                        d.re += h.re * (T)cnt;
+                        d.im += h.im * (T)cnt;
+                    }
                 }
 #pragma unroll
                 for (int v = 0; v < NV; ++v) {
@@ -195,8 +292,18 @@ __global__ void __launch_bounds__(kMvThreads) k_matvec(const MatvecArgs a)
                             acc[v] = d.re * xv;
                     }
                 }
-                t = -1;
-                cmask = 0;
+                // first family
+                f = 0;
+                c = -1;
+                cpm = 0;
+                bits = 0;
+                {
+                    const OpFamily fm = sm_fam[0];
+                    fmask = (W)fm.mask;
+                    fmat = (int)fm.mat;
+                    fdelta = (int)fm.delta;
+                    t = rot_down(r, fdelta, n, full);
+                }
                 if (advance())
                     has = true;
                 else
@@ -207,17 +314,23 @@ __global__ void __launch_bounds__(kMvThreads) k_matvec(const MatvecArgs a)
             break;
 
         W best;
-        int gbest;
-        if (kFact)
-            rep_search_fact<W, kTrack>(has ? cur : W(0), sm_kind, sm_masks, a.g.n_cos, a.g.rot_L,
-                                       a.g.rot_d, a.g.n_sites, a.g.n_perm, a.g.flip, full, best, gbest);
-        else
-            rep_search<W, kTrack>(has ? cur : W(0), sm_masks, a.g.n_perm, a.g.flip, full, best, gbest);
+        int gbest = 0;
+        const W s = has ? cur : W(0);
+        if (kFact) {
+            if (kTrack)
+                rep_search_fact<W, true>(s, sm_kind, sm_masks, a.g.n_cos, a.g.rot_L, a.g.rot_d, n,
+                                         a.g.n_perm, a.g.flip, full, best, gbest);
+            else
+                best = rep_min_fact<W>(s, sm_kind, sm_masks, a.g.n_cos, a.g.rot_L, a.g.rot_d, n,
+                                       a.g.flip, full);
+        } else {
+            rep_search<W, kTrack>(s, sm_masks, a.g.n_perm, a.g.flip, full, best, gbest);
+        }
 
         if (has) {
             const int64_t j = find_index((uint64_t)best, a.ix);
             if (j >= 0) {
-                const T ratio = sqrt((T)__ldg(a.ix.norms + j) / nr);
+                const T ratio = sm_sq[__ldg(a.ix.norms + j)] * rinv;
                 const Cplx<T> h = sm_mats[amp];
                 Cplx<T> coef = {h.re * ratio, -h.im * ratio};  // conj(h) sqrt(n'/n)
                 if (kTrack)

@@ -220,3 +220,20 @@ def test_factorization_of_lattice_groups(lib):
     for p in (ei.ring_group(12, 0, -1)[0], ei.torus_group(3, 4)[0], ei.torus_group(4, 4)[0]):
         nc, L, d, _ = factorize(lib, p)
         assert nc * L == len(p)
+
+
+def families(lib, n, op):
+    args = [np.ascontiguousarray(op[k]) for k in ("coeff", "sites", "local")]
+    return lib.edx_operator_families(n, len(op["sites"]), *[a.ctypes.data_as(ctypes.c_void_p) for a in args])
+
+
+def test_operator_rotation_families(lib):
+    # a ring: one family (offset 1, every site); the 6x6 J1-J2 torus: nearest
+    # bonds at offsets 1 and 31 (row wrap) and 6, next-nearest at 7, 1, 31, 25
+    assert families(lib, 32, ei.heisenberg_ring(32)) == 1
+    assert families(lib, 36, ei.j1j2_torus(6, 6, 1.0, 0.5)) == 7
+    # a repeated bond opens a second family of the same kind
+    op = ei.heisenberg_ring(8)
+    for k in ("sites", "coeff", "local"):
+        op[k] = np.concatenate([op[k], op[k][:1]])
+    assert families(lib, 8, op) == 2
