@@ -123,6 +123,33 @@ ed_status ed_basis_index(const ed_basis *basis, const uint64_t *d_query, int64_t
 void ed_basis_destroy(ed_basis *basis);
 
 /*
+ * ed_basis_count_noalloc -- the sector dimension (the number of
+ * representatives ed_basis_build would keep), computed without allocating any
+ * device memory.  The paper has no counterpart: this entry point exists for
+ * callers that cannot call cudaMalloc -- an application whose memory pool or
+ * caching allocator already owns the device memory, or a latency-critical
+ * path on which cudaMalloc / cudaFree (which synchronise the device) are not
+ * allowed.
+ *
+ *   arguments   as ed_basis_build, with at most 512 lattice elements
+ *               (n_elems > 512 returns ED_ERR_INVALID_ARG: the scratch has a
+ *               fixed size)
+ *   dim_out     host, receives the dimension
+ *
+ * All scratch (group tables, per-chunk counts, scan offsets; about 3.2 MB) is
+ * one fixed device array inside the library, present on every device that
+ * loads it until the process exits.  The first call on a device looks up the
+ * array's device address (make that first call before any stream capture).
+ * Every call reuses the same array: calls that overlap on the GPU (different
+ * streams or host threads at once) race and must be serialised by the caller.
+ * The call enqueues on `stream` and synchronises it before returning.
+ * Errors: as ed_basis_build, plus ED_ERR_INVALID_ARG for n_elems > 512.
+ */
+ed_status ed_basis_count_noalloc(int n_sites, int n_up, int spin_inversion, int n_elems,
+                                 const int32_t *perms, const double *chars, void *stream,
+                                 uint64_t *dim_out);
+
+/*
  * ed_operator_create -- H = sum_t coeff_t * h_t acting on the site pair
  * (sites[2t], sites[2t+1]) (the analytic Hamiltonian the matrix elements are
  * generated from, Sec. "Matrix-vector product", getRow / getManyRows).

@@ -428,6 +428,54 @@ namespace edk {
 
 OpView make_op_view(const ed_operator *op) { return op_view(op); }
 
+// Validated host tables for counting a sector with the generic group search
+// (used by the allocation-free count entry point).
+ed_status count_tables_host(int n_sites, int n_up, int spin_inversion, int n_elems,
+                            const int32_t *perms, const double *chars,
+                            std::vector<uint32_t> &masks32, std::vector<uint64_t> &masks64,
+                            std::vector<uint32_t> &chi_one)
+{
+    if (!perms || !chars)
+        return ED_ERR_INVALID_ARG;
+    if (n_sites < 1 || n_sites > 64 || n_elems < 1 || n_elems > 1024)
+        return ED_ERR_INVALID_ARG;
+    if (n_up < -1 || n_up > n_sites || (n_up == -1 && n_sites > 40))
+        return ED_ERR_INVALID_ARG;
+    if (spin_inversion < -1 || spin_inversion > 1)
+        return ED_ERR_INVALID_ARG;
+    if (spin_inversion != 0 && n_up != -1 && 2 * n_up != n_sites)
+        return ED_ERR_INVALID_ARG;
+    const ed_status st = validate_group(n_sites, n_elems, perms, chars);
+    if (st != ED_OK)
+        return st;
+    const int order = n_elems * (spin_inversion ? 2 : 1);
+    chi_one.assign((order + 31) / 32, 0);
+    for (int g = 0; g < order; ++g) {
+        const int p = g % n_elems;
+        cplx c(chars[2 * p], chars[2 * p + 1]);
+        if (g >= n_elems)
+            c *= (double)spin_inversion;
+        if (std::abs(c - 1.0) < kChiTol)
+            chi_one[g / 32] |= 1u << (g % 32);
+    }
+    masks32.assign((size_t)n_elems * kMaskStride, 0);
+    masks64.assign((size_t)n_elems * kMaskStride, 0);
+    for (int g = 0; g < n_elems; ++g) {
+        const int32_t *pm = perms + (size_t)g * n_sites;
+        if (n_sites <= 32) {
+            auto m = benes_masks(5, n_sites, pm);
+            for (int k = 0; k < 9; ++k)
+                masks32[(size_t)g * kMaskStride + k] = (uint32_t)m[k];
+        }
+        auto m = benes_masks(6, n_sites, pm);
+        for (int k = 0; k < 11; ++k)
+            masks64[(size_t)g * kMaskStride + k] = m[k];
+    }
+    return ED_OK;
+}
+
+uint64_t binomial_host(int n, int k) { return binomial(n, k); }
+
 static std::atomic<unsigned long long> g_launches{0};
 void count_launch(unsigned n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 

@@ -50,6 +50,13 @@ struct OpView {
     const uint8_t *offmask;  // n_mats x 4: bit c' set if h[c'][c] != 0, c' != c
 };
 
+// Host tables (generic group search) for counting a sector; validates the group.
+ed_status count_tables_host(int n_sites, int n_up, int spin_inversion, int n_elems,
+                            const int32_t *perms, const double *chars,
+                            std::vector<uint32_t> &masks32, std::vector<uint64_t> &masks64,
+                            std::vector<uint32_t> &chi_one);
+uint64_t binomial_host(int n, int k);
+
 // Operator/basis compatibility check (n_sites, symmetry); cached per basis.
 ed_status check_pair(const ed_operator *op, const ed_basis *b);
 OpView make_op_view(const ed_operator *op);

@@ -55,6 +55,7 @@ _SIGS = {
     "ed_matvec": (_i32, [_P, _P, _P, _P, _i32, _i32, _P]),
     "ed_lanczos": (_i32, [_P, _P, _P, _i32, _i32, ctypes.POINTER(_d), _P,
                           ctypes.POINTER(LanczosInfo), _P]),
+    "ed_basis_count_noalloc": (_i32, [_i32, _i32, _i32, _i32, _P, _P, _P, ctypes.POINTER(_u64)]),
     "edx_launch_count": (ctypes.c_ulonglong, []),
     "edx_force_generic": (None, [_i32]),
     "edx_basis_factored": (_i32, [_P, ctypes.POINTER(_i32), ctypes.POINTER(_i32), ctypes.POINTER(_i32)]),
@@ -144,6 +145,19 @@ def basis_build(n_sites: int, n_up: int, spin_inversion: int, perms, chars, stre
                                perms.ctypes.data_as(_P), chars.ctypes.data_as(_P), _stream(stream),
                                ctypes.byref(out)), "ed_basis_build")
     return Basis(out, n_sites)
+
+
+def basis_count_noalloc(n_sites: int, n_up: int, spin_inversion: int, perms, chars,
+                        stream=None) -> int:
+    """Sector dimension without any device allocation (fixed in-library scratch;
+    overlapping calls race)."""
+    perms = _host(perms, np.int32).reshape(-1, n_sites)
+    chars = _host(chars, np.float64).reshape(-1, 2)
+    d = ctypes.c_uint64()
+    _check(_lib.ed_basis_count_noalloc(n_sites, n_up, spin_inversion, len(perms),
+                                       perms.ctypes.data_as(_P), chars.ctypes.data_as(_P),
+                                       _stream(stream), ctypes.byref(d)), "ed_basis_count_noalloc")
+    return d.value
 
 
 def basis_size(basis: Basis) -> int:
