@@ -250,6 +250,7 @@ void free_basis(ed_basis *b)
     cudaFree(b->d_fchi_one);
     cudaFree(b->d_states);
     cudaFree(b->d_norms);
+    cudaFree(b->d_keys);
     cudaFree(b->d_tab);
     cudaFree(b->d_masks32);
     cudaFree(b->d_masks64);
@@ -524,7 +525,7 @@ edk::GroupView ed_basis::group_view() const
 
 edk::IndexView ed_basis::index_view() const
 {
-    return edk::IndexView{d_states, d_norms, dim, d_tab, tab_size, e_lo, e_hi, mbits};
+    return edk::IndexView{d_states, d_norms, d_keys, dim, d_tab, tab_size, e_lo, e_hi, mbits};
 }
 
 // ---------------------------------------------------------------------------
@@ -710,6 +711,10 @@ ed_status ed_basis_build(int n_sites, int n_up, int spin_inversion, int n_elems,
     ED_B_TRY(cudaMalloc(&b->d_states, std::max<uint64_t>(dim, 1) * sizeof(uint64_t)));
     ED_B_TRY(cudaMalloc(&b->d_norms, std::max<uint64_t>(dim, 1) * sizeof(uint16_t)));
     ED_B_TRY(edk::launch_enum_write(plan, gv, d_offsets, b->d_states, b->d_norms, stream));
+    if (n_sites <= 48) {
+        ED_B_TRY(cudaMalloc(&b->d_keys, std::max<uint64_t>(dim, 1) * sizeof(uint64_t)));
+        ED_B_TRY(edk::launch_pack_keys(b->d_states, b->d_norms, dim, b->d_keys, stream));
+    }
 
     // prefix table over the bit-length range of the basis
     uint64_t ends[2] = {0, 0};

@@ -296,6 +296,13 @@ __global__ void k_prefix_table(IndexView ix, uint32_t *tab)
     tab[t] = (uint32_t)lo;
 }
 
+__global__ void k_pack_keys(const uint64_t *states, const uint16_t *norms, uint64_t dim, uint64_t *keys)
+{
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < dim;
+         i += (uint64_t)gridDim.x * blockDim.x)
+        keys[i] = (states[i] << 16) | norms[i];
+}
+
 __global__ void k_check_sorted(const uint64_t *states, uint64_t dim, int *flag)
 {
     for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x + 1; i < dim;
@@ -346,6 +353,16 @@ cudaError_t launch_prefix_table(const IndexView &ix, uint32_t *tab, cudaStream_t
 {
     const uint64_t n = ix.tab_size + 1;
     k_prefix_table<<<(unsigned)((n + 255) / 256), 256, 0, stream>>>(ix, tab); count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pack_keys(const uint64_t *states, const uint16_t *norms, uint64_t dim, uint64_t *keys,
+                             cudaStream_t stream)
+{
+    if (dim == 0)
+        return cudaSuccess;
+    const uint64_t blocks = std::min<uint64_t>((dim + 255) / 256, 65536);
+    k_pack_keys<<<(unsigned)blocks, 256, 0, stream>>>(states, norms, dim, keys); count_launch();
     return cudaGetLastError();
 }
 

@@ -110,6 +110,7 @@ struct GroupView {
 struct IndexView {
     const uint64_t *states;  // ascending basis
     const uint16_t *norms;   // orbit norms
+    const uint64_t *keys;    // state << 16 | norm (n_sites <= 48), else null
     uint64_t dim;
     const uint32_t *tab;     // prefix offsets, tab_size + 1 entries
     uint64_t tab_size;
@@ -150,6 +151,35 @@ __device__ __forceinline__ int64_t find_index(uint64_t s, const IndexView &ix)
             hi = mid;
     }
     return (lo < end && __ldg(ix.states + lo) == s) ? (int64_t)lo : -1;
+}
+
+// stateToIndex over the packed keys (state << 16 | norm): the probe that finds
+// the state also delivers its orbit norm.  Indices are 32-bit (dim < 2^32).
+__device__ __forceinline__ bool find_key(uint64_t s, const IndexView &ix, uint32_t &idx, uint32_t &norm)
+{
+    const int bl = 64 - __clzll((long long)s);
+    if (bl < ix.e_lo || bl > ix.e_hi)
+        return false;
+    const uint64_t t = prefix_key(s, ix.e_lo, ix.mbits);
+    uint32_t lo = __ldg(ix.tab + t);
+    uint32_t hi = __ldg(ix.tab + t + 1);
+    const uint32_t end = hi;
+    const uint64_t target = s << 16;
+    while (lo < hi) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (__ldg(ix.keys + mid) < target)
+            lo = mid + 1;
+        else
+            hi = mid;
+    }
+    if (lo >= end)
+        return false;
+    const uint64_t k = __ldg(ix.keys + lo);
+    if ((k >> 16) != s)
+        return false;
+    idx = lo;
+    norm = (uint32_t)(k & 0xffff);
+    return true;
 }
 
 __device__ __forceinline__ bool chi_is_one(const uint32_t *bits, int g)
@@ -335,6 +365,7 @@ struct ed_basis {
     // device arrays
     uint64_t *d_states = nullptr;
     uint16_t *d_norms = nullptr;
+    uint64_t *d_keys = nullptr;  // state << 16 | norm, n_sites <= 48
     uint32_t *d_tab = nullptr;
     uint32_t *d_masks32 = nullptr;
     uint64_t *d_masks64 = nullptr;

@@ -2,9 +2,10 @@
 // (Sec. "Matrix-vector product": y_i = sum_j H_ij x_j with getRow and
 // stateToIndex), instantiated per precision in the ed_matvec_*.cu units.
 //
-// Work decomposition.  The grid is persistent; every warp owns a contiguous
-// block of rows and hands rows to its lanes on demand (ballot + popc), so a
-// lane that finishes a row takes the next one without waiting for the others.
+// Work decomposition.  The grid is persistent; rows are dealt to warps in
+// tiles of 32 (round-robin), and each warp hands its rows to its lanes on
+// demand (ballot + popc), so a lane that finishes a row takes the next one
+// without waiting for the others.
 // A lane owns its row r: it loads r and n(r), forms the diagonal from the
 // local configurations of every bond family (one word rotation and four
 // popcounts per family), and then walks the off-diagonal terms of H|r> one at a
@@ -204,12 +205,15 @@ __global__ void __launch_bounds__(kMvThreads) k_matvec(const MatvecArgs a)
     const unsigned kAll = 0xffffffffu;
     const int lane = threadIdx.x & 31;
     const unsigned lanes_below = (1u << lane) - 1u;
+    // Rows are dealt in tiles of 32 consecutive rows, round-robin over the
+    // warps of the grid: warp w takes tiles w, w + nw, w + 2 nw, ...  (the term
+    // count of a row varies slowly along the sorted basis, so contiguous blocks
+    // per warp would be unbalanced).  p counts the rows this warp has taken.
     const uint64_t gw = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
-    const uint64_t per = (dim + nw - 1) / nw;
-    const uint64_t row_begin = min(dim, gw * per);
-    const uint64_t row_end = min(dim, row_begin + per);
-    uint64_t next = row_begin;  // warp-uniform
+    auto row_of = [&](uint64_t p) { return ((p >> 5) * nw + gw) * 32 + (p & 31); };
+    uint64_t next = 0;  // warp-uniform
+    const bool packed = a.ix.keys != nullptr;
 
     bool has = false;
     uint64_t row = 0;
@@ -261,14 +265,20 @@ __global__ void __launch_bounds__(kMvThreads) k_matvec(const MatvecArgs a)
     while (true) {
         while (true) {
             const unsigned need = __ballot_sync(kAll, !has);
-            if (need == 0 || next >= row_end)
+            if (need == 0 || row_of(next) >= dim)
                 break;
-            const uint64_t mine = next + __popc(need & lanes_below);
+            const uint64_t mine = row_of(next + __popc(need & lanes_below));
             next += __popc(need);
-            if (!has && mine < row_end) {
+            if (!has && mine < dim) {
                 row = mine;
-                r = (W)__ldg(a.ix.states + row);
-                rinv = sm_isq[__ldg(a.ix.norms + row)];
+                if (packed) {
+                    const uint64_t k = __ldg(a.ix.keys + row);
+                    r = (W)(k >> 16);
+                    rinv = sm_isq[k & 0xffff];
+                } else {
+                    r = (W)__ldg(a.ix.states + row);
+                    rinv = sm_isq[__ldg(a.ix.norms + row)];
+                }
                 // diagonal: sum over families and configurations
                 Cplx<T> d = {T(0), T(0)};
                 for (int q = 0; q < n_fam; ++q) {
@@ -328,9 +338,21 @@ __global__ void __launch_bounds__(kMvThreads) k_matvec(const MatvecArgs a)
         }
 
         if (has) {
-            const int64_t j = find_index((uint64_t)best, a.ix);
-            if (j >= 0) {
-                const T ratio = sm_sq[__ldg(a.ix.norms + j)] * rinv;
+            uint32_t jj = 0, nj = 0;
+            bool found;
+            if (packed) {
+                found = find_key((uint64_t)best, a.ix, jj, nj);
+            } else {
+                const int64_t j64 = find_index((uint64_t)best, a.ix);
+                found = j64 >= 0;
+                if (found) {
+                    jj = (uint32_t)j64;
+                    nj = __ldg(a.ix.norms + j64);
+                }
+            }
+            if (found) {
+                const uint64_t j = jj;
+                const T ratio = sm_sq[nj] * rinv;
                 const Cplx<T> h = sm_mats[amp];
                 Cplx<T> coef = {h.re * ratio, -h.im * ratio};  // conj(h) sqrt(n'/n)
                 if (kTrack)
