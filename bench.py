@@ -426,6 +426,7 @@ def main():
         "nonzeros_per_s": value * nnz_row if nnz_row else None,
         "nnz_per_row": nnz_row,
         "generated_terms_per_row": t_gen,
+        "prefix_table": dict(zip(("entries", "largest_bucket", "probe_steps"), ed.basis_table(B))),
         "matvec_kernel": mv,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_int, "unit": "TOP/s",
                      "frac": achieved / peak_int, "traffic": None,

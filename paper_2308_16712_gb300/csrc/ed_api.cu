@@ -525,7 +525,7 @@ edk::GroupView ed_basis::group_view() const
 
 edk::IndexView ed_basis::index_view() const
 {
-    return edk::IndexView{d_states, d_norms, d_keys, dim, d_tab, tab_size, e_lo, e_hi, mbits};
+    return edk::IndexView{d_states, d_norms, d_keys, dim, d_tab, tab_size, e_lo, e_hi, mbits, probe_iters};
 }
 
 // ---------------------------------------------------------------------------
@@ -728,25 +728,33 @@ ed_status ed_basis_build(int n_sites, int n_up, int spin_inversion, int n_elems,
     b->e_hi = bitlen(ends[1]);
     const int n_exp = b->e_hi - b->e_lo + 1;
     int mb = 0;
-    while (mb < 26 && ((uint64_t)n_exp << (mb + 1)) * 4 <= std::max<uint64_t>(dim, 1))
+    while (mb < 26 && ((uint64_t)n_exp << (mb + 1)) * 2 <= std::max<uint64_t>(dim, 1))
         ++mb;
     b->mbits = mb;
     b->tab_size = (uint64_t)n_exp << mb;
     ED_B_TRY(cudaMalloc(&b->d_tab, (b->tab_size + 1) * sizeof(uint32_t)));
     ED_B_TRY(edk::launch_prefix_table(b->index_view(), b->d_tab, stream));
-    ED_B_TRY(cudaMalloc(&d_flag, sizeof(int)));
-    ED_B_TRY(cudaMemsetAsync(d_flag, 0, sizeof(int), stream));
+    ED_B_TRY(cudaMalloc(&d_flag, 2 * sizeof(int)));
+    ED_B_TRY(cudaMemsetAsync(d_flag, 0, 2 * sizeof(int), stream));
     ED_B_TRY(edk::launch_check_sorted(b->d_states, dim, d_flag, stream));
-    int flag = 0;
-    ED_B_TRY(cudaMemcpyAsync(&flag, d_flag, sizeof(int), cudaMemcpyDeviceToHost, stream));
+    ED_B_TRY(edk::launch_max_bucket(b->d_tab, b->tab_size, reinterpret_cast<uint32_t *>(d_flag + 1), stream));
+    int flag[2] = {0, 0};
+    ED_B_TRY(cudaMemcpyAsync(flag, d_flag, 2 * sizeof(int), cudaMemcpyDeviceToHost, stream));
     ED_B_TRY(cudaStreamSynchronize(stream));
+    b->max_bucket = (uint32_t)flag[1];
+    {
+        int k = 1;  // steps that reduce the largest bucket to one entry, plus the final probe
+        while ((1u << (k - 1)) < std::max<uint32_t>(b->max_bucket, 1))
+            ++k;
+        b->probe_iters = k;
+    }
     cudaFree(d_counts);
     cudaFree(d_offsets);
     cudaFree(d_tmp);
     cudaFree(d_binom);
     cudaFree(d_flag);
 #undef ED_B_TRY
-    if (flag) {
+    if (flag[0]) {
         free_basis(b);
         return ED_ERR_INTERNAL;
     }
@@ -892,6 +900,18 @@ int edx_factorize(int n, int ne, const int32_t *perms, int *rot_L, int *rot_d, u
     if (kinds_out)
         std::copy(F.kind.begin(), F.kind.end(), kinds_out);
     return (int)F.rep.size();
+}
+
+// Diagnostics hook: prefix-table shape of a basis (entries, largest bucket,
+// probe steps of the index search).
+int edx_basis_table(const ed_basis *b, uint64_t *tab_size, uint32_t *max_bucket, int *probe_iters)
+{
+    if (!b)
+        return -1;
+    if (tab_size) *tab_size = b->tab_size;
+    if (max_bucket) *max_bucket = b->max_bucket;
+    if (probe_iters) *probe_iters = b->probe_iters;
+    return 0;
 }
 
 // Diagnostics hook: whether a basis uses the factored search, and its shape.

@@ -296,6 +296,18 @@ __global__ void k_prefix_table(IndexView ix, uint32_t *tab)
     tab[t] = (uint32_t)lo;
 }
 
+__global__ void k_max_bucket(const uint32_t *tab, uint64_t tab_size, uint32_t *out)
+{
+    uint32_t m = 0;
+    for (uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; t < tab_size;
+         t += (uint64_t)gridDim.x * blockDim.x)
+        m = max(m, tab[t + 1] - tab[t]);
+    for (int o = 16; o > 0; o >>= 1)
+        m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0)
+        atomicMax(out, m);
+}
+
 __global__ void k_pack_keys(const uint64_t *states, const uint16_t *norms, uint64_t dim, uint64_t *keys)
 {
     for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < dim;
@@ -353,6 +365,13 @@ cudaError_t launch_prefix_table(const IndexView &ix, uint32_t *tab, cudaStream_t
 {
     const uint64_t n = ix.tab_size + 1;
     k_prefix_table<<<(unsigned)((n + 255) / 256), 256, 0, stream>>>(ix, tab); count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_max_bucket(const uint32_t *tab, uint64_t tab_size, uint32_t *out, cudaStream_t stream)
+{
+    const uint64_t blocks = std::max<uint64_t>(1, std::min<uint64_t>((tab_size + 255) / 256, 4096));
+    k_max_bucket<<<(unsigned)blocks, 256, 0, stream>>>(tab, tab_size, out); count_launch();
     return cudaGetLastError();
 }
 

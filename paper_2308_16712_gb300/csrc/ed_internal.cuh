@@ -116,6 +116,7 @@ struct IndexView {
     uint64_t tab_size;
     int e_lo, e_hi;          // bit-length range covered by the table
     int mbits;               // mantissa bits of the table key
+    int probe_iters;         // halving steps that reduce the largest bucket to one entry, + 1
 };
 
 // Monotone bucket key of a state: (bit length - e_lo, next mbits bits below the
@@ -163,21 +164,21 @@ __device__ __forceinline__ bool find_key(uint64_t s, const IndexView &ix, uint32
     const uint64_t t = prefix_key(s, ix.e_lo, ix.mbits);
     uint32_t lo = __ldg(ix.tab + t);
     uint32_t hi = __ldg(ix.tab + t + 1);
-    const uint32_t end = hi;
-    const uint64_t target = s << 16;
-    while (lo < hi) {
-        const uint32_t mid = (lo + hi) >> 1;
-        if (__ldg(ix.keys + mid) < target)
-            lo = mid + 1;
-        else
-            hi = mid;
+    // Branch-free search for the last key <= (s << 16 | 0xffff) in the bucket,
+    // with the same number of steps in every lane (no divergence).  An empty
+    // bucket probes a neighbouring element, which cannot match.
+    uint32_t base = min(lo, (uint32_t)(ix.dim - 1));
+    uint32_t len = max(hi - lo, 1u);
+    const uint64_t target = (s << 16) | 0xffffULL;
+    for (int k = 0; k < ix.probe_iters; ++k) {
+        const uint32_t half = len >> 1;
+        base = (__ldg(ix.keys + base + half) <= target) ? base + half : base;
+        len -= half;
     }
-    if (lo >= end)
-        return false;
-    const uint64_t k = __ldg(ix.keys + lo);
+    const uint64_t k = __ldg(ix.keys + base);
     if ((k >> 16) != s)
         return false;
-    idx = lo;
+    idx = base;
     norm = (uint32_t)(k & 0xffff);
     return true;
 }
@@ -383,6 +384,8 @@ struct ed_basis {
     uint32_t *d_fchi_one = nullptr;
     uint64_t tab_size = 0;
     int e_lo = 0, e_hi = 0, mbits = 0;
+    uint32_t max_bucket = 0;
+    int probe_iters = 1;
 
     edk::GroupView group_view() const;
     edk::IndexView index_view() const;

@@ -33,6 +33,8 @@ cudaError_t launch_scan(const uint32_t *counts, uint64_t n, uint64_t *offsets, u
                         cudaStream_t stream);
 // Prefix table over the ascending basis.
 cudaError_t launch_prefix_table(const IndexView &ix, uint32_t *tab, cudaStream_t stream);
+// *out = max over buckets of tab[t+1] - tab[t] (*out must start at 0)
+cudaError_t launch_max_bucket(const uint32_t *tab, uint64_t tab_size, uint32_t *out, cudaStream_t stream);
 // keys[i] = states[i] << 16 | norms[i]
 cudaError_t launch_pack_keys(const uint64_t *states, const uint16_t *norms, uint64_t dim, uint64_t *keys,
                              cudaStream_t stream);

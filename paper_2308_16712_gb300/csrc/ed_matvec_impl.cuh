@@ -26,6 +26,15 @@
 namespace edk {
 
 constexpr int kMvThreads = 256;
+// Resident blocks per SM requested from the compiler: the single-vector
+// kernels fit 48 registers (40 warps per SM); the accumulators of wide block
+// vectors need more registers and get fewer blocks.
+template <typename T, bool kC, int NV>
+constexpr int mv_min_blocks()
+{
+    constexpr int acc_regs = NV * (kC ? 2 : 1) * (int)(sizeof(T) / 4);
+    return acc_regs <= 4 ? 5 : (acc_regs <= 16 ? 3 : 2);
+}
 
 struct MatvecArgs {
     OpView op;
@@ -98,6 +107,38 @@ __device__ __forceinline__ W config_mask(W s, W t, W M, int c)
     return a & b & M;
 }
 
+// min and max over the rotations of h (n-bit word held doubled in lo:hi),
+// four independent chains per statistic (rotations b = 0,1,2,3 mod 4).
+template <bool kFullWord>
+__device__ __forceinline__ void rot_minmax32(uint32_t lo, uint32_t hi, int L, int d, int n, uint32_t msk,
+                                             uint32_t &mn, uint32_t &mx)
+{
+    uint32_t m0 = ~0u, m1 = ~0u, m2 = ~0u, m3 = ~0u, x0 = 0, x1 = 0, x2 = 0, x3 = 0;
+    auto rot = [&](int k) {
+        const uint32_t q = __funnelshift_rc(lo, hi, n - k);
+        return kFullWord ? q : (q & msk);
+    };
+    int b = 0;
+    for (; b + 4 <= L; b += 4) {
+        const uint32_t q0 = rot(b * d), q1 = rot((b + 1) * d), q2 = rot((b + 2) * d), q3 = rot((b + 3) * d);
+        m0 = min(m0, q0);
+        m1 = min(m1, q1);
+        m2 = min(m2, q2);
+        m3 = min(m3, q3);
+        x0 = max(x0, q0);
+        x1 = max(x1, q1);
+        x2 = max(x2, q2);
+        x3 = max(x3, q3);
+    }
+    for (; b < L; ++b) {
+        const uint32_t q = rot(b * d);
+        m0 = min(m0, q);
+        x0 = max(x0, q);
+    }
+    mn = min(mn, min(min(m0, m1), min(m2, m3)));
+    mx = max(mx, max(max(x0, x1), max(x2, x3)));
+}
+
 // Minimum over the factored group without tracking the minimiser: for every
 // coset image h, the running min and max over its rotations; the spin-flipped
 // candidates q ^ full have their minimum at full ^ max(q).
@@ -109,22 +150,10 @@ __device__ __forceinline__ W rep_min_fact(W s, const uint8_t *kinds, const W *ma
     for (int c = 0; c < n_cos; ++c) {
         const W h = coset_image(s, (int)kinds[c], masks + c * kMaskStride, n);
         if constexpr (sizeof(W) == 4) {
-            if (n == 32) {
-#pragma unroll 8
-                for (int b = 0; b < L; ++b) {
-                    const uint32_t q = __funnelshift_l(h, h, b * d);
-                    mn = min(mn, q);
-                    mx = max(mx, q);
-                }
-            } else {
-                const uint32_t lo = h | (h << n), hi = h >> (32 - n);
-#pragma unroll 8
-                for (int b = 0; b < L; ++b) {
-                    const uint32_t q = __funnelshift_rc(lo, hi, n - b * d) & full;
-                    mn = min(mn, q);
-                    mx = max(mx, q);
-                }
-            }
+            if (n == 32)
+                rot_minmax32<true>(h, h, L, d, 32, ~0u, mn, mx);
+            else
+                rot_minmax32<false>(h | (h << n), h >> (32 - n), L, d, n, full, mn, mx);
         } else {
             W q = h;
 #pragma unroll 4
@@ -139,7 +168,7 @@ __device__ __forceinline__ W rep_min_fact(W s, const uint8_t *kinds, const W *ma
 }
 
 template <typename W, typename T, bool kC, bool kTrack, bool kFact, int NV>
-__global__ void __launch_bounds__(kMvThreads) k_matvec(const MatvecArgs a)
+__global__ void __launch_bounds__(kMvThreads, (mv_min_blocks<T, kC, NV>())) k_matvec(const MatvecArgs a)
 {
     using V = typename ValT<T, kC>::type;
     extern __shared__ __align__(16) unsigned char smem[];
@@ -262,11 +291,10 @@ __global__ void __launch_bounds__(kMvThreads) k_matvec(const MatvecArgs a)
                 y[row * nvec + v] = acc[v];
     };
 
+    bool rows_left = row_of(0) < dim;
     while (true) {
-        while (true) {
-            const unsigned need = __ballot_sync(kAll, !has);
-            if (need == 0 || row_of(next) >= dim)
-                break;
+        unsigned need = __ballot_sync(kAll, !has);
+        while (need != 0 && rows_left) {
             const uint64_t mine = row_of(next + __popc(need & lanes_below));
             next += __popc(need);
             if (!has && mine < dim) {
@@ -319,9 +347,11 @@ __global__ void __launch_bounds__(kMvThreads) k_matvec(const MatvecArgs a)
                 else
                     store_row();
             }
+            rows_left = row_of(next) < dim;
+            need = __ballot_sync(kAll, !has);
         }
-        if (__ballot_sync(kAll, has) == 0)
-            break;
+        if (need == kAll)
+            break;  // no lane holds a row and none are left
 
         W best;
         int gbest = 0;

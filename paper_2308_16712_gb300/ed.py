@@ -58,6 +58,7 @@ _SIGS = {
     "ed_basis_count_noalloc": (_i32, [_i32, _i32, _i32, _i32, _P, _P, _P, ctypes.POINTER(_u64)]),
     "edx_launch_count": (ctypes.c_ulonglong, []),
     "edx_force_generic": (None, [_i32]),
+    "edx_basis_table": (_i32, [_P, ctypes.POINTER(_u64), ctypes.POINTER(ctypes.c_uint32), ctypes.POINTER(_i32)]),
     "edx_basis_factored": (_i32, [_P, ctypes.POINTER(_i32), ctypes.POINTER(_i32), ctypes.POINTER(_i32)]),
 }
 for _name, (_res, _args) in _SIGS.items():
@@ -233,6 +234,13 @@ def force_generic(on: bool) -> None:
     """Testing aid: use the generic Benes group search even where the factored
     (rotation x coset) search applies.  Affects later launches and builds."""
     _lib.edx_force_generic(1 if on else 0)
+
+
+def basis_table(basis: Basis):
+    """(prefix-table entries, largest bucket, probe steps of the index search)."""
+    t, m, k = _u64(), ctypes.c_uint32(), _i32()
+    _lib.edx_basis_table(basis.handle, ctypes.byref(t), ctypes.byref(m), ctypes.byref(k))
+    return t.value, m.value, k.value
 
 
 def basis_factored(basis: Basis):
