@@ -427,6 +427,8 @@ def main():
         "nnz_per_row": nnz_row,
         "generated_terms_per_row": t_gen,
         "prefix_table": dict(zip(("entries", "largest_bucket", "probe_steps"), ed.basis_table(B))),
+        "hash_index": dict(zip(("present", "log2_buckets", "largest_bucket", "wide_entries"),
+                               ed.basis_hash(B))),
         "matvec_kernel": mv,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_int, "unit": "TOP/s",
                      "frac": achieved / peak_int, "traffic": None,

@@ -237,6 +237,7 @@ bool factorize(int n, int ne, const int32_t *perms, Factorization &F)
 }
 
 bool g_force_generic = false;
+bool g_force_prefix = false;
 
 void free_basis(ed_basis *b)
 {
@@ -251,6 +252,8 @@ void free_basis(ed_basis *b)
     cudaFree(b->d_states);
     cudaFree(b->d_norms);
     cudaFree(b->d_keys);
+    cudaFree(b->d_htab);
+    cudaFree(b->d_hent);
     cudaFree(b->d_tab);
     cudaFree(b->d_masks32);
     cudaFree(b->d_masks64);
@@ -525,7 +528,14 @@ edk::GroupView ed_basis::group_view() const
 
 edk::IndexView ed_basis::index_view() const
 {
-    return edk::IndexView{d_states, d_norms, d_keys, dim, d_tab, tab_size, e_lo, e_hi, mbits, probe_iters};
+    edk::IndexView v{d_states, d_norms, d_keys, dim, d_tab, tab_size, e_lo, e_hi, mbits, probe_iters};
+    const bool use_hash = d_htab && !g_force_prefix;
+    v.htab = use_hash ? d_htab : nullptr;
+    v.hent = use_hash ? d_hent : nullptr;
+    v.hbits = hbits;
+    v.hwide = hwide;
+    v.norm_bits = norm_bits;
+    return v;
 }
 
 // ---------------------------------------------------------------------------
@@ -742,6 +752,61 @@ ed_status ed_basis_build(int n_sites, int n_up, int spin_inversion, int n_elems,
     ED_B_TRY(cudaMemcpyAsync(flag, d_flag, 2 * sizeof(int), cudaMemcpyDeviceToHost, stream));
     ED_B_TRY(cudaStreamSynchronize(stream));
     b->max_bucket = (uint32_t)flag[1];
+    if (dim) {
+        // hash index: 2^hbits >= dim buckets (about one state per bucket)
+        int hb = 1;
+        while ((1ULL << hb) < dim)
+            ++hb;
+        b->hbits = hb;
+        int nb = 1;
+        while ((1 << nb) <= b->order)
+            ++nb;
+        int ib = 1;
+        while ((1ULL << ib) < dim)
+            ++ib;
+        b->norm_bits = nb;
+        b->hwide = !(n_sites <= 32 && ib + nb <= 32);
+        const uint64_t T = 1ULL << hb;
+        uint32_t *d_hcount = nullptr;
+        uint64_t *d_hoff = nullptr, *d_htmp = nullptr;
+        cudaError_t he = cudaMalloc(&d_hcount, T * sizeof(uint32_t));
+        if (he == cudaSuccess)
+            he = cudaMalloc(&d_hoff, (T + 1) * sizeof(uint64_t));
+        if (he == cudaSuccess)
+            he = cudaMalloc(&d_htmp, edk::scan_tmp_words(T) * sizeof(uint64_t));
+        if (he == cudaSuccess)
+            he = cudaMalloc(&b->d_htab, (T + 1) * sizeof(uint32_t));
+        if (he == cudaSuccess)
+            he = cudaMalloc(&b->d_hent, dim * (b->hwide ? 16 : 8));
+        if (he == cudaSuccess)
+            he = cudaMemsetAsync(d_hcount, 0, T * sizeof(uint32_t), stream);
+        if (he == cudaSuccess)
+            he = edk::launch_hash_count(b->d_states, dim, hb, d_hcount, stream);
+        if (he == cudaSuccess)
+            he = edk::launch_scan(d_hcount, T, d_hoff, d_htmp, stream);
+        if (he == cudaSuccess)
+            he = edk::launch_offsets_to_u32(d_hoff, T + 1, b->d_htab, stream);
+        if (he == cudaSuccess)  // reuse the count array as the fill cursor
+            he = cudaMemcpyAsync(d_hcount, b->d_htab, T * sizeof(uint32_t), cudaMemcpyDeviceToDevice, stream);
+        if (he == cudaSuccess)
+            he = edk::launch_hash_fill(b->d_states, b->d_norms, dim, hb, d_hcount, b->d_hent, b->hwide,
+                                       b->norm_bits, stream);
+        uint32_t hmax = 0;
+        uint32_t *d_hmax = reinterpret_cast<uint32_t *>(d_flag);
+        if (he == cudaSuccess)
+            he = cudaMemsetAsync(d_hmax, 0, sizeof(uint32_t), stream);
+        if (he == cudaSuccess)
+            he = edk::launch_max_bucket(b->d_htab, T, d_hmax, stream);
+        if (he == cudaSuccess)
+            he = cudaMemcpyAsync(&hmax, d_hmax, sizeof(uint32_t), cudaMemcpyDeviceToHost, stream);
+        if (he == cudaSuccess)
+            he = cudaStreamSynchronize(stream);
+        cudaFree(d_hcount);
+        cudaFree(d_hoff);
+        cudaFree(d_htmp);
+        ED_B_TRY(he);
+        b->hash_max_bucket = hmax;
+    }
     {
         int k = 1;  // steps that reduce the largest bucket to one entry, plus the final probe
         while ((1u << (k - 1)) < std::max<uint32_t>(b->max_bucket, 1))
@@ -900,6 +965,21 @@ int edx_factorize(int n, int ne, const int32_t *perms, int *rot_L, int *rot_d, u
     if (kinds_out)
         std::copy(F.kind.begin(), F.kind.end(), kinds_out);
     return (int)F.rep.size();
+}
+
+// Test hook: 1 = the matvec finds indices through the prefix table and binary
+// search even where the hash index exists.  Affects later launches.
+void edx_force_prefix_search(int on) { g_force_prefix = on != 0; }
+
+// Diagnostics hook: largest bucket of the hash index and its entry width.
+int edx_basis_hash(const ed_basis *b, int *hbits, uint32_t *max_bucket, int *wide)
+{
+    if (!b)
+        return -1;
+    if (hbits) *hbits = b->hbits;
+    if (max_bucket) *max_bucket = b->hash_max_bucket;
+    if (wide) *wide = b->hwide;
+    return b->d_htab ? 1 : 0;
 }
 
 // Diagnostics hook: prefix-table shape of a basis (entries, largest bucket,

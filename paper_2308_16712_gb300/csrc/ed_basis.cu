@@ -296,6 +296,38 @@ __global__ void k_prefix_table(IndexView ix, uint32_t *tab)
     tab[t] = (uint32_t)lo;
 }
 
+__global__ void k_hash_count(const uint64_t *states, uint64_t dim, int hbits, uint32_t *counts)
+{
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < dim;
+         i += (uint64_t)gridDim.x * blockDim.x)
+        atomicAdd(counts + hash_bucket(states[i], hbits), 1u);
+}
+
+__global__ void k_offsets_to_u32(const uint64_t *offsets, uint64_t n, uint32_t *out)
+{
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (uint64_t)gridDim.x * blockDim.x)
+        out[i] = (uint32_t)offsets[i];
+}
+
+// The order of entries inside a bucket depends on atomic timing; lookups
+// compare states, so the result of a lookup does not.
+__global__ void k_hash_fill(const uint64_t *states, const uint16_t *norms, uint64_t dim, int hbits,
+                            uint32_t *cursor, void *entries, int wide, int norm_bits)
+{
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < dim;
+         i += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t s = states[i];
+        const uint32_t pos = atomicAdd(cursor + hash_bucket(s, hbits), 1u);
+        if (wide)
+            reinterpret_cast<ulonglong2 *>(entries)[pos] =
+                make_ulonglong2(s, (uint64_t)i | ((uint64_t)norms[i] << 32));
+        else
+            reinterpret_cast<uint2 *>(entries)[pos] =
+                make_uint2((uint32_t)s, ((uint32_t)i << norm_bits) | norms[i]);
+    }
+}
+
 __global__ void k_max_bucket(const uint32_t *tab, uint64_t tab_size, uint32_t *out)
 {
     uint32_t m = 0;
@@ -365,6 +397,37 @@ cudaError_t launch_prefix_table(const IndexView &ix, uint32_t *tab, cudaStream_t
 {
     const uint64_t n = ix.tab_size + 1;
     k_prefix_table<<<(unsigned)((n + 255) / 256), 256, 0, stream>>>(ix, tab); count_launch();
+    return cudaGetLastError();
+}
+
+static unsigned grid_for(uint64_t n)
+{
+    return (unsigned)std::max<uint64_t>(1, std::min<uint64_t>((n + 255) / 256, 65536));
+}
+
+cudaError_t launch_hash_count(const uint64_t *states, uint64_t dim, int hbits, uint32_t *counts,
+                              cudaStream_t stream)
+{
+    if (!dim)
+        return cudaSuccess;
+    k_hash_count<<<grid_for(dim), 256, 0, stream>>>(states, dim, hbits, counts); count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_offsets_to_u32(const uint64_t *offsets, uint64_t n, uint32_t *out, cudaStream_t stream)
+{
+    k_offsets_to_u32<<<grid_for(n), 256, 0, stream>>>(offsets, n, out); count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_hash_fill(const uint64_t *states, const uint16_t *norms, uint64_t dim, int hbits,
+                             uint32_t *cursor, void *entries, int wide, int norm_bits,
+                             cudaStream_t stream)
+{
+    if (!dim)
+        return cudaSuccess;
+    k_hash_fill<<<grid_for(dim), 256, 0, stream>>>(states, norms, dim, hbits, cursor, entries, wide,
+                                                    norm_bits); count_launch();
     return cudaGetLastError();
 }
 

@@ -117,7 +117,49 @@ struct IndexView {
     int e_lo, e_hi;          // bit-length range covered by the table
     int mbits;               // mantissa bits of the table key
     int probe_iters;         // halving steps that reduce the largest bucket to one entry, + 1
+    // hash index: bucket b = hash(state) holds entries hent[htab[b] .. htab[b+1])
+    const uint32_t *htab;    // 2^hbits + 1 offsets (null: use the prefix table)
+    const void *hent;        // entries: 8 bytes (state:32 | packed index,norm:32) or 16 bytes
+    int hbits;               // log2 of the bucket count
+    int hwide;               // 1: 16-byte entries {state, index | norm << 32}
+    int norm_bits;           // 8-byte entries: low norm_bits of the packed word hold the norm
 };
+
+__host__ __device__ __forceinline__ uint32_t hash_bucket(uint64_t s, int hbits)
+{
+    return (uint32_t)((s * 0x9E3779B97F4A7C15ULL) >> (64 - hbits));
+}
+
+// stateToIndex through the hash index: scans the state's bucket (about one
+// entry on average; the entries of a bucket are contiguous).
+__device__ __forceinline__ bool find_hashed(uint64_t s, const IndexView &ix, uint32_t &idx, uint32_t &norm)
+{
+    const uint32_t b = hash_bucket(s, ix.hbits);
+    uint32_t e = __ldg(ix.htab + b);
+    const uint32_t end = __ldg(ix.htab + b + 1);
+    if (ix.hwide) {
+        const ulonglong2 *ent = reinterpret_cast<const ulonglong2 *>(ix.hent);
+        for (; e < end; ++e) {
+            const ulonglong2 v = __ldg(ent + e);
+            if (v.x == s) {
+                idx = (uint32_t)v.y;
+                norm = (uint32_t)(v.y >> 32);
+                return true;
+            }
+        }
+    } else {
+        const uint2 *ent = reinterpret_cast<const uint2 *>(ix.hent);
+        for (; e < end; ++e) {
+            const uint2 v = __ldg(ent + e);
+            if (v.x == (uint32_t)s) {
+                idx = v.y >> ix.norm_bits;
+                norm = v.y & ((1u << ix.norm_bits) - 1u);
+                return true;
+            }
+        }
+    }
+    return false;
+}
 
 // Monotone bucket key of a state: (bit length - e_lo, next mbits bits below the
 // leading one).  Ascending states give non-decreasing keys.
@@ -164,21 +206,21 @@ __device__ __forceinline__ bool find_key(uint64_t s, const IndexView &ix, uint32
     const uint64_t t = prefix_key(s, ix.e_lo, ix.mbits);
     uint32_t lo = __ldg(ix.tab + t);
     uint32_t hi = __ldg(ix.tab + t + 1);
-    // Branch-free search for the last key <= (s << 16 | 0xffff) in the bucket,
-    // with the same number of steps in every lane (no divergence).  An empty
-    // bucket probes a neighbouring element, which cannot match.
-    uint32_t base = min(lo, (uint32_t)(ix.dim - 1));
-    uint32_t len = max(hi - lo, 1u);
-    const uint64_t target = (s << 16) | 0xffffULL;
-    for (int k = 0; k < ix.probe_iters; ++k) {
-        const uint32_t half = len >> 1;
-        base = (__ldg(ix.keys + base + half) <= target) ? base + half : base;
-        len -= half;
+    const uint32_t end = hi;
+    const uint64_t target = s << 16;
+    while (lo < hi) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (__ldg(ix.keys + mid) < target)
+            lo = mid + 1;
+        else
+            hi = mid;
     }
-    const uint64_t k = __ldg(ix.keys + base);
+    if (lo >= end)
+        return false;
+    const uint64_t k = __ldg(ix.keys + lo);
     if ((k >> 16) != s)
         return false;
-    idx = base;
+    idx = lo;
     norm = (uint32_t)(k & 0xffff);
     return true;
 }
@@ -386,6 +428,11 @@ struct ed_basis {
     int e_lo = 0, e_hi = 0, mbits = 0;
     uint32_t max_bucket = 0;
     int probe_iters = 1;
+    // hash index
+    uint32_t *d_htab = nullptr;
+    void *d_hent = nullptr;
+    int hbits = 0, hwide = 0, norm_bits = 0;
+    uint32_t hash_max_bucket = 0;
 
     edk::GroupView group_view() const;
     edk::IndexView index_view() const;

@@ -33,6 +33,14 @@ cudaError_t launch_scan(const uint32_t *counts, uint64_t n, uint64_t *offsets, u
                         cudaStream_t stream);
 // Prefix table over the ascending basis.
 cudaError_t launch_prefix_table(const IndexView &ix, uint32_t *tab, cudaStream_t stream);
+// Hash index build: counts[b] += 1 for every state's bucket (counts zeroed),
+// then (after an exclusive scan into offsets) entries scattered into buckets.
+cudaError_t launch_hash_count(const uint64_t *states, uint64_t dim, int hbits, uint32_t *counts,
+                              cudaStream_t stream);
+cudaError_t launch_offsets_to_u32(const uint64_t *offsets, uint64_t n, uint32_t *out, cudaStream_t stream);
+cudaError_t launch_hash_fill(const uint64_t *states, const uint16_t *norms, uint64_t dim, int hbits,
+                             uint32_t *cursor, void *entries, int wide, int norm_bits,
+                             cudaStream_t stream);
 // *out = max over buckets of tab[t+1] - tab[t] (*out must start at 0)
 cudaError_t launch_max_bucket(const uint32_t *tab, uint64_t tab_size, uint32_t *out, cudaStream_t stream);
 // keys[i] = states[i] << 16 | norms[i]

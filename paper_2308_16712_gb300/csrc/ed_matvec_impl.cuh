@@ -370,7 +370,9 @@ __global__ void __launch_bounds__(kMvThreads, (mv_min_blocks<T, kC, NV>())) k_ma
         if (has) {
             uint32_t jj = 0, nj = 0;
             bool found;
-            if (packed) {
+            if (a.ix.htab) {
+                found = find_hashed((uint64_t)best, a.ix, jj, nj);
+            } else if (packed) {
                 found = find_key((uint64_t)best, a.ix, jj, nj);
             } else {
                 const int64_t j64 = find_index((uint64_t)best, a.ix);

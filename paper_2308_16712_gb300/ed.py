@@ -58,6 +58,8 @@ _SIGS = {
     "ed_basis_count_noalloc": (_i32, [_i32, _i32, _i32, _i32, _P, _P, _P, ctypes.POINTER(_u64)]),
     "edx_launch_count": (ctypes.c_ulonglong, []),
     "edx_force_generic": (None, [_i32]),
+    "edx_force_prefix_search": (None, [_i32]),
+    "edx_basis_hash": (_i32, [_P, ctypes.POINTER(_i32), ctypes.POINTER(ctypes.c_uint32), ctypes.POINTER(_i32)]),
     "edx_basis_table": (_i32, [_P, ctypes.POINTER(_u64), ctypes.POINTER(ctypes.c_uint32), ctypes.POINTER(_i32)]),
     "edx_basis_factored": (_i32, [_P, ctypes.POINTER(_i32), ctypes.POINTER(_i32), ctypes.POINTER(_i32)]),
 }
@@ -234,6 +236,19 @@ def force_generic(on: bool) -> None:
     """Testing aid: use the generic Benes group search even where the factored
     (rotation x coset) search applies.  Affects later launches and builds."""
     _lib.edx_force_generic(1 if on else 0)
+
+
+def force_prefix_search(on: bool) -> None:
+    """Testing aid: find indices through the prefix table and binary search even
+    where the hash index exists.  Affects later launches."""
+    _lib.edx_force_prefix_search(1 if on else 0)
+
+
+def basis_hash(basis: Basis):
+    """(hash index present, log2 buckets, largest bucket, 16-byte entries)."""
+    hb, m, wd = _i32(), ctypes.c_uint32(), _i32()
+    r = _lib.edx_basis_hash(basis.handle, ctypes.byref(hb), ctypes.byref(m), ctypes.byref(wd))
+    return bool(r == 1), hb.value, m.value, bool(wd.value)
 
 
 def basis_table(basis: Basis):

@@ -46,14 +46,17 @@ def make(case, with_oracle=True):
     return build_pair(n, n_up, z, p, c, opf(), with_oracle)
 
 
-@pytest.fixture(params=["factored", "generic"], autouse=True)
+@pytest.fixture(params=["factored", "generic", "prefix"], autouse=True)
 def search_mode(request):
-    """Run every parity test with the factored (rotation x coset) group search
-    and again with the generic Benes search over every element."""
+    """Run every parity test three times: factored (rotation x coset) group
+    search with the hash index; generic Benes search over every element with
+    the hash index; factored search with the prefix-table binary search."""
     torch, ed = gpu()
     ed.force_generic(request.param == "generic")
+    ed.force_prefix_search(request.param == "prefix")
     yield request.param
     ed.force_generic(False)
+    ed.force_prefix_search(False)
 
 
 @pytest.mark.parametrize("case", SECTORS, ids=[s[0] for s in SECTORS])
@@ -63,6 +66,10 @@ def test_basis_bit_exact(case, search_mode):
     fact, L, d, nc = ed.basis_factored(S["B"])
     if case[0].startswith(("ring", "torus")) and search_mode == "factored":
         assert fact and nc * L == len(case[4]()[0])
+    has_hash, hbits, hmax, wide = ed.basis_hash(S["B"])
+    assert has_hash == (S["dim"] > 0)
+    if S["dim"]:
+        assert (1 << hbits) >= S["dim"] and hmax <= 16
     st, nm = gpu_basis_numpy(S["B"])
     assert S["dim"] == len(S["st"]) == oracle.sector_dim(S["G"], case[2])
     assert np.array_equal(st, S["st"])
