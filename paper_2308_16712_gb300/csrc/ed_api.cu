@@ -753,9 +753,9 @@ ed_status ed_basis_build(int n_sites, int n_up, int spin_inversion, int n_elems,
     ED_B_TRY(cudaStreamSynchronize(stream));
     b->max_bucket = (uint32_t)flag[1];
     if (dim) {
-        // hash index: 2^hbits >= dim buckets (about one state per bucket)
+        // hash index: 2^hbits >= dim / 2 buckets (one to two states per bucket)
         int hb = 1;
-        while ((1ULL << hb) < dim)
+        while ((2ULL << hb) < dim)
             ++hb;
         b->hbits = hb;
         int nb = 1;

@@ -177,7 +177,7 @@ __host__ __device__ __forceinline__ uint64_t prefix_key(uint64_t s, int e_lo, in
 }
 
 // "stateToIndex": position of s in the ascending basis or -1.
-__device__ __forceinline__ int64_t find_index(uint64_t s, const IndexView &ix)
+static __device__ __noinline__ int64_t find_index(uint64_t s, const IndexView &ix)
 {
     const int bl = 64 - __clzll((long long)s);
     if (bl < ix.e_lo || bl > ix.e_hi)
@@ -198,7 +198,7 @@ __device__ __forceinline__ int64_t find_index(uint64_t s, const IndexView &ix)
 
 // stateToIndex over the packed keys (state << 16 | norm): the probe that finds
 // the state also delivers its orbit norm.  Indices are 32-bit (dim < 2^32).
-__device__ __forceinline__ bool find_key(uint64_t s, const IndexView &ix, uint32_t &idx, uint32_t &norm)
+static __device__ __noinline__ bool find_key(uint64_t s, const IndexView &ix, uint32_t &idx, uint32_t &norm)
 {
     const int bl = 64 - __clzll((long long)s);
     if (bl < ix.e_lo || bl > ix.e_hi)

@@ -26,15 +26,8 @@
 namespace edk {
 
 constexpr int kMvThreads = 256;
-// Resident blocks per SM requested from the compiler: the single-vector
-// kernels fit 48 registers (40 warps per SM); the accumulators of wide block
-// vectors need more registers and get fewer blocks.
-template <typename T, bool kC, int NV>
-constexpr int mv_min_blocks()
-{
-    constexpr int acc_regs = NV * (kC ? 2 : 1) * (int)(sizeof(T) / 4);
-    return acc_regs <= 4 ? 5 : (acc_regs <= 16 ? 3 : 2);
-}
+// The register budget is left to the compiler: capping it for more resident
+// warps cost more (spills, longer dependency chains) than it gained.
 
 struct MatvecArgs {
     OpView op;
@@ -56,6 +49,18 @@ template <typename T> __device__ __forceinline__ Cplx<T> load_cf(const float2 *p
 template <> __device__ __forceinline__ Cplx<float> load_cf<float>(const float2 *p) { return {p->x, p->y}; }
 
 __host__ __device__ inline size_t align16(size_t v) { return (v + 15) & ~size_t(15); }
+
+// streaming stores of y (written once, not re-read by this kernel)
+__device__ __forceinline__ void store_cs(float *p, float v) { __stcs(p, v); }
+__device__ __forceinline__ void store_cs(double *p, double v) { __stcs(p, v); }
+__device__ __forceinline__ void store_cs(Cplx<float> *p, Cplx<float> v)
+{
+    __stcs(reinterpret_cast<float2 *>(p), make_float2(v.re, v.im));
+}
+__device__ __forceinline__ void store_cs(Cplx<double> *p, Cplx<double> v)
+{
+    __stcs(reinterpret_cast<double2 *>(p), make_double2(v.re, v.im));
+}
 
 // Shared-memory layout: masks | chi | families | matrices | offmask | coset kinds | sqrt tables
 template <typename W, typename T, bool kTrack, bool kFact>
@@ -107,36 +112,53 @@ __device__ __forceinline__ W config_mask(W s, W t, W M, int c)
     return a & b & M;
 }
 
-// min and max over the rotations of h (n-bit word held doubled in lo:hi),
-// four independent chains per statistic (rotations b = 0,1,2,3 mod 4).
-template <bool kFullWord>
-__device__ __forceinline__ void rot_minmax32(uint32_t lo, uint32_t hi, int L, int d, int n, uint32_t msk,
-                                             uint32_t &mn, uint32_t &mx)
+// min and max over the rotations of the n-bit word h (n <= 32).
+// Rotation step 1 (every ring translation): the loop is unrolled over the 32
+// possible amounts so that each rotation is one funnel shift by an immediate
+// of the doubled word aligned to bit 32; amounts beyond n are skipped by a
+// warp-uniform predicate.  Other steps use run-time shift amounts.
+__device__ __forceinline__ void rot_minmax32(uint32_t h, int L, int d, int n, uint32_t full, uint32_t &mn,
+                                             uint32_t &mx)
 {
-    uint32_t m0 = ~0u, m1 = ~0u, m2 = ~0u, m3 = ~0u, x0 = 0, x1 = 0, x2 = 0, x3 = 0;
-    auto rot = [&](int k) {
-        const uint32_t q = __funnelshift_rc(lo, hi, n - k);
-        return kFullWord ? q : (q & msk);
-    };
-    int b = 0;
-    for (; b + 4 <= L; b += 4) {
-        const uint32_t q0 = rot(b * d), q1 = rot((b + 1) * d), q2 = rot((b + 2) * d), q3 = rot((b + 3) * d);
-        m0 = min(m0, q0);
-        m1 = min(m1, q1);
-        m2 = min(m2, q2);
-        m3 = min(m3, q3);
-        x0 = max(x0, q0);
-        x1 = max(x1, q1);
-        x2 = max(x2, q2);
-        x3 = max(x3, q3);
+    uint32_t m0 = ~0u, m1 = ~0u, x0 = 0, x1 = 0;
+    if (d == 1 && n == 32) {
+#pragma unroll
+        for (int b = 0; b < 32; b += 2) {
+            const uint32_t q0 = __funnelshift_l(h, h, b);
+            const uint32_t q1 = __funnelshift_l(h, h, b + 1);
+            m0 = min(m0, q0);
+            x0 = max(x0, q0);
+            m1 = min(m1, q1);
+            x1 = max(x1, q1);
+        }
+    } else if (d == 1) {
+        // (h | h << n) << (32 - n) as a 64-bit word hi:lo; rotation by b is
+        // bits [32 - b, 64 - b) masked to n bits
+        const uint64_t e = ((uint64_t)h | ((uint64_t)h << n)) << (32 - n);
+        const uint32_t lo = (uint32_t)e, hi = (uint32_t)(e >> 32);
+#pragma unroll
+        for (int b = 0; b < 32; b += 2) {
+            if (b < L) {
+                const uint32_t q0 = __funnelshift_r(lo, hi, 32 - b) & full;
+                m0 = min(m0, q0);
+                x0 = max(x0, q0);
+            }
+            if (b + 1 < L) {
+                const uint32_t q1 = __funnelshift_r(lo, hi, 31 - b) & full;
+                m1 = min(m1, q1);
+                x1 = max(x1, q1);
+            }
+        }
+    } else {
+        const uint32_t lo = h | (h << n), hi = h >> (32 - n);
+        for (int b = 0; b < L; ++b) {
+            const uint32_t q = __funnelshift_rc(lo, hi, n - b * d) & full;
+            m0 = min(m0, q);
+            x0 = max(x0, q);
+        }
     }
-    for (; b < L; ++b) {
-        const uint32_t q = rot(b * d);
-        m0 = min(m0, q);
-        x0 = max(x0, q);
-    }
-    mn = min(mn, min(min(m0, m1), min(m2, m3)));
-    mx = max(mx, max(max(x0, x1), max(x2, x3)));
+    mn = min(mn, min(m0, m1));
+    mx = max(mx, max(x0, x1));
 }
 
 // Minimum over the factored group without tracking the minimiser: for every
@@ -150,10 +172,7 @@ __device__ __forceinline__ W rep_min_fact(W s, const uint8_t *kinds, const W *ma
     for (int c = 0; c < n_cos; ++c) {
         const W h = coset_image(s, (int)kinds[c], masks + c * kMaskStride, n);
         if constexpr (sizeof(W) == 4) {
-            if (n == 32)
-                rot_minmax32<true>(h, h, L, d, 32, ~0u, mn, mx);
-            else
-                rot_minmax32<false>(h | (h << n), h >> (32 - n), L, d, n, full, mn, mx);
+            rot_minmax32(h, L, d, n, full, mn, mx);
         } else {
             W q = h;
 #pragma unroll 4
@@ -168,7 +187,7 @@ __device__ __forceinline__ W rep_min_fact(W s, const uint8_t *kinds, const W *ma
 }
 
 template <typename W, typename T, bool kC, bool kTrack, bool kFact, int NV>
-__global__ void __launch_bounds__(kMvThreads, (mv_min_blocks<T, kC, NV>())) k_matvec(const MatvecArgs a)
+__global__ void __launch_bounds__(kMvThreads) k_matvec(const MatvecArgs a)
 {
     using V = typename ValT<T, kC>::type;
     extern __shared__ __align__(16) unsigned char smem[];
@@ -288,7 +307,7 @@ __global__ void __launch_bounds__(kMvThreads, (mv_min_blocks<T, kC, NV>())) k_ma
 #pragma unroll
         for (int v = 0; v < NV; ++v)
             if (v < nvec)
-                y[row * nvec + v] = acc[v];
+                store_cs(y + row * nvec + v, acc[v]);
     };
 
     bool rows_left = row_of(0) < dim;
@@ -300,7 +319,7 @@ __global__ void __launch_bounds__(kMvThreads, (mv_min_blocks<T, kC, NV>())) k_ma
             if (!has && mine < dim) {
                 row = mine;
                 if (packed) {
-                    const uint64_t k = __ldg(a.ix.keys + row);
+                    const uint64_t k = __ldcs(a.ix.keys + row);  // streamed once: evict first
                     r = (W)(k >> 16);
                     rinv = sm_isq[k & 0xffff];
                 } else {
