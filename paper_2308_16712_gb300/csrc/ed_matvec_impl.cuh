@@ -139,7 +139,7 @@ __device__ __forceinline__ void rot_minmax32(uint32_t h, int L, int d, int n, ui
 #pragma unroll
         for (int b = 0; b < 32; b += 2) {
             if (b < L) {
-                const uint32_t q0 = __funnelshift_r(lo, hi, 32 - b) & full;
+                const uint32_t q0 = __funnelshift_rc(lo, hi, 32 - b) & full;  // clamps: b = 0 gives hi
                 m0 = min(m0, q0);
                 x0 = max(x0, q0);
             }
