@@ -69,7 +69,7 @@ def test_basis_bit_exact(case, search_mode):
     has_hash, hbits, hmax, wide = ed.basis_hash(S["B"])
     assert has_hash == (S["dim"] > 0)
     if S["dim"]:
-        assert (1 << hbits) >= S["dim"] and hmax <= 16
+        assert (2 << hbits) >= S["dim"] and hmax <= 16
     st, nm = gpu_basis_numpy(S["B"])
     assert S["dim"] == len(S["st"]) == oracle.sector_dim(S["G"], case[2])
     assert np.array_equal(st, S["st"])
