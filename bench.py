@@ -270,6 +270,29 @@ def search_ops_per_term(n, n_perm, flip, fact, rot_L, n_cos, kinds):
     return head + n_cos * rot_L * per_rot + (1 if flip else 0)
 
 
+def run_one_step(args, w):
+    import torch
+    from paper_2308_16712_gb300 import ed
+    n, op = w["n_sites"], w["op"]
+    O = ed.operator_create(n, op["sites"], op["coeff"], op["local"])
+    x0 = None
+    marks = []
+    for rep in range(2):
+        t0 = time.perf_counter()
+        launches0 = ed.launch_count()
+        B = ed.basis_build(n, w["n_up"], w["spin_inversion"], w["perms"], w["chars"])
+        t1 = time.perf_counter()
+        if x0 is None:
+            x0 = torch.from_numpy(ei.x_by_index(0, ed.basis_size(B))[:, 0]).cuda()
+        r = ed.lanczos(O, B, x0, w["lanczos_steps"], ed.ED_LANCZOS_F32_MATVEC)
+        torch.cuda.synchronize()
+        t2 = time.perf_counter()
+        marks.append({"basis_ms": 1e3 * (t1 - t0), "lanczos_ms": 1e3 * (t2 - t1),
+                      "matvec_ms": r.matvec_ms, "launches": ed.launch_count() - launches0})
+        del B
+    print(json.dumps({"mode": "step", "workload": w["name"], "steps": marks}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -278,9 +301,10 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="ring32")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--mode", default="job", choices=["job", "matvec"],
+    ap.add_argument("--mode", default="job", choices=["job", "matvec", "step"],
                     help="job: the benchmark; matvec: only the basis build and --steps matvec "
-                         "launches per dtype (a short program for profiler captures)")
+                         "launches per dtype; step: one untimed and one more whole step "
+                         "(short programs for profiler captures)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     w = ei.workload(args.workload)
@@ -288,6 +312,8 @@ def main():
         return run_reference(args, w)
     if args.mode == "matvec":
         return run_matvec_only(args, w)
+    if args.mode == "step":
+        return run_one_step(args, w)
 
     import torch
     from paper_2308_16712_gb300 import ed
