@@ -27,24 +27,25 @@ constexpr int kRedThreads = 256;
 constexpr int kRefineSteps = 6;
 
 // ---- compensated sums ------------------------------------------------------
+// fp64 is the scarce resource on this GPU, so each thread sums its few dozen
+// elements with plain fp64 fused multiply-adds into two accumulators, and only
+// the merges across threads and blocks are compensated: Knuth's branch-free
+// TwoSum carries the rounding error of every merge in a second word.
 struct KSum {
     double s, c;
 };
 
-__device__ __forceinline__ void ksum_add(KSum &k, double x)
+__device__ __forceinline__ KSum two_sum(double a, double b)
 {
-    const double t = k.s + x;
-    if (fabs(k.s) >= fabs(x))
-        k.c += (k.s - t) + x;
-    else
-        k.c += (x - t) + k.s;
-    k.s = t;
+    const double s = a + b;
+    const double bb = s - a;
+    return {s, (a - (s - bb)) + (b - bb)};
 }
 
 __device__ __forceinline__ KSum ksum_merge(KSum a, KSum b)
 {
-    KSum r{a.s, a.c + b.c};
-    ksum_add(r, b.s);
+    KSum r = two_sum(a.s, b.s);
+    r.c += a.c + b.c;
     return r;
 }
 
@@ -87,6 +88,14 @@ __device__ double reduce_partials(const double2 *part, int nparts)
     return total;
 }
 
+// out = sum of the partials (root = 0) or its square root (root = 1); one block.
+__global__ void __launch_bounds__(kRedThreads) k_finalize(const double2 *part, int nparts, double *out, int root)
+{
+    const double t = reduce_partials(part, nparts);
+    if (threadIdx.x == 0)
+        *out = root ? sqrt(fmax(t, 0.0)) : t;
+}
+
 // ---- vector element access (real or complex, fp64 or fp32) -------------------
 template <bool kC> struct Vec;
 template <> struct Vec<false> {
@@ -97,7 +106,7 @@ template <> struct Vec<false> {
     __device__ static double norm2(double a) { return a * a; }
     __device__ static double up(float a) { return (double)a; }
     __device__ static float down(double a) { return (float)a; }
-    __device__ static double axpby(double w, double a, double v, double b, double p) { return w - a * v - b * p; }
+    __device__ static double axpby(double w, double a, double v, double b, double p) { return fma(-b, p, fma(-a, v, w)); }
     __device__ static double scale(double w, double s) { return w * s; }
     __device__ static double zero() { return 0.0; }
     __device__ static double fma_acc(double acc, double y, double v) { return acc + y * v; }
@@ -112,7 +121,7 @@ template <> struct Vec<true> {
     __device__ static float2 down(double2 a) { return make_float2((float)a.x, (float)a.y); }
     __device__ static double2 axpby(double2 w, double a, double2 v, double b, double2 p)
     {
-        return make_double2(w.x - a * v.x - b * p.x, w.y - a * v.y - b * p.y);
+        return make_double2(fma(-b, p.x, fma(-a, v.x, w.x)), fma(-b, p.y, fma(-a, v.y, w.y)));
     }
     __device__ static double2 scale(double2 w, double s) { return make_double2(w.x * s, w.y * s); }
     __device__ static double2 zero() { return make_double2(0.0, 0.0); }
@@ -128,16 +137,26 @@ __global__ void __launch_bounds__(kRedThreads) k_dot_part(const typename Vec<kC>
                                                            uint64_t n, double2 *part)
 {
     using VT = Vec<kC>;
-    KSum k{0.0, 0.0};
+    double s0 = 0.0, s1 = 0.0;
     const uint64_t per = (n + gridDim.x - 1) / gridDim.x;
     const uint64_t lo = min(n, blockIdx.x * per), hi = min(n, lo + per);
-    for (uint64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
-        if constexpr (kF32)
-            ksum_add(k, VT::dotf(a[i], reinterpret_cast<const typename VT::F *>(bv)[i]));
-        else
-            ksum_add(k, VT::dot(a[i], reinterpret_cast<const typename VT::D *>(bv)[i]));
+    uint64_t i = lo + threadIdx.x;
+    for (; i + blockDim.x < hi; i += 2 * blockDim.x) {
+        if constexpr (kF32) {
+            s0 += VT::dotf(a[i], reinterpret_cast<const typename VT::F *>(bv)[i]);
+            s1 += VT::dotf(a[i + blockDim.x], reinterpret_cast<const typename VT::F *>(bv)[i + blockDim.x]);
+        } else {
+            s0 += VT::dot(a[i], reinterpret_cast<const typename VT::D *>(bv)[i]);
+            s1 += VT::dot(a[i + blockDim.x], reinterpret_cast<const typename VT::D *>(bv)[i + blockDim.x]);
+        }
     }
-    k = block_ksum(k);
+    if (i < hi) {
+        if constexpr (kF32)
+            s0 += VT::dotf(a[i], reinterpret_cast<const typename VT::F *>(bv)[i]);
+        else
+            s0 += VT::dot(a[i], reinterpret_cast<const typename VT::D *>(bv)[i]);
+    }
+    const KSum k = block_ksum(two_sum(s0, s1));
     if (threadIdx.x == 0)
         part[blockIdx.x] = make_double2(k.s, k.c);
 }
@@ -146,12 +165,17 @@ template <bool kC>
 __global__ void __launch_bounds__(kRedThreads) k_norm_part(const typename Vec<kC>::D *a, uint64_t n, double2 *part)
 {
     using VT = Vec<kC>;
-    KSum k{0.0, 0.0};
+    double s0 = 0.0, s1 = 0.0;
     const uint64_t per = (n + gridDim.x - 1) / gridDim.x;
     const uint64_t lo = min(n, blockIdx.x * per), hi = min(n, lo + per);
-    for (uint64_t i = lo + threadIdx.x; i < hi; i += blockDim.x)
-        ksum_add(k, VT::norm2(a[i]));
-    k = block_ksum(k);
+    uint64_t i = lo + threadIdx.x;
+    for (; i + blockDim.x < hi; i += 2 * blockDim.x) {
+        s0 += VT::norm2(a[i]);
+        s1 += VT::norm2(a[i + blockDim.x]);
+    }
+    if (i < hi)
+        s0 += VT::norm2(a[i]);
+    const KSum k = block_ksum(two_sum(s0, s1));
     if (threadIdx.x == 0)
         part[blockIdx.x] = make_double2(k.s, k.c);
 }
@@ -161,18 +185,16 @@ template <bool kC, bool kF32>
 __global__ void __launch_bounds__(kRedThreads) k_update(const void *w_in, typename Vec<kC>::D *w,
                                                          const typename Vec<kC>::D *v,
                                                          const typename Vec<kC>::D *vp, uint64_t n,
-                                                         const double2 *dot_part, int nparts,
-                                                         double *alpha, const double *beta_j,
+                                                         const double *alpha, const double *beta_j,
                                                          double2 *norm_part)
 {
     using VT = Vec<kC>;
-    const double a = reduce_partials(dot_part, nparts);
-    if (blockIdx.x == 0 && threadIdx.x == 0)
-        *alpha = a;
+    const double a = *alpha;
     const double b = vp ? *beta_j : 0.0;
-    KSum k{0.0, 0.0};
+    double s0 = 0.0, s1 = 0.0;
     const uint64_t per = (n + gridDim.x - 1) / gridDim.x;
     const uint64_t lo = min(n, blockIdx.x * per), hi = min(n, lo + per);
+    int parity = 0;
     for (uint64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
         typename VT::D wi;
         if constexpr (kF32)
@@ -181,9 +203,13 @@ __global__ void __launch_bounds__(kRedThreads) k_update(const void *w_in, typena
             wi = reinterpret_cast<const typename VT::D *>(w_in)[i];
         const typename VT::D r = VT::axpby(wi, a, v[i], b, vp ? vp[i] : VT::zero());
         w[i] = r;
-        ksum_add(k, VT::norm2(r));
+        if (parity)
+            s1 += VT::norm2(r);
+        else
+            s0 += VT::norm2(r);
+        parity ^= 1;
     }
-    k = block_ksum(k);
+    const KSum k = block_ksum(two_sum(s0, s1));
     if (threadIdx.x == 0)
         norm_part[blockIdx.x] = make_double2(k.s, k.c);
 }
@@ -193,13 +219,10 @@ template <bool kC>
 __global__ void __launch_bounds__(kRedThreads) k_normalize(const typename Vec<kC>::D *w,
                                                             typename Vec<kC>::D *v_out,
                                                             typename Vec<kC>::F *x32, uint64_t n,
-                                                            const double2 *norm_part, int nparts,
-                                                            double *beta_out)
+                                                            const double *beta)
 {
     using VT = Vec<kC>;
-    const double b = sqrt(fmax(reduce_partials(norm_part, nparts), 0.0));
-    if (blockIdx.x == 0 && threadIdx.x == 0)
-        *beta_out = b;
+    const double b = *beta;
     const double s = b > 0.0 ? 1.0 / b : 0.0;
     for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (uint64_t)gridDim.x * blockDim.x) {
@@ -269,12 +292,12 @@ __global__ void __launch_bounds__(kRedThreads) k_residual(const typename Vec<kC>
     const double th = num / den;
     if (blockIdx.x == 0 && threadIdx.x == 0)
         *theta_out = th;
-    KSum k{0.0, 0.0};
+    double s0 = 0.0;
     const uint64_t per = (n + gridDim.x - 1) / gridDim.x;
     const uint64_t lo = min(n, blockIdx.x * per), hi = min(n, lo + per);
     for (uint64_t i = lo + threadIdx.x; i < hi; i += blockDim.x)
-        ksum_add(k, VT::norm2(VT::axpby(hu[i], th, u[i], 0.0, VT::zero())));
-    k = block_ksum(k);
+        s0 += VT::norm2(VT::axpby(hu[i], th, u[i], 0.0, VT::zero()));
+    const KSum k = block_ksum(KSum{s0, 0.0});
     if (threadIdx.x == 0)
         res_part[blockIdx.x] = make_double2(k.s, k.c);
 }
@@ -308,36 +331,48 @@ __device__ int sturm_count(const double *a, const double *b, int m, double x)
 // Lowest eigenvalue and eigenvector of the leading m_eff x m_eff block, where
 // m_eff stops at the first beta that vanishes (invariant subspace).
 // a[0..m), beta[0..m]: beta[j] couples v_{j-1} and v_j (beta[0] unused).
+// One warp: multisection -- each lane evaluates the Sturm count at one of 32
+// interior points, which shrinks the bracket of the lowest eigenvalue 33-fold
+// per round -- then inverse iteration on lane 0.  Launch with 32 threads.
 __global__ void k_tridiag_lowest(const double *alpha, const double *beta, int m, double *y,
                                  double *lambda_out, int *m_eff_out, double *work)
 {
-    if (threadIdx.x != 0 || blockIdx.x != 0)
-        return;
+    const int lane = threadIdx.x & 31;
     int me = m;
-    double scale = 0.0;
-    for (int i = 0; i < m; ++i)
-        scale = fmax(scale, fabs(alpha[i]) + fabs(beta[i + 1]));
-    for (int i = 1; i < m; ++i)
-        if (!(beta[i] > 1e-13 * fmax(scale, 1e-300))) {
-            me = i;
-            break;
+    double scale = 0.0, lo = 1e300, hi = -1e300;
+    if (lane == 0) {
+        for (int i = 0; i < m; ++i)
+            scale = fmax(scale, fabs(alpha[i]) + fabs(beta[i + 1]));
+        for (int i = 1; i < m; ++i)
+            if (!(beta[i] > 1e-13 * fmax(scale, 1e-300))) {
+                me = i;
+                break;
+            }
+        for (int i = 0; i < me; ++i) {  // Gershgorin interval
+            const double r = (i ? fabs(beta[i]) : 0.0) + (i + 1 < me ? fabs(beta[i + 1]) : 0.0);
+            lo = fmin(lo, alpha[i] - r);
+            hi = fmax(hi, alpha[i] + r);
         }
-    // Gershgorin interval
-    double lo = 1e300, hi = -1e300;
-    for (int i = 0; i < me; ++i) {
-        const double r = (i ? fabs(beta[i]) : 0.0) + (i + 1 < me ? fabs(beta[i + 1]) : 0.0);
-        lo = fmin(lo, alpha[i] - r);
-        hi = fmax(hi, alpha[i] + r);
     }
-    for (int it = 0; it < 200 && hi - lo > 0.0; ++it) {
-        const double mid = 0.5 * (lo + hi);
-        if (mid <= lo || mid >= hi)
+    me = __shfl_sync(0xffffffffu, me, 0);
+    scale = __shfl_sync(0xffffffffu, scale, 0);
+    lo = __shfl_sync(0xffffffffu, lo, 0);
+    hi = __shfl_sync(0xffffffffu, hi, 0);
+    for (int it = 0; it < 24; ++it) {
+        const double width = hi - lo;
+        if (!(width > 2e-16 * fmax(fabs(lo), fabs(hi))))
             break;
-        if (sturm_count(alpha, beta, me, mid) >= 1)
-            hi = mid;
-        else
-            lo = mid;
+        const double x = lo + width * (double)(lane + 1) / 33.0;
+        const unsigned below = __ballot_sync(0xffffffffu, sturm_count(alpha, beta, me, x) >= 1);
+        // first lane whose point has an eigenvalue below it
+        const int f = below ? __ffs(below) - 1 : 32;
+        const double nlo = f == 0 ? lo : lo + width * (double)f / 33.0;
+        const double nhi = f == 32 ? hi : lo + width * (double)(f + 1) / 33.0;
+        lo = nlo;
+        hi = nhi;
     }
+    if (lane != 0)
+        return;
     const double lam = 0.5 * (lo + hi);
     // inverse iteration: (T - lam I) z = y, LU without pivoting with guarded pivots
     double *dd = work;  // pivots
@@ -345,7 +380,6 @@ __global__ void k_tridiag_lowest(const double *alpha, const double *beta, int m,
     for (int i = 0; i < me; ++i)
         y[i] = 1.0;
     for (int iter = 0; iter < 4; ++iter) {
-        // forward elimination
         double piv = alpha[0] - lam;
         if (fabs(piv) < eps)
             piv = eps;
@@ -523,18 +557,21 @@ ed_status run_lanczos(const ed_operator *op, const ed_basis *b, const void *x0, 
                 if (e != cudaSuccess)
                     return e;
                 k_dot_part<kC, true><<<nparts, kRedThreads, 0, st>>>(v, w32, n, part_a); count_launch();
-                k_update<kC, true><<<nparts, kRedThreads, 0, st>>>(w32, w, v, vp, n, part_a, nparts,
-                                                                    alpha + j, beta + j, part_b); count_launch();
+                k_finalize<<<1, kRedThreads, 0, st>>>(part_a, nparts, alpha + j, 0); count_launch();
+                k_update<kC, true><<<nparts, kRedThreads, 0, st>>>(w32, w, v, vp, n, alpha + j, beta + j,
+                                                                    part_b); count_launch();
             } else {
                 if ((e = H64(v, w)) != cudaSuccess)
                     return e;
                 k_dot_part<kC, false><<<nparts, kRedThreads, 0, st>>>(v, w, n, part_a); count_launch();
-                k_update<kC, false><<<nparts, kRedThreads, 0, st>>>(w, w, v, vp, n, part_a, nparts,
-                                                                     alpha + j, beta + j, part_b); count_launch();
+                k_finalize<<<1, kRedThreads, 0, st>>>(part_a, nparts, alpha + j, 0); count_launch();
+                k_update<kC, false><<<nparts, kRedThreads, 0, st>>>(w, w, v, vp, n, alpha + j, beta + j,
+                                                                     part_b); count_launch();
             }
             D *vn = Vs ? Vs + (uint64_t)(j + 1) * n : (vp ? vp : ring[1]);
-            k_normalize<kC><<<vgrid, kRedThreads, 0, st>>>(w, vn, use_f32 ? x32 : nullptr, n, part_b,
-                                                           nparts, beta + j + 1); count_launch();
+            k_finalize<<<1, kRedThreads, 0, st>>>(part_b, nparts, beta + j + 1, 1); count_launch();
+            k_normalize<kC><<<vgrid, kRedThreads, 0, st>>>(w, vn, use_f32 ? x32 : nullptr, n,
+                                                           beta + j + 1); count_launch();
             vp = v;
             v = vn;
         }
@@ -544,7 +581,7 @@ ed_status run_lanczos(const ed_operator *op, const ed_basis *b, const void *x0, 
     // main pass
     ED_L_TRY(run((const D *)x0, steps, f32, store ? V : nullptr, nullptr));
     ED_L_TRY(cudaMemsetAsync(y, 0, (mmax + 1) * sizeof(double), st));
-    k_tridiag_lowest<<<1, 1, 0, st>>>(alpha, beta, steps, y, scal + 0, m_eff, work); count_launch();
+    k_tridiag_lowest<<<1, 32, 0, st>>>(alpha, beta, steps, y, scal + 0, m_eff, work); count_launch();
     if (store) {
         k_combine<kC><<<vgrid, kRedThreads, 0, st>>>(psi, V, y, m_eff, n); count_launch();
     } else {
@@ -564,7 +601,7 @@ ed_status run_lanczos(const ed_operator *op, const ed_basis *b, const void *x0, 
         ED_L_TRY(cudaMemsetAsync(beta, 0, (mmax + 2) * sizeof(double), st));
         ED_L_TRY(run(psi, mref, false, Vr, nullptr));
         ED_L_TRY(cudaMemsetAsync(y, 0, (mmax + 1) * sizeof(double), st));
-        k_tridiag_lowest<<<1, 1, 0, st>>>(alpha, beta, mref, y, scal + 1, m_eff, work); count_launch();
+        k_tridiag_lowest<<<1, 32, 0, st>>>(alpha, beta, mref, y, scal + 1, m_eff, work); count_launch();
         k_combine<kC><<<vgrid, kRedThreads, 0, st>>>(psi, Vr, y, m_eff, n); count_launch();
         ED_L_TRY(cudaGetLastError());
     }
