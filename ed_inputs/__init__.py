@@ -83,6 +83,39 @@ def x_by_state(seed: int, states, nvec: int = 1, complex_: bool = False) -> np.n
     return uniform_pm1(seed, c)
 
 
+def _hash64_torch(x):
+    """hash64_01 on an int64 torch tensor holding uint64 bit patterns (logical
+    shifts done as arithmetic shift + mask; multiplication wraps mod 2**64)."""
+    import torch
+    def srl(v, k):
+        return (v >> k) & ((1 << (64 - k)) - 1)
+    m1 = torch.tensor(np.int64(np.uint64(0xBF58476D1CE4E5B9).view(np.int64)), device=x.device)
+    m2 = torch.tensor(np.int64(np.uint64(0x94D049BB133111EB).view(np.int64)), device=x.device)
+    x = (x ^ srl(x, 30)) * m1
+    x = (x ^ srl(x, 27)) * m2
+    return x ^ srl(x, 31)
+
+
+def x_by_state_torch(seed: int, states, nvec: int = 1, complex_: bool = False, dtype=None):
+    """Device version of ``x_by_state`` for a torch int64 tensor of states (same
+    numbers, computed where the states live)."""
+    import torch
+    golden = torch.tensor(np.int64(GOLDEN.view(np.int64)), device=states.device)
+    seed_t = torch.tensor(np.int64(np.uint64(seed).view(np.int64)), device=states.device)
+    c = states.reshape(-1, 1) * nvec + torch.arange(nvec, device=states.device).reshape(1, -1)
+
+    def unif(cnt):
+        h = _hash64_torch(seed_t + cnt * golden)
+        u = ((h >> 11) & ((1 << 53) - 1)).to(torch.float64) * (2.0 ** -53)
+        return 2.0 * u - 1.0
+
+    if complex_:
+        out = torch.complex(unif(2 * c), unif(2 * c + 1))
+    else:
+        out = unif(c)
+    return out if dtype is None else out.to(dtype)
+
+
 # ----------------------------------------------------------------------------
 # symmetry groups (site permutations + characters)
 # ----------------------------------------------------------------------------

@@ -1,0 +1,107 @@
+"""The benchmark configurations other than the timed one, at their full sizes,
+as parity cases: basis dimensions against the character formula (and, for the
+N=40 ring, against the paper's Table 2), sampled representatives checked one by
+one by the oracle, and sampled rows of y = Hx (x keyed by the state) against the
+oracle's row evaluation.
+
+Bars as in test_gpu_parity: bit-exact integers, fp64/complex128 within 1e-12 of
+max|y| on the sampled rows, fp32/complex64 within 2e-6."""
+import math
+
+import numpy as np
+import pytest
+
+import ed_inputs as ei
+import oracle
+from gpu_util import gpu, rel_err
+
+pytestmark = pytest.mark.gpu
+
+F64_TOL = 1e-12
+F32_TOL = 2e-6
+
+
+def sampled_rows_check(B, O, G, H, seed, nvec, cplx, n_rows=120, rng_seed=0):
+    """Sampled rows of y = Hx against the oracle; x keyed by state, generated on
+    the device from the GPU basis; only the sampled rows come back to the host."""
+    torch, ed = gpu()
+    st_t, nm_t = ed.basis_states(B)
+    dim = st_t.numel()
+    rng = np.random.default_rng(rng_seed)
+    idx = np.unique(np.concatenate([[0, dim - 1], rng.integers(0, dim, n_rows)]))
+    idx_t = torch.from_numpy(idx).cuda()
+    st = st_t[idx_t].cpu().numpy().view(np.uint64)
+    nm = nm_t[idx_t].cpu().numpy().view(np.uint16)
+    # sampled representatives are representatives with the stored norm
+    for s_, n_ in list(zip(st, nm))[:40]:
+        rep, _, norm, _ = oracle.state_info(G, int(s_))
+        assert rep == int(s_) and norm == int(n_)
+    want, _ = oracle.rows_statex(G, H, st, seed, nvec, cplx)
+    for dt, tol in ((torch.complex128 if cplx else torch.float64, F64_TOL),
+                    (torch.complex64 if cplx else torch.float32, F32_TOL)):
+        xt = ei.x_by_state_torch(seed, st_t, nvec, cplx, dtype=dt).contiguous()
+        yt = torch.empty_like(xt)
+        ed.matvec(O, B, xt, yt, nvec)
+        got = yt[idx_t].cpu().numpy().astype(np.complex128)
+        assert rel_err(got, want if cplx else want.real) < tol
+        del xt, yt
+        torch.cuda.empty_cache()
+
+
+def test_ring40_config():
+    """Heisenberg ring N=40, Sz=0, k=0, p=+1, z=+1: 861 725 794 representatives
+    (the paper's Table 2), 64-bit words, factored search."""
+    torch, ed = gpu()
+    w = ei.workload("ring40")
+    B = ed.basis_build(40, 20, +1, w["perms"], w["chars"])
+    assert ed.basis_size(B) == 861725794
+    assert ed.basis_factored(B)[0]
+    O = ed.operator_create(40, w["op"]["sites"], w["op"]["coeff"], w["op"]["local"])
+    G = oracle.Group(40, w["perms"], w["chars"], +1)
+    st_t, _ = ed.basis_states(B)
+    assert bool((st_t[1:] > st_t[:-1]).all())
+    sampled_rows_check(B, O, G, oracle.Operator(w["op"]), 31, 1, False, n_rows=60)
+
+
+def test_torus6x6_config():
+    """6x6 J1-J2 (J2 = 0.5), Sz=0, momentum (pi/3, 0), z=+1, translations only:
+    complex characters, minimiser tracked, 64-bit words."""
+    torch, ed = gpu()
+    w = ei.workload("torus6x6")
+    B = ed.basis_build(36, 18, +1, w["perms"], w["chars"])
+    G = oracle.Group(36, w["perms"], w["chars"], +1)
+    dim = ed.basis_size(B)
+    assert dim == oracle.sector_dim(G, 18) == 126039218
+    assert not ed.basis_is_real(B)
+    O = ed.operator_create(36, w["op"]["sites"], w["op"]["coeff"], w["op"]["local"])
+    sampled_rows_check(B, O, G, oracle.Operator(w["op"]), 37, 1, True, n_rows=60)
+
+
+def test_xxz28_all_sectors():
+    """XXZ ring N=28 (Jxy=1, Delta=1.5): all 140 sectors (Sz = 0..3 x 28 momenta,
+    z = +-1 at Sz = 0); the dimensions of each Sz resolve the U(1) sector; block
+    vectors nvec=8 checked on sampled rows of a few sectors."""
+    torch, ed = gpu()
+    op = ei.xxz_ring(28, 1.0, 1.5)
+    O = ed.operator_create(28, op["sites"], op["coeff"], op["local"])
+    H = oracle.Operator(op)
+    sectors = ei.xxz28_sectors()
+    assert len(sectors) == 140
+    totals = {}
+    dims = []
+    for s in sectors:
+        B = ed.basis_build(28, s["n_up"], s["spin_inversion"], s["perms"], s["chars"])
+        d = ed.basis_size(B)
+        dims.append(d)
+        totals[s["n_up"]] = totals.get(s["n_up"], 0) + d
+        del B
+    for n_up, tot in totals.items():
+        assert tot == math.comb(28, n_up)
+    assert min(dims) >= 100000 and max(dims) <= 1400000
+    for k in (0, 33, 77, 139):  # Sz=0 z=+1 k=0; a complex Sz=0 sector; Sz=1 and Sz=3 sectors
+        s = sectors[k]
+        B = ed.basis_build(28, s["n_up"], s["spin_inversion"], s["perms"], s["chars"])
+        G = oracle.Group(28, s["perms"], s["chars"], s["spin_inversion"])
+        assert ed.basis_size(B) == oracle.sector_dim(G, s["n_up"])
+        cplx = not ed.basis_is_real(B)
+        sampled_rows_check(B, O, G, H, 41 + k, 8, cplx, n_rows=40, rng_seed=k)

@@ -297,3 +297,13 @@ def test_input_generator_properties():
     # the mixer is a bijection (distinct inputs give distinct outputs)
     h = ei.hash64_01(np.arange(1 << 16, dtype=np.uint64))
     assert len(np.unique(h)) == 1 << 16
+
+
+def test_device_generator_matches_numpy_generator():
+    import torch
+    st = np.random.default_rng(4).integers(0, 1 << 62, 5000).astype(np.uint64)
+    st[:3] = [0, (1 << 40) - 1, (1 << 63) + 12345]
+    for cplx, nvec in ((False, 1), (True, 3)):
+        want = ei.x_by_state(9, st, nvec, cplx)
+        got = ei.x_by_state_torch(9, torch.from_numpy(st.view(np.int64)), nvec, cplx).numpy()
+        assert np.array_equal(got, want)
