@@ -229,45 +229,38 @@ def generated_terms_per_row(states, n):
 
 
 def run_matvec_only(args, w):
+    """Basis build and --steps matvec launches per dtype, timed with CUDA events
+    (a short program, also used for profiler captures)."""
     import torch
     from paper_2308_16712_gb300 import ed
     n = w["n_sites"]
     op = w["op"]
     O = ed.operator_create(n, op["sites"], op["coeff"], op["local"])
+    t0 = time.perf_counter()
     B = ed.basis_build(n, w["n_up"], w["spin_inversion"], w["perms"], w["chars"])
+    build_ms = 1e3 * (time.perf_counter() - t0)
     dim = ed.basis_size(B)
-    for dt in (torch.float32, torch.float64):
-        x = torch.from_numpy(ei.x_by_index(5, dim)[:, 0]).cuda().to(dt)
+    cplx = not ed.basis_is_real(B)
+    nvec = args.nvec
+    states, _ = ed.basis_states(B)
+    out = {"mode": "matvec", "workload": w["name"], "dim": dim, "nvec": nvec, "basis_build_ms": build_ms,
+           "launches": 2 * args.steps}
+    dts = (torch.complex64, torch.complex128) if cplx else (torch.float32, torch.float64)
+    for dt in dts:
+        x = ei.x_by_state_torch(5, states, nvec, cplx, dtype=dt).contiguous()
         y = torch.empty_like(x)
+        ts = []
         for _ in range(args.steps):
-            ed.matvec(O, B, x, y, 1)
-    torch.cuda.synchronize()
-    print(json.dumps({"mode": "matvec", "workload": w["name"], "dim": dim, "launches": 2 * args.steps}))
-
-
-def search_ops_per_term(n, n_perm, flip, fact, rot_L, n_cos, kinds):
-    """INT32 operations of one representative search (real characters, so no
-    minimiser is tracked) as the kernel runs it -- an instruction-level count of
-    the algorithm, not a measurement.
-    32-bit words: Benes stage = 2 shifts + 2 three-input logic ops (9 stages);
-    rotation of the doubled word = 1 funnel shift (+1 mask op when n < 32);
-    running min = 1 op per candidate; with spin inversion the factored search
-    keeps a running max as well (1 op) and needs no per-candidate complement,
-    the generic one complements (1 op) and takes a second min (1 op).
-    64-bit words: shifts, logic ops, min and max cost two 32-bit operations
-    each (4 for a 64-bit min or max); an incremental rotation costs 6."""
-    if n <= 32:
-        benes, rev = 36, (1 if n == 32 else 2)
-        per_rot = (1 if n == 32 else 2) + (2 if flip else 1)
-        per_perm = benes + (3 if flip else 1)
-    else:
-        benes, rev = 84, 4
-        per_rot = 6 + (8 if flip else 4)
-        per_perm = benes + (2 + 8 if flip else 4)
-    if not fact:
-        return n_perm * per_perm
-    head = sum({0: 0, 1: rev, 2: benes}[int(k)] for k in kinds)
-    return head + n_cos * rot_L * per_rot + (1 if flip else 0)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            ed.matvec(O, B, x, y, nvec)
+            b.record()
+            torch.cuda.synchronize()
+            ts.append(a.elapsed_time(b))
+        out[str(dt).replace("torch.", "")] = {"ms": min(ts), "rows_per_s": dim / (min(ts) * 1e-3),
+                                             "vector_rows_per_s": nvec * dim / (min(ts) * 1e-3)}
+        del x, y
+    print(json.dumps(out))
 
 
 def run_one_step(args, w):
@@ -300,6 +293,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="ring32")
+    ap.add_argument("--nvec", type=int, default=1, help="vectors per matvec in --mode matvec")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--mode", default="job", choices=["job", "matvec", "step"],
                     help="job: the benchmark; matvec: only the basis build and --steps matvec "

@@ -253,6 +253,14 @@ def workload(name: str) -> dict:
         p, c = torus_group(6, 6, 1, 0)
         return dict(name=name, n_sites=36, n_up=18, spin_inversion=+1, perms=p, chars=c,
                     op=j1j2_torus(6, 6, 1.0, 0.5), complex_=True, lanczos_steps=100)
+    if name == "xxz28_k0":
+        p, c = ring_group(28, 0)
+        return dict(name=name, n_sites=28, n_up=14, spin_inversion=+1, perms=p, chars=c,
+                    op=xxz_ring(28, 1.0, 1.5), complex_=False, lanczos_steps=100)
+    if name == "xxz28_k5":
+        p, c = ring_group(28, 5)
+        return dict(name=name, n_sites=28, n_up=14, spin_inversion=+1, perms=p, chars=c,
+                    op=xxz_ring(28, 1.0, 1.5), complex_=True, lanczos_steps=100)
     raise KeyError(name)
 
 
