@@ -180,14 +180,17 @@ def cpu_baseline(w, budget_s=15.0):
             "nnz_per_row": float(nnz.mean())}
 
 
-def run_reference(args, w):
+def run_reference(args, w, budget_s=150.0):
+    """The reference arm: the CPU oracle timed on the machine's host cores (rank 0
+    only; other ranks exit without work), each step a bounded sample of rows
+    sized so the whole run takes about budget_s seconds."""
     rank, world, _ = dist_setup(args.gpus)
     if rank != 0:
-        return
+        return None
     G, H, rows = oracle_rows(w, 64)
     dt, _ = time_oracle_rows(G, H, rows[:8])
     per_row = max(dt / 8, 1e-6)
-    rows_per_step = int(min(max(150.0 / (args.steps + args.warmup) / per_row, 8), 20000))
+    rows_per_step = int(min(max(budget_s / (args.steps + args.warmup) / per_row, 8), 20000))
     G, H, rows = oracle_rows(w, rows_per_step * (args.steps + args.warmup), seed=3)
     chunks = np.array_split(rows, args.steps + args.warmup)
     for c in chunks[: args.warmup]:
@@ -207,6 +210,7 @@ def run_reference(args, w):
                                        "single-threaded C oracle (x keyed by state)"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+    return line
 
 
 # ---------------------------------------------------------------------------
