@@ -150,14 +150,14 @@ def oracle_rows(w, n_rows, seed=1):
     import oracle
     G = oracle.Group(w["n_sites"], w["perms"], w["chars"], w["spin_inversion"])
     rng = np.random.default_rng(seed)
-    rows = set()
-    while len(rows) < n_rows:
+    rows = []
+    while len(rows) < n_rows:  # with repetition: small sectors have few rows
         bits = rng.choice(w["n_sites"], w["n_up"], replace=False)
         s = sum(1 << int(b) for b in bits)
         rep, _, norm, _ = oracle.state_info(G, s)
         if norm:
-            rows.add(rep)
-    return G, oracle.Operator(w["op"]), np.array(sorted(rows), np.uint64)
+            rows.append(rep)
+    return G, oracle.Operator(w["op"]), np.array(rows, np.uint64)
 
 
 def time_oracle_rows(G, H, rows):
