@@ -422,8 +422,8 @@ ed_operator *build_operator_host(int n_sites, int n_terms, const double *coeff,
 
 edk::OpView op_view(const ed_operator *op)
 {
-    return edk::OpView{(int)op->h_fams.size(), op->n_mats, op->d_fams, op->d_mats, op->d_matsf,
-                       op->d_offmask};
+    return edk::OpView{(int)op->h_fams.size(), op->n_mats, op->max_offdiag, op->d_fams, op->d_mats,
+                       op->d_matsf, op->d_offmask};
 }
 
 }  // namespace
@@ -490,6 +490,10 @@ ed_status check_pair(const ed_operator *op, const ed_basis *b)
         return ED_ERR_INVALID_ARG;
     if (op->n_sites != b->n_sites)
         return ED_ERR_INVALID_ARG;
+    // the matvec keeps each row's terms in a 512-entry per-warp list and packs
+    // a matrix-entry number into 16 bits
+    if (op->max_offdiag > 512 || op->n_mats > 4095)
+        return ED_ERR_UNSUPPORTED;
     if (op->checked.load() == b)
         return ED_OK;
     if (!operator_is_symmetric(op, b->n_perm, b->perms.data(), b->spin_inversion))

@@ -57,6 +57,7 @@ cudaError_t launch_index(const IndexView &ix, const uint64_t *query, int64_t *ou
 struct OpView {
     int n_fam;
     int n_mats;
+    int max_terms;           // most off-diagonal terms one row can produce
     const OpFamily *fams;    // rotation families
     const double2 *mats;     // n_mats x 16, coeff * h
     const float2 *matsf;
