@@ -290,6 +290,54 @@ def run_one_step(args, w):
     print(json.dumps({"mode": "step", "workload": w["name"], "steps": marks}))
 
 
+def search_ops_per_term(n, n_perm, flip, fact, rot_L, n_cos, kinds):
+    """INT32 operations of one representative search (real characters, so no
+    minimiser is tracked) as the kernel runs it -- an instruction-level count of
+    the algorithm, not a measurement.
+    32-bit words: Benes stage = 2 shifts + 2 three-input logic ops (9 stages);
+    rotation of the doubled word = 1 funnel shift (+1 mask op when n < 32);
+    running min = 1 op per candidate; with spin inversion the factored search
+    keeps a running max as well (1 op) and needs no per-candidate complement,
+    the generic one complements (1 op) and takes a second min (1 op).
+    64-bit words: shifts, logic ops, min and max cost two 32-bit operations
+    each (4 for a 64-bit min or max); an incremental rotation costs 6."""
+    if n <= 32:
+        benes, rev = 36, (1 if n == 32 else 2)
+        per_rot = (1 if n == 32 else 2) + (2 if flip else 1)
+        per_perm = benes + (3 if flip else 1)
+    else:
+        benes, rev = 84, 4
+        per_rot = 6 + (8 if flip else 4)
+        per_perm = benes + (2 + 8 if flip else 4)
+    if not fact:
+        return n_perm * per_perm
+    head = sum({0: 0, 1: rev, 2: benes}[int(k)] for k in kinds)
+    return head + n_cos * rot_L * per_rot + (1 if flip else 0)
+
+
+def run_one_step(args, w):
+    import torch
+    from paper_2308_16712_gb300 import ed
+    n, op = w["n_sites"], w["op"]
+    O = ed.operator_create(n, op["sites"], op["coeff"], op["local"])
+    x0 = None
+    marks = []
+    for rep in range(2):
+        t0 = time.perf_counter()
+        launches0 = ed.launch_count()
+        B = ed.basis_build(n, w["n_up"], w["spin_inversion"], w["perms"], w["chars"])
+        t1 = time.perf_counter()
+        if x0 is None:
+            x0 = torch.from_numpy(ei.x_by_index(0, ed.basis_size(B))[:, 0]).cuda()
+        r = ed.lanczos(O, B, x0, w["lanczos_steps"], ed.ED_LANCZOS_F32_MATVEC)
+        torch.cuda.synchronize()
+        t2 = time.perf_counter()
+        marks.append({"basis_ms": 1e3 * (t1 - t0), "lanczos_ms": 1e3 * (t2 - t1),
+                      "matvec_ms": r.matvec_ms, "launches": ed.launch_count() - launches0})
+        del B
+    print(json.dumps({"mode": "step", "workload": w["name"], "steps": marks}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)

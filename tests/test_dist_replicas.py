@@ -63,3 +63,13 @@ def test_reference_arm_rank_zero_only():
         res = dict(out)
     assert res[1] is None
     assert res[0] == ("reference", "rows/s", True, 0)
+
+
+def test_bench_roofline_op_count():
+    """The algorithmic INT32 count the benchmark divides by the launch time:
+    N=32 ring with reflection and spin inversion = 2 cosets x 32 rotations x
+    (1 funnel shift + min + max) + 1 reversal + 1 final complement."""
+    import bench
+    assert bench.search_ops_per_term(32, 64, True, True, 32, 2, [0, 1]) == 2 * 32 * 3 + 1 + 1
+    # generic search: 64 permutations x (36-op Benes + complement + 2 mins)
+    assert bench.search_ops_per_term(32, 64, True, False, 1, 0, []) == 64 * 39
