@@ -267,29 +267,6 @@ def run_matvec_only(args, w):
     print(json.dumps(out))
 
 
-def run_one_step(args, w):
-    import torch
-    from paper_2308_16712_gb300 import ed
-    n, op = w["n_sites"], w["op"]
-    O = ed.operator_create(n, op["sites"], op["coeff"], op["local"])
-    x0 = None
-    marks = []
-    for rep in range(2):
-        t0 = time.perf_counter()
-        launches0 = ed.launch_count()
-        B = ed.basis_build(n, w["n_up"], w["spin_inversion"], w["perms"], w["chars"])
-        t1 = time.perf_counter()
-        if x0 is None:
-            x0 = torch.from_numpy(ei.x_by_index(0, ed.basis_size(B))[:, 0]).cuda()
-        r = ed.lanczos(O, B, x0, w["lanczos_steps"], ed.ED_LANCZOS_F32_MATVEC)
-        torch.cuda.synchronize()
-        t2 = time.perf_counter()
-        marks.append({"basis_ms": 1e3 * (t1 - t0), "lanczos_ms": 1e3 * (t2 - t1),
-                      "matvec_ms": r.matvec_ms, "launches": ed.launch_count() - launches0})
-        del B
-    print(json.dumps({"mode": "step", "workload": w["name"], "steps": marks}))
-
-
 def search_ops_per_term(n, n_perm, flip, fact, rot_L, n_cos, kinds):
     """INT32 operations of one representative search (real characters, so no
     minimiser is tracked) as the kernel runs it -- an instruction-level count of

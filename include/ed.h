@@ -182,9 +182,7 @@ void ed_operator_destroy(ed_operator *op);
  * No allocation and no host synchronisation.  Deterministic: the same inputs
  * give bit-identical y.  Errors: ED_ERR_INVALID_ARG (including a complex
  * sector with a real dtype, or operator/basis with different n_sites),
- * ED_ERR_SYMMETRY_MISMATCH, ED_ERR_UNSUPPORTED (an operator whose rows can
- * produce more than 512 off-diagonal terms, or with more than 4095 distinct
- * scaled two-site matrices), ED_ERR_CUDA.
+ * ED_ERR_SYMMETRY_MISMATCH, ED_ERR_CUDA.
  */
 ed_status ed_matvec(const ed_operator *op, const ed_basis *basis, const void *d_x, void *d_y,
                     int nvec, ed_dtype dtype, void *stream);

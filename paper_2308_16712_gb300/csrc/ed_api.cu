@@ -490,10 +490,6 @@ ed_status check_pair(const ed_operator *op, const ed_basis *b)
         return ED_ERR_INVALID_ARG;
     if (op->n_sites != b->n_sites)
         return ED_ERR_INVALID_ARG;
-    // the matvec keeps each row's terms in a 512-entry per-warp list and packs
-    // a matrix-entry number into 16 bits
-    if (op->max_offdiag > 512 || op->n_mats > 4095)
-        return ED_ERR_UNSUPPORTED;
     if (op->checked.load() == b)
         return ED_OK;
     if (!operator_is_symmetric(op, b->n_perm, b->perms.data(), b->spin_inversion))

@@ -2,21 +2,19 @@
 // (Sec. "Matrix-vector product": y_i = sum_j H_ij x_j with getRow and
 // stateToIndex), instantiated per precision in the ed_matvec_*.cu units.
 //
-// Work decomposition.  The grid is persistent; the basis is cut into tiles of
-// R consecutive rows (R = 32, or fewer when rows can produce many terms), dealt
-// round-robin to warps.  For each tile a warp works in three phases:
-//  0. each row lane loads its row r and n(r), forms the diagonal from the
-//     local configurations of every bond family (one word rotation and four
-//     popcounts per family), counts its off-diagonal terms, and after a warp
-//     scan writes the produced states into the warp's term list in shared
-//     memory;
-//  A. all 32 lanes take 32 terms at a time: the representative search runs in
-//     lockstep over the group (mask reads are shared-memory broadcasts), then
-//     each lane looks its representative up (hash index or prefix table) and
-//     writes the found index and coefficient conj(h) chi sqrt(n'/n) back;
-//  B. each row lane sums its own terms, in list order, gathering x at the
-//     found indices, and writes y.
-// The order of every sum is fixed: the result is deterministic, with no atomics.
+// Work decomposition.  The grid is persistent; rows are dealt to warps in
+// tiles of 32 (round-robin), and each warp hands its rows to its lanes on
+// demand (ballot + popc), so a lane that finishes a row takes the next one
+// without waiting for the others.
+// A lane owns its row r: it loads r and n(r), forms the diagonal from the
+// local configurations of every bond family (one word rotation and four
+// popcounts per family), and then walks the off-diagonal terms of H|r> one at a
+// time (bit by bit through the family masks).  All 32 lanes run the
+// representative search of their current term in lockstep over the same group
+// element (the mask reads are shared-memory broadcasts), then each lane looks
+// the representative up in the sorted basis, gathers x at that index and
+// accumulates in registers, in a fixed order: the result is deterministic and
+// needs no atomics.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -27,8 +25,7 @@
 
 namespace edk {
 
-constexpr int kMvThreads = 128;  // 4 warps per block
-constexpr int kTermCap = 512;    // term slots per warp
+constexpr int kMvThreads = 256;
 // The register budget is left to the compiler: capping it for more resident
 // warps cost more (spills, longer dependency chains) than it gained.
 
@@ -39,7 +36,6 @@ struct MatvecArgs {
     const void *x;
     void *y;
     int nvec;
-    int tile_rows;  // rows per tile: tile_rows * op.max_terms <= kTermCap
 };
 
 template <typename T, bool kC> struct ValT { using type = T; };
@@ -66,22 +62,9 @@ __device__ __forceinline__ void store_cs(Cplx<double> *p, Cplx<double> v)
     __stcs(reinterpret_cast<double2 *>(p), make_double2(v.re, v.im));
 }
 
-// coefficient type of a term
-template <typename T, bool kC> using CoefT = typename ValT<T, kC>::type;
-
-// Per-warp term list: slot A holds the produced state, then the found index;
-// slot B holds (matrix entry | row << 16), then the coefficient.
-template <typename W, typename T, bool kC>
-__host__ __device__ inline size_t warp_slots_bytes()
-{
-    const size_t a = sizeof(W) > 4 ? sizeof(W) : 4;
-    const size_t b = sizeof(CoefT<T, kC>) > 4 ? sizeof(CoefT<T, kC>) : 4;
-    return align16((size_t)kTermCap * a) + align16((size_t)kTermCap * b) + align16(32 * sizeof(T));
-}
-
-// Shared-memory layout: masks | chi | families | matrices | offmask | coset kinds | sqrt tables | warp slots
-template <typename W, typename T, bool kC, bool kTrack, bool kFact>
-__host__ __device__ inline void matvec_smem_layout(const GroupView &g, const OpView &op, size_t off[9])
+// Shared-memory layout: masks | chi | families | matrices | offmask | coset kinds | sqrt tables
+template <typename W, typename T, bool kTrack, bool kFact>
+__host__ __device__ inline void matvec_smem_layout(const GroupView &g, const OpView &op, size_t off[8])
 {
     const int nm = kFact ? g.n_cos : g.n_perm;
     off[0] = 0;
@@ -92,15 +75,14 @@ __host__ __device__ inline void matvec_smem_layout(const GroupView &g, const OpV
     off[5] = align16(off[4] + (size_t)op.n_mats * 4);
     off[6] = align16(off[5] + (kFact ? (size_t)g.n_cos : 0));
     off[7] = align16(off[6] + 2 * (size_t)(g.order + 1) * sizeof(T));
-    off[8] = off[7] + (size_t)(kMvThreads / 32) * warp_slots_bytes<W, T, kC>();
 }
 
-template <typename W, typename T, bool kC, bool kTrack, bool kFact>
+template <typename W, typename T, bool kTrack, bool kFact>
 __host__ __device__ inline size_t matvec_smem_bytes(const GroupView &g, const OpView &op)
 {
-    size_t off[9];
-    matvec_smem_layout<W, T, kC, kTrack, kFact>(g, op, off);
-    return off[8];
+    size_t off[8];
+    matvec_smem_layout<W, T, kTrack, kFact>(g, op, off);
+    return off[7];
 }
 
 // bit i of the result = bit (i + delta) mod n of s  (0 < delta < n)
@@ -208,10 +190,9 @@ template <typename W, typename T, bool kC, bool kTrack, bool kFact, int NV>
 __global__ void __launch_bounds__(kMvThreads) k_matvec(const MatvecArgs a)
 {
     using V = typename ValT<T, kC>::type;
-    using C = CoefT<T, kC>;
     extern __shared__ __align__(16) unsigned char smem[];
-    size_t off[9];
-    matvec_smem_layout<W, T, kC, kTrack, kFact>(a.g, a.op, off);
+    size_t off[8];
+    matvec_smem_layout<W, T, kTrack, kFact>(a.g, a.op, off);
     W *sm_masks = reinterpret_cast<W *>(smem + off[0]);
     Cplx<T> *sm_chi = reinterpret_cast<Cplx<T> *>(smem + off[1]);
     OpFamily *sm_fam = reinterpret_cast<OpFamily *>(smem + off[2]);
@@ -262,19 +243,6 @@ __global__ void __launch_bounds__(kMvThreads) k_matvec(const MatvecArgs a)
     }
     __syncthreads();
 
-    const int lane = threadIdx.x & 31;
-    const int wib = threadIdx.x >> 5;
-    unsigned char *wbase = smem + off[7] + (size_t)wib * warp_slots_bytes<W, T, kC>();
-    constexpr size_t kSlotA = sizeof(W) > 4 ? sizeof(W) : 4;
-    constexpr size_t kSlotB = sizeof(C) > 4 ? sizeof(C) : 4;
-    unsigned char *slotA = wbase;
-    unsigned char *slotB = wbase + align16((size_t)kTermCap * kSlotA);
-    T *row_rinv = reinterpret_cast<T *>(slotB + align16((size_t)kTermCap * kSlotB));
-    auto a_state = [&](int k) -> W & { return *reinterpret_cast<W *>(slotA + (size_t)k * kSlotA); };
-    auto a_index = [&](int k) -> uint32_t & { return *reinterpret_cast<uint32_t *>(slotA + (size_t)k * kSlotA); };
-    auto b_meta = [&](int k) -> uint32_t & { return *reinterpret_cast<uint32_t *>(slotB + (size_t)k * kSlotB); };
-    auto b_coef = [&](int k) -> C & { return *reinterpret_cast<C *>(slotB + (size_t)k * kSlotB); };
-
     const V *__restrict__ x = reinterpret_cast<const V *>(a.x);
     V *__restrict__ y = reinterpret_cast<V *>(a.y);
     const int nvec = a.nvec;
@@ -283,174 +251,182 @@ __global__ void __launch_bounds__(kMvThreads) k_matvec(const MatvecArgs a)
     const uint64_t dim = a.ix.dim;
     const W full = (W)a.g.full;
     const unsigned kAll = 0xffffffffu;
-    const int R = a.tile_rows;
-    const bool packed = a.ix.keys != nullptr;
+    const int lane = threadIdx.x & 31;
+    const unsigned lanes_below = (1u << lane) - 1u;
+    // Rows are dealt in tiles of 32 consecutive rows, round-robin over the
+    // warps of the grid: warp w takes tiles w, w + nw, w + 2 nw, ...  (the term
+    // count of a row varies slowly along the sorted basis, so contiguous blocks
+    // per warp would be unbalanced).  p counts the rows this warp has taken.
     const uint64_t gw = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
-    const uint64_t ntiles = (dim + R - 1) / R;
+    auto row_of = [&](uint64_t p) { return ((p >> 5) * nw + gw) * 32 + (p & 31); };
+    uint64_t next = 0;  // warp-uniform
+    const bool packed = a.ix.keys != nullptr;
 
-    for (uint64_t tile = gw; tile < ntiles; tile += nw) {
-        // ---- phase 0: rows, diagonal, term lists ---------------------------------
-        const uint64_t row = tile * (uint64_t)R + lane;
-        const bool live = lane < R && row < dim;
-        W r = 0;
-        T rinv = 0;
-        Cplx<T> diag = {T(0), T(0)};
-        int cnt = 0;
-        if (live) {
-            uint32_t nr;
-            if (packed) {
-                const uint64_t k = __ldcs(a.ix.keys + row);  // streamed once: evict first
-                r = (W)(k >> 16);
-                nr = (uint32_t)(k & 0xffff);
-            } else {
-                r = (W)__ldg(a.ix.states + row);
-                nr = __ldg(a.ix.norms + row);
-            }
-            rinv = sm_isq[nr];
-            for (int q = 0; q < n_fam; ++q) {
-                const OpFamily fm = sm_fam[q];
-                const W tq = rot_down(r, (int)fm.delta, n, full);
-#pragma unroll
-                for (int cc = 0; cc < 4; ++cc) {
-                    const int pc = popc(config_mask(r, tq, (W)fm.mask, cc));
-                    const Cplx<T> h = sm_mats[fm.mat * 16 + cc * 5];
-                    diag.re += h.re * (T)pc;
-                    diag.im += h.im * (T)pc;
-                    cnt += pc * __popc((unsigned)sm_off[fm.mat * 4 + cc]);
-                }
-            }
-        }
-        int incl = cnt;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int v = __shfl_up_sync(kAll, incl, o);
-            if (lane >= o)
-                incl += v;
-        }
-        const int first = incl - cnt;
-        const int total = __shfl_sync(kAll, incl, 31);
-        if (live) {
-            row_rinv[lane] = rinv;
-            int k = first;
-            for (int q = 0; q < n_fam; ++q) {
-                const OpFamily fm = sm_fam[q];
-                const int delta = (int)fm.delta;
-                const W tq = rot_down(r, delta, n, full);
-                for (int cc = 0; cc < 4; ++cc) {
-                    const uint32_t targets = sm_off[fm.mat * 4 + cc];
-                    if (!targets)
-                        continue;
-                    W bits = config_mask(r, tq, (W)fm.mask, cc);
-                    while (bits) {
-                        const int i = lowest_bit(bits);
-                        bits &= bits - 1;
-                        int j = i + delta;
-                        j -= j >= n ? n : 0;
-                        uint32_t tg = targets;
-                        while (tg) {
-                            const int cp = __ffs(tg) - 1;
-                            tg &= tg - 1;
-                            const int fl = cc ^ cp;
-                            a_state(k) = r ^ (W((fl >> 1) & 1) << i) ^ (W(fl & 1) << j);
-                            b_meta(k) = (uint32_t)(fm.mat * 16 + cp * 4 + cc) | ((uint32_t)lane << 16);
-                            ++k;
-                        }
-                    }
-                }
-            }
-        }
-        __syncwarp();
+    bool has = false;
+    uint64_t row = 0;
+    W r = 0, t = 0, fmask = 0, bits = 0, cur = 0;
+    T rinv = 1;
+    int f = 0, c = 0, i = 0, fdelta = 0, fmat = 0, amp = 0;
+    uint32_t cpm = 0;
+    V acc[NV];
 
-        // ---- phase A: search and look up 32 terms at a time ----------------------
-        for (int b0 = 0; b0 < total; b0 += 32) {
-            const int k = b0 + lane;
-            const bool valid = k < total;
-            const W s = valid ? a_state(k) : W(0);
-            W best;
-            int gbest = 0;
-            if (kFact) {
-                if (kTrack)
-                    rep_search_fact<W, true>(s, sm_kind, sm_masks, a.g.n_cos, a.g.rot_L, a.g.rot_d, n,
-                                             a.g.n_perm, a.g.flip, full, best, gbest);
-                else
-                    best = rep_min_fact<W>(s, sm_kind, sm_masks, a.g.n_cos, a.g.rot_L, a.g.rot_d, n,
-                                           a.g.flip, full);
-            } else {
-                rep_search<W, kTrack>(s, sm_masks, a.g.n_perm, a.g.flip, full, best, gbest);
+    // next off-diagonal term of H|r> in (family, configuration, site, target) order
+    auto advance = [&]() -> bool {
+        while (true) {
+            if (cpm) {
+                const int cp = __ffs(cpm) - 1;
+                cpm &= cpm - 1;
+                const int fl = c ^ cp;
+                int j = i + fdelta;
+                j -= j >= n ? n : 0;
+                cur = r ^ (W((fl >> 1) & 1) << i) ^ (W(fl & 1) << j);
+                amp = fmat * 16 + cp * 4 + c;
+                return true;
             }
-            if (valid) {
-                const uint32_t meta = b_meta(k);
-                uint32_t jj = 0, nj = 0;
-                bool found;
-                if (a.ix.htab) {
-                    found = find_hashed((uint64_t)best, a.ix, jj, nj);
-                } else if (packed) {
-                    found = find_key((uint64_t)best, a.ix, jj, nj);
+            if (bits) {
+                i = lowest_bit(bits);
+                bits &= bits - 1;
+                cpm = sm_off[fmat * 4 + c];
+                continue;
+            }
+            if (++c == 4) {
+                c = 0;
+                if (++f >= n_fam)
+                    return false;
+                const OpFamily fm = sm_fam[f];
+                fmask = (W)fm.mask;
+                fmat = (int)fm.mat;
+                fdelta = (int)fm.delta;
+                t = rot_down(r, fdelta, n, full);
+            }
+            bits = sm_off[fmat * 4 + c] ? config_mask(r, t, fmask, c) : W(0);
+        }
+    };
+    auto store_row = [&]() {
+#pragma unroll
+        for (int v = 0; v < NV; ++v)
+            if (v < nvec)
+                store_cs(y + row * nvec + v, acc[v]);
+    };
+
+    bool rows_left = row_of(0) < dim;
+    while (true) {
+        unsigned need = __ballot_sync(kAll, !has);
+        while (need != 0 && rows_left) {
+            const uint64_t mine = row_of(next + __popc(need & lanes_below));
+            next += __popc(need);
+            if (!has && mine < dim) {
+                row = mine;
+                if (packed) {
+                    const uint64_t k = __ldcs(a.ix.keys + row);  // streamed once: evict first
+                    r = (W)(k >> 16);
+                    rinv = sm_isq[k & 0xffff];
                 } else {
-                    const int64_t j64 = find_index((uint64_t)best, a.ix);
-                    found = j64 >= 0;
-                    if (found) {
-                        jj = (uint32_t)j64;
-                        nj = __ldg(a.ix.norms + j64);
+                    r = (W)__ldg(a.ix.states + row);
+                    rinv = sm_isq[__ldg(a.ix.norms + row)];
+                }
+                // diagonal: sum over families and configurations
+                Cplx<T> d = {T(0), T(0)};
+                for (int q = 0; q < n_fam; ++q) {
+                    const OpFamily fm = sm_fam[q];
+                    const W tq = rot_down(r, (int)fm.delta, n, full);
+#pragma unroll
+                    for (int cc = 0; cc < 4; ++cc) {
+                        const int cnt = popc(config_mask(r, tq, (W)fm.mask, cc));
+                        const Cplx<T> h = sm_mats[fm.mat * 16 + cc * 5];
+                        d.re += h.re * (T)cnt;
+                        d.im += h.im * (T)cnt;
                     }
                 }
-                C coef{};
-                if (found) {
-                    const T ratio = sm_sq[nj] * row_rinv[meta >> 16];
-                    const Cplx<T> h = sm_mats[meta & 0xffff];
-                    Cplx<T> cf = {h.re * ratio, -h.im * ratio};  // conj(h) sqrt(n'/n)
-                    if (kTrack)
-                        cf = cmul(cf, sm_chi[gbest]);
-                    if constexpr (kC)
-                        coef = cf;
-                    else
-                        coef = cf.re;
-                }
-                a_index(k) = found ? jj : 0xffffffffu;
-                b_coef(k) = coef;
-            }
-        }
-        __syncwarp();
-
-        // ---- phase B: each row lane sums its terms in list order -----------------
-        if (live) {
-            V acc[NV];
 #pragma unroll
-            for (int v = 0; v < NV; ++v) {
-                if (v < nvec) {
-                    const V xv = x[row * nvec + v];
-                    if constexpr (kC)
-                        acc[v] = cmul(conjc(diag), xv);
-                    else
-                        acc[v] = diag.re * xv;
+                for (int v = 0; v < NV; ++v) {
+                    if (v < nvec) {
+                        const V xv = x[row * nvec + v];
+                        if constexpr (kC)
+                            acc[v] = cmul(conjc(d), xv);
+                        else
+                            acc[v] = d.re * xv;
+                    }
+                }
+                // first family
+                f = 0;
+                c = -1;
+                cpm = 0;
+                bits = 0;
+                {
+                    const OpFamily fm = sm_fam[0];
+                    fmask = (W)fm.mask;
+                    fmat = (int)fm.mat;
+                    fdelta = (int)fm.delta;
+                    t = rot_down(r, fdelta, n, full);
+                }
+                if (advance())
+                    has = true;
+                else
+                    store_row();
+            }
+            rows_left = row_of(next) < dim;
+            need = __ballot_sync(kAll, !has);
+        }
+        if (need == kAll)
+            break;  // no lane holds a row and none are left
+
+        W best;
+        int gbest = 0;
+        const W s = has ? cur : W(0);
+        if (kFact) {
+            if (kTrack)
+                rep_search_fact<W, true>(s, sm_kind, sm_masks, a.g.n_cos, a.g.rot_L, a.g.rot_d, n,
+                                         a.g.n_perm, a.g.flip, full, best, gbest);
+            else
+                best = rep_min_fact<W>(s, sm_kind, sm_masks, a.g.n_cos, a.g.rot_L, a.g.rot_d, n,
+                                       a.g.flip, full);
+        } else {
+            rep_search<W, kTrack>(s, sm_masks, a.g.n_perm, a.g.flip, full, best, gbest);
+        }
+
+        if (has) {
+            uint32_t jj = 0, nj = 0;
+            bool found;
+            if (a.ix.htab) {
+                found = find_hashed((uint64_t)best, a.ix, jj, nj);
+            } else if (packed) {
+                found = find_key((uint64_t)best, a.ix, jj, nj);
+            } else {
+                const int64_t j64 = find_index((uint64_t)best, a.ix);
+                found = j64 >= 0;
+                if (found) {
+                    jj = (uint32_t)j64;
+                    nj = __ldg(a.ix.norms + j64);
                 }
             }
-            for (int k = first; k < first + cnt; ++k) {
-                const uint32_t j = a_index(k);
-                if (j == 0xffffffffu)
-                    continue;
-                const C cf = b_coef(k);
+            if (found) {
+                const uint64_t j = jj;
+                const T ratio = sm_sq[nj] * rinv;
+                const Cplx<T> h = sm_mats[amp];
+                Cplx<T> coef = {h.re * ratio, -h.im * ratio};  // conj(h) sqrt(n'/n)
+                if (kTrack)
+                    coef = cmul(coef, sm_chi[gbest]);
 #pragma unroll
                 for (int v = 0; v < NV; ++v) {
                     if (v < nvec) {
                         const V xv = x[(uint64_t)j * nvec + v];
                         if constexpr (kC) {
-                            const Cplx<T> p = cmul(cf, xv);
+                            const Cplx<T> p = cmul(coef, xv);
                             acc[v].re += p.re;
                             acc[v].im += p.im;
                         } else {
-                            acc[v] += cf * xv;
+                            acc[v] += coef.re * xv;
                         }
                     }
                 }
             }
-#pragma unroll
-            for (int v = 0; v < NV; ++v)
-                if (v < nvec)
-                    store_cs(y + row * nvec + v, acc[v]);
+            if (!advance()) {
+                store_row();
+                has = false;
+            }
         }
-        __syncwarp();
     }
 }
 
@@ -458,7 +434,7 @@ template <typename W, typename T, bool kC, bool kTrack, bool kFact, int NV>
 cudaError_t matvec_launch(const MatvecArgs &a, cudaStream_t stream)
 {
     auto kern = k_matvec<W, T, kC, kTrack, kFact, NV>;
-    const size_t smem = matvec_smem_bytes<W, T, kC, kTrack, kFact>(a.g, a.op);
+    const size_t smem = matvec_smem_bytes<W, T, kTrack, kFact>(a.g, a.op);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess)
         return e;
@@ -468,12 +444,10 @@ cudaError_t matvec_launch(const MatvecArgs &a, cudaStream_t stream)
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kMvThreads, smem);
     if (e != cudaSuccess)
         return e;
-    MatvecArgs args = a;
-    args.tile_rows = std::max(1, std::min(32, kTermCap / std::max(1, a.op.max_terms)));
-    const uint64_t tiles = (a.ix.dim + args.tile_rows - 1) / args.tile_rows;
-    const uint64_t blocks_needed = (tiles + (kMvThreads / 32) - 1) / (kMvThreads / 32);
+    const uint64_t warps_needed = (a.ix.dim + 31) / 32;
+    const uint64_t blocks_needed = (warps_needed * 32 + kMvThreads - 1) / kMvThreads;
     const int grid = (int)std::min<uint64_t>(blocks_needed, (uint64_t)sms * std::max(per_sm, 1));
-    kern<<<std::max(grid, 1), kMvThreads, smem, stream>>>(args); count_launch();
+    kern<<<std::max(grid, 1), kMvThreads, smem, stream>>>(a); count_launch();
     return cudaGetLastError();
 }
 
