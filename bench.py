@@ -315,6 +315,32 @@ def run_one_step(args, w):
     print(json.dumps({"mode": "step", "workload": w["name"], "steps": marks}))
 
 
+def run_solve(args, w):
+    """One ground-state solve per Lanczos mode (fp32 matvec and fp64), timed,
+    for workloads too large for the benchmark loop (e.g. the N=40 ring)."""
+    import torch
+    from paper_2308_16712_gb300 import ed
+    n, op = w["n_sites"], w["op"]
+    O = ed.operator_create(n, op["sites"], op["coeff"], op["local"])
+    t0 = time.perf_counter()
+    B = ed.basis_build(n, w["n_up"], w["spin_inversion"], w["perms"], w["chars"])
+    build_s = time.perf_counter() - t0
+    dim = ed.basis_size(B)
+    cplx = not ed.basis_is_real(B)
+    x0 = torch.from_numpy(ei.x_by_index(0, dim, 1, cplx)[:, 0]).cuda()
+    out = {"mode": "solve", "workload": w["name"], "dim": dim, "basis_build_s": build_s,
+           "lanczos_steps": w["lanczos_steps"]}
+    for name, mode in (("f32_matvec", ed.ED_LANCZOS_F32_MATVEC), ("f64", ed.ED_LANCZOS_F64)):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        r = ed.lanczos(O, B, x0, w["lanczos_steps"], mode)
+        torch.cuda.synchronize()
+        out[name] = {"e0": r.e0, "ritz": r.ritz, "residual": r.residual, "matvecs": r.matvecs,
+                     "matvec_ms": r.matvec_ms, "wall_s": time.perf_counter() - t0}
+    out["dE0"] = abs(out["f32_matvec"]["e0"] - out["f64"]["e0"])
+    print(json.dumps(out), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -324,7 +350,7 @@ def main():
     ap.add_argument("--workload", default="ring32")
     ap.add_argument("--nvec", type=int, default=1, help="vectors per matvec in --mode matvec")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--mode", default="job", choices=["job", "matvec", "step"],
+    ap.add_argument("--mode", default="job", choices=["job", "matvec", "step", "solve"],
                     help="job: the benchmark; matvec: only the basis build and --steps matvec "
                          "launches per dtype; step: one untimed and one more whole step "
                          "(short programs for profiler captures)")
@@ -337,6 +363,8 @@ def main():
         return run_matvec_only(args, w)
     if args.mode == "step":
         return run_one_step(args, w)
+    if args.mode == "solve":
+        return run_solve(args, w)
 
     import torch
     from paper_2308_16712_gb300 import ed
