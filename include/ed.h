@@ -75,6 +75,18 @@ typedef struct ed_operator ed_operator;
 const char *ed_status_string(ed_status status);
 
 /*
+ * ed_stream_status -- errors found on the device by work enqueued earlier.
+ * The paper's runtime needs no such call (its errors surface synchronously);
+ * here kernels run asynchronously and record violated invariants in a device
+ * status word instead of trapping (e.g. the enumeration's write pass finding a
+ * chunk whose count differs from its count pass).  Synchronises `stream`,
+ * then reads and clears the word.
+ * Returns ED_OK, ED_ERR_INTERNAL (an invariant failed) or ED_ERR_CUDA (an
+ * asynchronous launch or execution error).
+ */
+ed_status ed_stream_status(void *stream);
+
+/*
  * ed_basis_build -- enumerate the representatives of one symmetry sector
  * (Sec. "States enumeration": chunked filter of the bitstring range; the
  * filter condition is the representative test and nonzero orbit norm above).
@@ -186,6 +198,32 @@ void ed_operator_destroy(ed_operator *op);
  */
 ed_status ed_matvec(const ed_operator *op, const ed_basis *basis, const void *d_x, void *d_y,
                     int nvec, ed_dtype dtype, void *stream);
+
+/* One sector of a batched product: y = H x over `basis` (x, y as in ed_matvec). */
+typedef struct {
+    const ed_basis *basis;
+    const void *d_x;
+    void *d_y;
+} ed_sector;
+
+/*
+ * ed_matvec_multi -- y_s = H x_s for up to 160 symmetry sectors in one
+ * persistent launch (the matvec of Sec. "Matrix-vector product" applied to a
+ * batch of sectors of uneven dimension, so that no launch tail is paid per
+ * sector).  Every basis must be built from the same n_sites and the same list
+ * of lattice permutations (characters, spin inversion and n_up may differ);
+ * dtype must be complex if any sector is.  Sectors with dimension 0 are
+ * skipped.  Results equal those of ed_matvec on each sector, bit for bit.
+ *
+ *   sectors   host array of n_sectors entries
+ *   nvec, dtype, stream   as ed_matvec
+ *
+ * No allocation; no host synchronisation.  Errors: ED_ERR_INVALID_ARG (also
+ * for sectors with different permutations), ED_ERR_SYMMETRY_MISMATCH,
+ * ED_ERR_CUDA.
+ */
+ed_status ed_matvec_multi(const ed_operator *op, const ed_sector *sectors, int n_sectors, int nvec,
+                          ed_dtype dtype, void *stream);
 
 /* Lanczos precision modes. */
 typedef enum {

@@ -543,6 +543,21 @@ edk::IndexView ed_basis::index_view() const
 // ---------------------------------------------------------------------------
 extern "C" {
 
+ed_status ed_stream_status(void *stream)
+{
+    cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+    if (e != cudaSuccess) {
+        (void)cudaGetLastError();
+        return ED_ERR_CUDA;
+    }
+    unsigned int st = 0;
+    if (edk::basis_status_take(&st) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return ED_ERR_CUDA;
+    }
+    return st ? ED_ERR_INTERNAL : ED_OK;
+}
+
 const char *ed_status_string(ed_status s)
 {
     switch (s) {
@@ -752,6 +767,11 @@ ed_status ed_basis_build(int n_sites, int n_up, int spin_inversion, int n_elems,
     ED_B_TRY(cudaMemcpyAsync(flag, d_flag, 2 * sizeof(int), cudaMemcpyDeviceToHost, stream));
     ED_B_TRY(cudaStreamSynchronize(stream));
     b->max_bucket = (uint32_t)flag[1];
+    {
+        unsigned int dev_status = 0;
+        ED_B_TRY(edk::basis_status_take(&dev_status));
+        flag[0] |= (int)dev_status;
+    }
     if (dim) {
         // hash index: 2^hbits >= dim / 2 buckets (one to two states per bucket)
         int hb = 1;

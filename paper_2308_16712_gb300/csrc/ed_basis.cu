@@ -17,6 +17,11 @@ namespace {
 
 constexpr int kEnumThreads = 256;
 
+// Device-detected invariant violations of the kernels in this file (bit 0:
+// a chunk's write pass disagreed with its count pass).  Read and cleared by
+// ed_stream_status.
+__device__ unsigned int g_basis_status;
+
 __device__ __forceinline__ uint64_t unrank_colex(uint64_t rank, int n, int k, const uint64_t *binom)
 {
     uint64_t s = 0;
@@ -147,6 +152,8 @@ __global__ void __launch_bounds__(kEnumThreads) k_enumerate(EnumPlan plan, Group
         }
         if (!kWrite)
             counts[c] = kept;
+        else if (offsets[c] + kept != offsets[c + 1])
+            atomicOr(&g_basis_status, 1u);
     }
 }
 
@@ -363,6 +370,15 @@ __global__ void k_index(IndexView ix, const uint64_t *q, int64_t *out, uint64_t 
 }
 
 }  // namespace
+
+cudaError_t basis_status_take(unsigned int *status)
+{
+    unsigned int zero = 0;
+    cudaError_t e = cudaMemcpyFromSymbol(status, g_basis_status, sizeof(unsigned int));
+    if (e == cudaSuccess && *status)
+        e = cudaMemcpyToSymbol(g_basis_status, &zero, sizeof(unsigned int));
+    return e;
+}
 
 cudaError_t launch_enum_count(const EnumPlan &plan, const GroupView &g, uint32_t *counts,
                               cudaStream_t stream)

@@ -20,6 +20,8 @@ struct EnumPlan {
     const uint64_t *binom;  // device (65 x 65) binomial table
 };
 
+// Reads and clears the basis kernels' device status word (synchronous).
+cudaError_t basis_status_take(unsigned int *status);
 // Pass 1: per-chunk representative counts.
 cudaError_t launch_enum_count(const EnumPlan &plan, const GroupView &g, uint32_t *counts,
                               cudaStream_t stream);

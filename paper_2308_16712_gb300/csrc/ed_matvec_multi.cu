@@ -1,0 +1,96 @@
+// ed_matvec_multi.cu -- the batched multi-sector matvec: argument checks,
+// sector table and dtype dispatch.
+#include <algorithm>
+#include <mutex>
+#include <vector>
+
+#include "ed_matvec_multi_impl.cuh"
+
+namespace edk {
+cudaError_t multi_f64(const MultiArgs &a, bool track, cudaStream_t s) { return multi_dispatch_prec<double, false>(a, track, s); }
+cudaError_t multi_f32(const MultiArgs &a, bool track, cudaStream_t s) { return multi_dispatch_prec<float, false>(a, track, s); }
+cudaError_t multi_c128(const MultiArgs &a, bool track, cudaStream_t s) { return multi_dispatch_prec<double, true>(a, track, s); }
+cudaError_t multi_c64(const MultiArgs &a, bool track, cudaStream_t s) { return multi_dispatch_prec<float, true>(a, track, s); }
+}  // namespace edk
+
+extern "C" ed_status ed_matvec_multi(const ed_operator *op, const ed_sector *sectors, int n_sectors, int nvec,
+                                     ed_dtype dtype, void *stream)
+{
+    using namespace edk;
+    if (!op || !sectors || n_sectors < 1 || n_sectors > kMaxSectors || nvec < 1 || nvec > 16)
+        return ED_ERR_INVALID_ARG;
+    if (dtype != ED_F64 && dtype != ED_F32 && dtype != ED_C128 && dtype != ED_C64)
+        return ED_ERR_INVALID_ARG;
+    const bool cplx = dtype == ED_C128 || dtype == ED_C64;
+    const ed_basis *b0 = sectors[0].basis;
+    if (!b0)
+        return ED_ERR_INVALID_ARG;
+    static MultiArgs args;  // 17 KB: built on the host, passed by value to the kernel
+    static std::mutex args_mutex;
+    std::lock_guard<std::mutex> lock(args_mutex);
+    args.op = make_op_view(op);
+    args.g = b0->group_view();
+    args.nvec = nvec;
+    args.max_order = 0;
+    bool track = false;
+    int m = 0;
+    uint64_t tiles = 0;
+    for (int s = 0; s < n_sectors; ++s) {
+        const ed_basis *b = sectors[s].basis;
+        if (!b || b->n_sites != b0->n_sites || b->n_perm != b0->n_perm || b->perms != b0->perms)
+            return ED_ERR_INVALID_ARG;  // every sector must use the same lattice permutations
+        const ed_status st = check_pair(op, b);
+        if (st != ED_OK)
+            return st;
+        if (!cplx && !(b->real_chars && op->real))
+            return ED_ERR_INVALID_ARG;
+        if (!b->dim)
+            continue;
+        const void *x = sectors[s].d_x;
+        void *y = sectors[s].d_y;
+        if (!x || !y || x == y || (((uintptr_t)x | (uintptr_t)y) & 15))
+            return ED_ERR_INVALID_ARG;
+        if (!b->d_htab)
+            return ED_ERR_UNSUPPORTED;
+        const GroupView gv = b->group_view();
+        const IndexView iv = b->index_view();
+        SectorDesc &d = args.sec[m++];
+        d.keys = iv.keys;
+        d.states = iv.states;
+        d.norms = iv.norms;
+        d.htab = b->d_htab;
+        d.hent = b->d_hent;
+        d.chi = gv.fact ? gv.fchi : gv.chi;
+        d.chif = gv.fact ? gv.fchif : gv.chif;
+        d.x = x;
+        d.y = y;
+        d.dim = b->dim;
+        d.tile_begin = tiles;
+        d.hbits = b->hbits;
+        d.hwide = b->hwide;
+        d.norm_bits = b->norm_bits;
+        d.flip = b->spin_inversion != 0;
+        tiles += (b->dim + 31) / 32;
+        track = track || !b->trivial_chars;
+        args.max_order = std::max(args.max_order, b->order);
+    }
+    args.n_sectors = m;
+    args.total_tiles = tiles;
+    if (!m)
+        return ED_OK;
+    // the shared search uses the larger flip-expanded order only for the
+    // characters, which are per sector; the group view's own flip is unused
+    args.g.flip = 0;
+    cudaError_t e;
+    switch (dtype) {
+    case ED_F64: e = multi_f64(args, track, (cudaStream_t)stream); break;
+    case ED_F32: e = multi_f32(args, track, (cudaStream_t)stream); break;
+    case ED_C128: e = multi_c128(args, track, (cudaStream_t)stream); break;
+    default: e = multi_c64(args, track, (cudaStream_t)stream); break;
+    }
+    if (e != cudaSuccess) {
+        (void)cudaGetLastError();
+        return ED_ERR_CUDA;
+    }
+    return ED_OK;
+}

@@ -36,6 +36,10 @@ _P = ctypes.c_void_p
 _i32, _u64, _i64, _d = ctypes.c_int, ctypes.c_uint64, ctypes.c_int64, ctypes.c_double
 
 
+class Sector(ctypes.Structure):
+    _fields_ = [("basis", ctypes.c_void_p), ("d_x", ctypes.c_void_p), ("d_y", ctypes.c_void_p)]
+
+
 class LanczosInfo(ctypes.Structure):
     _fields_ = [("steps", ctypes.c_int), ("matvecs", ctypes.c_int), ("ritz", ctypes.c_double),
                 ("e0", ctypes.c_double), ("residual", ctypes.c_double),
@@ -44,6 +48,7 @@ class LanczosInfo(ctypes.Structure):
 
 _SIGS = {
     "ed_status_string": (ctypes.c_char_p, [_i32]),
+    "ed_stream_status": (_i32, [_P]),
     "ed_basis_build": (_i32, [_i32, _i32, _i32, _i32, _P, _P, _P, ctypes.POINTER(_P)]),
     "ed_basis_size": (_i32, [_P, ctypes.POINTER(_u64)]),
     "ed_basis_states": (_i32, [_P, ctypes.POINTER(_P), ctypes.POINTER(_P)]),
@@ -53,6 +58,7 @@ _SIGS = {
     "ed_operator_create": (_i32, [_i32, _i32, _P, _P, _P, ctypes.POINTER(_P)]),
     "ed_operator_destroy": (None, [_P]),
     "ed_matvec": (_i32, [_P, _P, _P, _P, _i32, _i32, _P]),
+    "ed_matvec_multi": (_i32, [_P, _P, _i32, _i32, _i32, _P]),
     "ed_lanczos": (_i32, [_P, _P, _P, _i32, _i32, ctypes.POINTER(_d), _P,
                           ctypes.POINTER(LanczosInfo), _P]),
     "ed_basis_count_noalloc": (_i32, [_i32, _i32, _i32, _i32, _P, _P, _P, ctypes.POINTER(_u64)]),
@@ -136,6 +142,11 @@ class Operator:
 
 def status_string(status: int) -> str:
     return _lib.ed_status_string(status).decode()
+
+
+def stream_status(stream=None) -> int:
+    """Synchronise the stream and return the device-detected status (0 = ok)."""
+    return int(_lib.ed_stream_status(_stream(stream)))
 
 
 def basis_build(n_sites: int, n_up: int, spin_inversion: int, perms, chars, stream=None) -> Basis:
@@ -263,6 +274,24 @@ def basis_factored(basis: Basis):
     L, d, c = _i32(), _i32(), _i32()
     f = _lib.edx_basis_factored(basis.handle, ctypes.byref(L), ctypes.byref(d), ctypes.byref(c))
     return bool(f == 1), L.value, d.value, c.value
+
+
+def matvec_multi(op: Operator, items, nvec: int = 1, stream=None):
+    """y_s = H x_s for every (basis, x, y) in ``items`` in one launch; all x and y
+    share one dtype."""
+    items = list(items)
+    if not items:
+        return
+    code = _DTYPE_CODE[str(items[0][1].dtype).replace("torch.", "")]
+    arr = (Sector * len(items))()
+    for k, (b, x, y) in enumerate(items):
+        if x.dtype != items[0][1].dtype or y.dtype != x.dtype:
+            raise ValueError("all x and y must share one dtype")
+        if not (x.is_contiguous() and y.is_contiguous()):
+            raise ValueError("x and y must be contiguous")
+        arr[k] = Sector(b.handle, x.data_ptr() if x.numel() else None, y.data_ptr() if y.numel() else None)
+    _check(_lib.ed_matvec_multi(op.handle, arr, len(items), nvec, code, _stream(stream)),
+           "ed_matvec_multi")
 
 
 @dataclass

@@ -98,6 +98,20 @@ def test_xxz28_all_sectors():
     for n_up, tot in totals.items():
         assert tot == math.comb(28, n_up)
     assert min(dims) >= 100000 and max(dims) <= 1400000
+    # all 140 sectors in one launch, nvec = 8, against the sector-by-sector product
+    items = []
+    for s in sectors:
+        B = ed.basis_build(28, s["n_up"], s["spin_inversion"], s["perms"], s["chars"])
+        st, _ = ed.basis_states(B)
+        x = ei.x_by_state_torch(5, st, 8, True, dtype=torch.complex64).contiguous()
+        items.append((B, x, torch.empty_like(x)))
+    ed.matvec_multi(O, items, 8)
+    for B, x, y in items[::7]:
+        y1 = torch.empty_like(x)
+        ed.matvec(O, B, x, y1, 8)
+        assert torch.equal(y, y1)
+    del items
+    torch.cuda.empty_cache()
     for k in (0, 33, 77, 139):  # Sz=0 z=+1 k=0; a complex Sz=0 sector; Sz=1 and Sz=3 sectors
         s = sectors[k]
         B = ed.basis_build(28, s["n_up"], s["spin_inversion"], s["perms"], s["chars"])

@@ -239,3 +239,12 @@ def test_ring32_matvec_sampled_rows(ring32):
     yf = torch.empty_like(xf)
     ed.matvec(S["O"], S["B"], xf, yf, 1)
     assert rel_err(yf.cpu().numpy()[idx, 0].astype(np.float64), want[:, 0].real) < F32_TOL
+
+
+def test_stream_status_clean_after_work():
+    torch, ed = gpu()
+    S = make(SECTORS[0], with_oracle=False)
+    x = torch.ones(S["dim"], dtype=torch.float64, device="cuda")
+    y = torch.empty_like(x)
+    ed.matvec(S["O"], S["B"], x, y, 1)
+    assert ed.stream_status() == 0
