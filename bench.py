@@ -341,6 +341,52 @@ def run_solve(args, w):
     print(json.dumps(out), flush=True)
 
 
+def run_multi(args):
+    """The XXZ ring N=28 (Jxy=1, Delta=1.5) in all 140 sectors: one
+    ed_matvec_multi launch over every sector against one ed_matvec per sector,
+    block vectors of --nvec columns, single and double precision."""
+    import torch
+    from paper_2308_16712_gb300 import ed
+    op = ei.xxz_ring(28, 1.0, 1.5)
+    O = ed.operator_create(28, op["sites"], op["coeff"], op["local"])
+    t0 = time.perf_counter()
+    bases = [ed.basis_build(28, s["n_up"], s["spin_inversion"], s["perms"], s["chars"])
+             for s in ei.xxz28_sectors()]
+    build_s = time.perf_counter() - t0
+    dims = [ed.basis_size(b) for b in bases]
+    nvec = args.nvec
+    out = {"mode": "multi", "workload": "xxz28: 140 sectors", "rows": sum(dims), "nvec": nvec,
+           "basis_build_s": build_s, "min_dim": min(dims), "max_dim": max(dims)}
+    for dt in (torch.complex64, torch.complex128):
+        items = []
+        for b in bases:
+            st, _ = ed.basis_states(b)
+            x = ei.x_by_state_torch(5, st, nvec, True, dtype=dt).contiguous()
+            items.append((b, x, torch.empty_like(x)))
+
+        def timed(fn, reps=3):
+            fn()
+            best = 1e30
+            for _ in range(reps):
+                a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record()
+                fn()
+                e.record()
+                torch.cuda.synchronize()
+                best = min(best, a.elapsed_time(e))
+            return best
+
+        ms_multi = timed(lambda: ed.matvec_multi(O, items, nvec))
+        ms_single = timed(lambda: [ed.matvec(O, b, x, y, nvec) for b, x, y in items])
+        out[str(dt).replace("torch.", "")] = {
+            "multi_ms": ms_multi, "per_sector_ms": ms_single,
+            "vector_rows_per_s_multi": nvec * sum(dims) / (ms_multi * 1e-3),
+            "vector_rows_per_s_per_sector": nvec * sum(dims) / (ms_single * 1e-3)}
+        del items
+        torch.cuda.empty_cache()
+    print(json.dumps(out), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -350,7 +396,7 @@ def main():
     ap.add_argument("--workload", default="ring32")
     ap.add_argument("--nvec", type=int, default=1, help="vectors per matvec in --mode matvec")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--mode", default="job", choices=["job", "matvec", "step", "solve"],
+    ap.add_argument("--mode", default="job", choices=["job", "matvec", "step", "solve", "multi"],
                     help="job: the benchmark; matvec: only the basis build and --steps matvec "
                          "launches per dtype; step: one untimed and one more whole step "
                          "(short programs for profiler captures)")
@@ -365,6 +411,8 @@ def main():
         return run_one_step(args, w)
     if args.mode == "solve":
         return run_solve(args, w)
+    if args.mode == "multi":
+        return run_multi(args)
 
     import torch
     from paper_2308_16712_gb300 import ed
