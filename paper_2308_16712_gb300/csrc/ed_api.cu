@@ -575,12 +575,19 @@ const char *ed_status_string(ed_status s)
     return "unknown status";
 }
 
-ed_status ed_basis_build(int n_sites, int n_up, int spin_inversion, int n_elems,
-                         const int32_t *perms, const double *chars, void *stream_, ed_basis **out)
+}  // extern "C"
+
+namespace {
+// The basis build; with count_only != null it stops after the count pass and
+// the scan and returns the sector dimension there (no basis is kept).
+ed_status basis_build_impl(int n_sites, int n_up, int spin_inversion, int n_elems,
+                           const int32_t *perms, const double *chars, void *stream_, ed_basis **out,
+                           uint64_t *count_only)
 {
-    if (!out || !perms || !chars)
+    if ((!out && !count_only) || !perms || !chars)
         return ED_ERR_INVALID_ARG;
-    *out = nullptr;
+    if (out)
+        *out = nullptr;
     if (n_sites < 1 || n_sites > 64 || n_elems < 1 || n_elems > 1024)
         return ED_ERR_INVALID_ARG;
     if (n_up < -1 || n_up > n_sites || (n_up == -1 && n_sites > 40))
@@ -727,6 +734,12 @@ ed_status ed_basis_build(int n_sites, int n_up, int spin_inversion, int n_elems,
     ED_B_TRY(cudaMemcpyAsync(&dim, d_offsets + plan.n_chunks, sizeof(uint64_t),
                              cudaMemcpyDeviceToHost, stream));
     ED_B_TRY(cudaStreamSynchronize(stream));
+    if (count_only) {
+        *count_only = dim;
+        free_basis(b);
+        cudaFree(d_counts); cudaFree(d_offsets); cudaFree(d_tmp); cudaFree(d_binom);
+        return ED_OK;
+    }
     if (dim >= (1ULL << 32)) {
         free_basis(b);
         cudaFree(d_counts); cudaFree(d_offsets); cudaFree(d_tmp); cudaFree(d_binom);
@@ -845,6 +858,24 @@ ed_status ed_basis_build(int n_sites, int n_up, int spin_inversion, int n_elems,
     }
     *out = b;
     return ED_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+ed_status ed_basis_build(int n_sites, int n_up, int spin_inversion, int n_elems,
+                         const int32_t *perms, const double *chars, void *stream, ed_basis **out)
+{
+    return basis_build_impl(n_sites, n_up, spin_inversion, n_elems, perms, chars, stream, out, nullptr);
+}
+
+ed_status ed_basis_count(int n_sites, int n_up, int spin_inversion, int n_elems, const int32_t *perms,
+                         const double *chars, void *stream, uint64_t *dim)
+{
+    if (!dim)
+        return ED_ERR_INVALID_ARG;
+    return basis_build_impl(n_sites, n_up, spin_inversion, n_elems, perms, chars, stream, nullptr, dim);
 }
 
 ed_status ed_basis_size(const ed_basis *b, uint64_t *dim)

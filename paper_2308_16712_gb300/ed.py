@@ -51,6 +51,7 @@ _SIGS = {
     "ed_stream_status": (_i32, [_P]),
     "ed_basis_build": (_i32, [_i32, _i32, _i32, _i32, _P, _P, _P, ctypes.POINTER(_P)]),
     "ed_basis_size": (_i32, [_P, ctypes.POINTER(_u64)]),
+    "ed_basis_count": (_i32, [_i32, _i32, _i32, _i32, _P, _P, _P, ctypes.POINTER(_u64)]),
     "ed_basis_states": (_i32, [_P, ctypes.POINTER(_P), ctypes.POINTER(_P)]),
     "ed_basis_is_real": (_i32, [_P, ctypes.POINTER(_i32)]),
     "ed_basis_index": (_i32, [_P, _P, _P, _u64, _P]),
@@ -159,6 +160,17 @@ def basis_build(n_sites: int, n_up: int, spin_inversion: int, perms, chars, stre
                                perms.ctypes.data_as(_P), chars.ctypes.data_as(_P), _stream(stream),
                                ctypes.byref(out)), "ed_basis_build")
     return Basis(out, n_sites)
+
+
+def basis_count(n_sites: int, n_up: int, spin_inversion: int, perms, chars, stream=None) -> int:
+    """Sector dimension from the enumeration's count pass (no basis kept)."""
+    perms = _host(perms, np.int32).reshape(-1, n_sites)
+    chars = _host(chars, np.float64).reshape(-1, 2)
+    d = ctypes.c_uint64()
+    _check(_lib.ed_basis_count(n_sites, n_up, spin_inversion, len(perms), perms.ctypes.data_as(_P),
+                               chars.ctypes.data_as(_P), _stream(stream), ctypes.byref(d)),
+           "ed_basis_count")
+    return d.value
 
 
 def basis_count_noalloc(n_sites: int, n_up: int, spin_inversion: int, perms, chars,
