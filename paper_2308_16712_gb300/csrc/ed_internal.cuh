@@ -318,47 +318,22 @@ __device__ __forceinline__ void for_each_image32(uint32_t s, const uint8_t *kind
     }
 }
 
-// Rotation left by d (0 < d < 32) of an n-bit word, 32 < n <= 64, on explicit
-// 32-bit halves (funnel shifts; no general 64-bit shift): the top d bits move
-// to the bottom.  kTopInHi: n - d >= 32, the top d bits lie in the high half.
-template <bool kTopInHi>
-__device__ __forceinline__ uint64_t rotl_words(uint64_t q, int d, int n, uint32_t mask_hi)
-{
-    const uint32_t lo = (uint32_t)q, hi = (uint32_t)(q >> 32);
-    const uint32_t top = kTopInHi ? (hi >> (n - d - 32)) : __funnelshift_r(lo, hi, n - d);
-    const uint32_t nhi = __funnelshift_l(lo, hi, d) & mask_hi;
-    const uint32_t nlo = (lo << d) | top;
-    return ((uint64_t)nhi << 32) | nlo;
-}
-
-template <bool kTopInHi, typename F>
-__device__ __forceinline__ bool rotations64(uint64_t q, int L, int d, int n, int base, int n_perm, int flip,
-                                            uint64_t full, F &f)
-{
-    const uint32_t mask_hi = (uint32_t)(full >> 32);
-    for (int b = 0; b < L; ++b) {
-        if (f(q, base + b))
-            return true;
-        if (flip && f(q ^ full, base + b + n_perm))
-            return true;
-        q = rotl_words<kTopInHi>(q, d, n, mask_hi);
-    }
-    return false;
-}
-
 // 64-bit words: the rotation is applied incrementally, rho = rotate by d.
 template <typename F>
 __device__ __forceinline__ void for_each_image64(uint64_t s, const uint8_t *kinds, const uint64_t *masks,
                                                  int n_cos, int L, int d, int n, int n_perm, int flip,
                                                  uint64_t full, F &&f)
 {
-    const bool top_in_hi = n - d >= 32;
     for (int c = 0; c < n_cos; ++c) {
-        const uint64_t q = coset_image(s, (int)kinds[c], masks + c * kMaskStride, n);
-        const bool stop = top_in_hi ? rotations64<true>(q, L, d, n, c * L, n_perm, flip, full, f)
-                                    : rotations64<false>(q, L, d, n, c * L, n_perm, flip, full, f);
-        if (stop)
-            return;
+        uint64_t q = coset_image(s, (int)kinds[c], masks + c * kMaskStride, n);
+        const int base = c * L;
+        for (int b = 0; b < L; ++b) {
+            if (f(q, base + b))
+                return;
+            if (flip && f(q ^ full, base + b + n_perm))
+                return;
+            q = ((q << d) | (q >> (n - d))) & full;
+        }
     }
 }
 

@@ -175,33 +175,13 @@ __device__ __forceinline__ W rep_min_fact(W s, const uint8_t *kinds, const W *ma
         if constexpr (sizeof(W) == 4) {
             rot_minmax32(h, L, d, n, full, mn, mx);
         } else {
-            // two chains: even rotations from h, odd ones from rho(h), stepping by 2d
-            const uint32_t mask_hi = (uint32_t)((uint64_t)full >> 32);
-            const bool top_in_hi = n - d >= 32;
-            auto minmax = [&](auto tag) {
-                constexpr bool kTop = decltype(tag)::value;
-                uint64_t q0 = h, q1 = rotl_words<kTop>(h, d, n, mask_hi);
-                uint64_t m0 = ~0ULL, m1 = ~0ULL, x0 = 0, x1 = 0;
-                int b = 0;
-                for (; b + 1 < L; b += 2) {
-                    m0 = min(m0, q0);
-                    x0 = max(x0, q0);
-                    m1 = min(m1, q1);
-                    x1 = max(x1, q1);
-                    q0 = rotl_words<kTop>(rotl_words<kTop>(q0, d, n, mask_hi), d, n, mask_hi);
-                    q1 = rotl_words<kTop>(rotl_words<kTop>(q1, d, n, mask_hi), d, n, mask_hi);
-                }
-                if (b < L) {
-                    m0 = min(m0, q0);
-                    x0 = max(x0, q0);
-                }
-                mn = min(mn, (W)min(m0, m1));
-                mx = max(mx, (W)max(x0, x1));
-            };
-            if (top_in_hi)
-                minmax(std::integral_constant<bool, true>());
-            else
-                minmax(std::integral_constant<bool, false>());
+            W q = h;
+#pragma unroll 4
+            for (int b = 0; b < L; ++b) {
+                mn = min(mn, q);
+                mx = max(mx, q);
+                q = ((q << d) | (q >> (n - d))) & full;
+            }
         }
     }
     return flip ? min(mn, (W)(mx ^ full)) : mn;
