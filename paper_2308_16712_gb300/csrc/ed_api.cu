@@ -996,6 +996,27 @@ ed_status ed_matvec(const ed_operator *op, const ed_basis *b, const void *x, voi
     return ED_OK;
 }
 
+// Diagnostics hook: exact number of stored nonzeros of H in the sector
+// (allocates an 8-byte counter; synchronises the device).  Returns 0 or -1.
+int edx_count_nnz(const ed_operator *op, const ed_basis *b, unsigned long long *out)
+{
+    if (!op || !b || !out || edk::check_pair(op, b) != ED_OK)
+        return -1;
+    *out = 0;
+    if (!b->dim)
+        return 0;
+    unsigned long long *d = nullptr;
+    if (cudaMalloc(&d, sizeof(unsigned long long)) != cudaSuccess)
+        return -1;
+    cudaError_t e = cudaMemset(d, 0, sizeof(unsigned long long));
+    if (e == cudaSuccess)
+        e = edk::launch_count_nnz(op_view(op), b->group_view(), b->index_view(), d, 0);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(out, d, sizeof(unsigned long long), cudaMemcpyDeviceToHost);
+    cudaFree(d);
+    return e == cudaSuccess ? 0 : -1;
+}
+
 // Test hook (not part of the public header): 1 = use the generic Benes search
 // for every group even when the factored form is available (both paths are
 // then exercised by the same parity tests).  Affects later launches.

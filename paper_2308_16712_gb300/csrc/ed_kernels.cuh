@@ -77,6 +77,11 @@ uint64_t binomial_host(int n, int k);
 ed_status check_pair(const ed_operator *op, const ed_basis *b);
 OpView make_op_view(const ed_operator *op);
 
+// *total += stored nonzeros of H in the sector (off-diagonal terms found in
+// the basis plus one diagonal entry per row)
+cudaError_t launch_count_nnz(const OpView &op, const GroupView &g, const IndexView &ix,
+                             unsigned long long *total, cudaStream_t stream);
+
 cudaError_t launch_matvec(const OpView &op, const GroupView &g, const IndexView &ix, bool track,
                           const void *x, void *y, int nvec, ed_dtype dtype, cudaStream_t stream);
 

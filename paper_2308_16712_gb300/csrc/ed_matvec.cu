@@ -17,3 +17,106 @@ cudaError_t launch_matvec(const OpView &op, const GroupView &g, const IndexView 
 }
 
 }  // namespace edk
+
+// ---------------------------------------------------------------------------
+// Exact count of the stored nonzeros of H in a sector: every off-diagonal term
+// whose representative is in the basis, plus one diagonal entry per row.  One
+// thread per row; counts are summed with integer atomics (order-independent).
+// ---------------------------------------------------------------------------
+namespace edk {
+namespace {
+
+template <typename W, bool kFact>
+__global__ void __launch_bounds__(256) k_count_nnz(const OpView op, const GroupView g, const IndexView ix,
+                                                   unsigned long long *total)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int nm = kFact ? g.n_cos : g.n_perm;
+    W *sm_masks = reinterpret_cast<W *>(smem);
+    uint8_t *sm_kind = reinterpret_cast<uint8_t *>(sm_masks + (size_t)nm * kMaskStride);
+    const W *gm;
+    if (kFact)
+        gm = sizeof(W) == 4 ? reinterpret_cast<const W *>(g.cos_masks32) : reinterpret_cast<const W *>(g.cos_masks64);
+    else
+        gm = sizeof(W) == 4 ? reinterpret_cast<const W *>(g.masks32) : reinterpret_cast<const W *>(g.masks64);
+    for (int e = threadIdx.x; e < nm * kMaskStride; e += blockDim.x)
+        sm_masks[e] = gm[e];
+    if (kFact)
+        for (int e = threadIdx.x; e < g.n_cos; e += blockDim.x)
+            sm_kind[e] = g.cos_kind[e];
+    __syncthreads();
+    const W full = (W)g.full;
+    const int n = g.n_sites;
+    unsigned long long cnt = 0;
+    for (uint64_t row = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; row < ix.dim;
+         row += (uint64_t)gridDim.x * blockDim.x) {
+        const W r = (W)ix.states[row];
+        cnt += 1;  // the diagonal entry
+        for (int q = 0; q < op.n_fam; ++q) {
+            const OpFamily fm = op.fams[q];
+            int j = 0;
+            const W tq = (W)(((uint64_t)r >> fm.delta | (uint64_t)r << (n - fm.delta)) & g.full);
+            for (int cc = 0; cc < 4; ++cc) {
+                const uint32_t targets = op.offmask[fm.mat * 4 + cc];
+                if (!targets)
+                    continue;
+                const W a = (cc & 2) ? r : (W)~r, b = (cc & 1) ? tq : (W)~tq;
+                W bits = a & b & (W)fm.mask;
+                while (bits) {
+                    const int i = sizeof(W) == 4 ? __ffs((uint32_t)bits) - 1 : __ffsll((long long)bits) - 1;
+                    bits &= bits - 1;
+                    j = i + (int)fm.delta;
+                    j -= j >= n ? n : 0;
+                    uint32_t tg = targets;
+                    while (tg) {
+                        const int cp = __ffs(tg) - 1;
+                        tg &= tg - 1;
+                        const int fl = cc ^ cp;
+                        const W s = r ^ (W((fl >> 1) & 1) << i) ^ (W(fl & 1) << j);
+                        W best;
+                        int gb;
+                        if (kFact)
+                            rep_search_fact<W, false>(s, sm_kind, sm_masks, g.n_cos, g.rot_L, g.rot_d, n, g.n_perm,
+                                                      g.flip, full, best, gb);
+                        else
+                            rep_search<W, false>(s, sm_masks, g.n_perm, g.flip, full, best, gb);
+                        cnt += find_index((uint64_t)best, ix) >= 0 ? 1 : 0;
+                    }
+                }
+            }
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1)
+        cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+    if ((threadIdx.x & 31) == 0)
+        atomicAdd(total, cnt);
+}
+
+template <typename W, bool kFact>
+cudaError_t nnz_launch(const OpView &op, const GroupView &g, const IndexView &ix, unsigned long long *total,
+                       cudaStream_t stream)
+{
+    const int nm = kFact ? g.n_cos : g.n_perm;
+    const size_t smem = (size_t)nm * kMaskStride * sizeof(W) + (size_t)g.n_cos + 16;
+    auto kern = k_count_nnz<W, kFact>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess)
+        return e;
+    const uint64_t blocks = std::max<uint64_t>(1, std::min<uint64_t>((ix.dim + 255) / 256, 152 * 16));
+    kern<<<(unsigned)blocks, 256, smem, stream>>>(op, g, ix, total); count_launch();
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_count_nnz(const OpView &op, const GroupView &g, const IndexView &ix,
+                             unsigned long long *total, cudaStream_t stream)
+{
+    if (g.n_sites <= 32)
+        return g.fact ? nnz_launch<uint32_t, true>(op, g, ix, total, stream)
+                      : nnz_launch<uint32_t, false>(op, g, ix, total, stream);
+    return g.fact ? nnz_launch<uint64_t, true>(op, g, ix, total, stream)
+                  : nnz_launch<uint64_t, false>(op, g, ix, total, stream);
+}
+
+}  // namespace edk

@@ -65,6 +65,7 @@ _SIGS = {
     "ed_basis_count_noalloc": (_i32, [_i32, _i32, _i32, _i32, _P, _P, _P, ctypes.POINTER(_u64)]),
     "edx_launch_count": (ctypes.c_ulonglong, []),
     "edx_force_generic": (None, [_i32]),
+    "edx_count_nnz": (_i32, [_P, _P, ctypes.POINTER(ctypes.c_ulonglong)]),
     "edx_force_prefix_search": (None, [_i32]),
     "edx_basis_hash": (_i32, [_P, ctypes.POINTER(_i32), ctypes.POINTER(ctypes.c_uint32), ctypes.POINTER(_i32)]),
     "edx_basis_table": (_i32, [_P, ctypes.POINTER(_u64), ctypes.POINTER(ctypes.c_uint32), ctypes.POINTER(_i32)]),
@@ -259,6 +260,14 @@ def force_generic(on: bool) -> None:
     """Testing aid: use the generic Benes group search even where the factored
     (rotation x coset) search applies.  Affects later launches and builds."""
     _lib.edx_force_generic(1 if on else 0)
+
+
+def count_nnz(op: Operator, basis: Basis) -> int:
+    """Exact number of stored nonzeros of H in the sector (diagnostics)."""
+    v = ctypes.c_ulonglong()
+    if _lib.edx_count_nnz(op.handle, basis.handle, ctypes.byref(v)) != 0:
+        raise RuntimeError("edx_count_nnz failed")
+    return int(v.value)
 
 
 def force_prefix_search(on: bool) -> None:

@@ -248,3 +248,13 @@ def test_stream_status_clean_after_work():
     y = torch.empty_like(x)
     ed.matvec(S["O"], S["B"], x, y, 1)
     assert ed.stream_status() == 0
+
+
+@pytest.mark.parametrize("case", SECTORS[:9], ids=[s[0] for s in SECTORS[:9]])
+def test_nnz_count_matches_oracle(case):
+    torch, ed = gpu()
+    S = make(case)
+    # off-diagonal terms whose representative has nonzero norm, plus one
+    # diagonal entry per row (the oracle's per-row count)
+    _, nnz = oracle.rows_statex(S["G"], S["H"], S["st"], 0)
+    assert ed.count_nnz(S["O"], S["B"]) == int(nnz.sum())
