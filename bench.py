@@ -384,6 +384,34 @@ def run_multi(args):
             "vector_rows_per_s_per_sector": nvec * sum(dims) / (ms_single * 1e-3)}
         del items
         torch.cuda.empty_cache()
+    steps = args.lanczos_steps
+    if steps > 0:
+        # all 140 lowest energies: one batched, graph-replayed solve against
+        # ed_lanczos sector by sector (fp32 matvec, fp64 recurrence + refinement)
+        mode = ed.ED_LANCZOS_F32_MATVEC
+        xs = []
+        for b in bases:
+            st, _ = ed.basis_states(b)
+            xs.append(ei.x_by_state_torch(5, st, 1, True, dtype=torch.complex128).reshape(-1).contiguous())
+        items = [(b, x, None) for b, x in zip(bases, xs)]
+        ed.lanczos_multi(O, items, 3, mode)  # warm-up
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        res = ed.lanczos_multi(O, items, steps, mode)
+        t_multi = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        res1 = [ed.lanczos(O, b, x, steps, mode) for b, x in zip(bases, xs)]
+        t_single = time.perf_counter() - t0
+        e_sz = {}
+        for s, r in zip(ei.xxz28_sectors(), res):
+            e_sz[s["n_up"] - 14] = min(e_sz.get(s["n_up"] - 14, float("inf")), r.e0)
+        out["lanczos"] = {
+            "steps": steps, "mode": "f32_matvec", "sectors": len(items),
+            "batched_s": t_multi, "per_sector_s": t_single,
+            "matvecs_batched": res[0].matvecs,
+            "max_rel_dE0_vs_per_sector": max(abs(a.e0 - b.e0) / abs(b.e0) for a, b in zip(res, res1)),
+            "max_residual": max(r.residual for r in res),
+            "e0_min_by_sz": e_sz}
     print(json.dumps(out), flush=True)
 
 
@@ -395,6 +423,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="ring32")
     ap.add_argument("--nvec", type=int, default=1, help="vectors per matvec in --mode matvec")
+    ap.add_argument("--lanczos-steps", type=int, default=100,
+                    help="Lanczos steps of the batched solve in --mode multi (0: skip)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--mode", default="job", choices=["job", "matvec", "step", "solve", "multi"],
                     help="job: the benchmark; matvec: only the basis build and --steps matvec "

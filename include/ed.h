@@ -280,6 +280,48 @@ ed_status ed_lanczos(const ed_operator *op, const ed_basis *basis, const void *d
                      int mode, double *e0_out, void *d_vec_out, ed_lanczos_info *info,
                      void *stream);
 
+/*
+ * ed_lanczos_multi -- lowest eigenvalue of H in each of up to 160 symmetry
+ * sectors, by the recurrence of ed_lanczos run on all sectors together
+ * (Sec. "Introduction": symmetries make H block diagonal, one independent
+ * eigenproblem of reduced dimension per block; here many blocks at once).
+ * Every product is one multi-sector launch as in ed_matvec_multi, or, when
+ * every sector alone fills the GPU (at least one row per resident thread), one
+ * ed_matvec launch per sector; the vector updates and the compensated fp64 dot
+ * products are segmented per sector; each run of steps is captured once as a
+ * CUDA graph of two steps and replayed.
+ * The sectors follow the rules of ed_matvec_multi (same n_sites and lattice
+ * permutations); every sector must be non-empty.
+ *
+ *   sectors   host array; d_x = device start vector (dim values of `dtype`,
+ *             need not be normalised), d_y = device output for the normalised
+ *             ground-state approximation (may be NULL)
+ *   steps     1..10000 Lanczos steps, the same for every sector; a sector that
+ *             reaches an invariant subspace stops contributing early
+ *   mode      ED_LANCZOS_F64 or ED_LANCZOS_F32_MATVEC, optionally OR-ed with
+ *             ED_LANCZOS_RECOMPUTE (form the Ritz vectors by a second pass even
+ *             when the Lanczos vectors would fit in memory)
+ *   dtype     ED_F64 (every sector and H real) or ED_C128: the type of d_x, d_y
+ *   e0_out    host, n_sectors energies (may be NULL)
+ *   info      host, n_sectors entries (may be NULL); matvecs counts the batched
+ *             products; matvec_ms is 0 (products inside a graph are not timed
+ *             one by one)
+ *
+ * The Lanczos vectors are kept when they fit in half of the free device
+ * memory (in the fp32-matvec mode as the fp32 copies the products consumed:
+ * that Ritz vector only starts the fp64 refinement), else the Ritz vectors
+ * come from a second, bit-identical pass.  Per sector the energy is the fp64
+ * Rayleigh quotient of its final vector, as ed_lanczos returns.  Allocates
+ * its work vectors (five fp64 vectors of the summed dimension, two fp32 ones
+ * in the fp32-matvec mode, and the kept Lanczos vectors); synchronises
+ * `stream` before returning.  Not to be called while `stream` is being
+ * captured.  Errors: ED_ERR_INVALID_ARG, ED_ERR_SYMMETRY_MISMATCH,
+ * ED_ERR_UNSUPPORTED (a basis without the hash index), ED_ERR_OOM, ED_ERR_CUDA.
+ */
+ed_status ed_lanczos_multi(const ed_operator *op, const ed_sector *sectors, int n_sectors, int steps,
+                           int mode, ed_dtype dtype, double *e0_out, ed_lanczos_info *info,
+                           void *stream);
+
 #ifdef __cplusplus
 }
 #endif

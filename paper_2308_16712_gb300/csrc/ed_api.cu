@@ -482,6 +482,8 @@ uint64_t binomial_host(int n, int k) { return binomial(n, k); }
 
 static std::atomic<unsigned long long> g_launches{0};
 void count_launch(unsigned n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+void uncount_launch(unsigned n) { g_launches.fetch_sub(n, std::memory_order_relaxed); }
+unsigned long long launches_so_far() { return g_launches.load(std::memory_order_relaxed); }
 
 // Operator/basis compatibility and the symmetry check (cached per basis).
 ed_status check_pair(const ed_operator *op, const ed_basis *b)

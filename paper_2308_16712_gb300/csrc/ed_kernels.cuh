@@ -9,6 +9,10 @@ namespace edk {
 
 // Kernel launches issued by the library since it was loaded (diagnostics).
 void count_launch(unsigned n = 1);
+// Takes back n counted launches (kernels recorded into a graph by stream
+// capture are counted again each time the graph is launched).
+void uncount_launch(unsigned n);
+unsigned long long launches_so_far();
 
 // ---- basis build (Sec. "States enumeration") --------------------------------
 struct EnumPlan {

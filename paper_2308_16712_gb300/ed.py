@@ -62,6 +62,8 @@ _SIGS = {
     "ed_matvec_multi": (_i32, [_P, _P, _i32, _i32, _i32, _P]),
     "ed_lanczos": (_i32, [_P, _P, _P, _i32, _i32, ctypes.POINTER(_d), _P,
                           ctypes.POINTER(LanczosInfo), _P]),
+    "ed_lanczos_multi": (_i32, [_P, _P, _i32, _i32, _i32, _i32, ctypes.POINTER(_d),
+                                ctypes.POINTER(LanczosInfo), _P]),
     "ed_basis_count_noalloc": (_i32, [_i32, _i32, _i32, _i32, _P, _P, _P, ctypes.POINTER(_u64)]),
     "edx_launch_count": (ctypes.c_ulonglong, []),
     "edx_force_generic": (None, [_i32]),
@@ -334,3 +336,27 @@ def lanczos(op: Operator, basis: Basis, x0, steps: int, mode: int = ED_LANCZOS_F
                            _stream(stream)), "ed_lanczos")
     return LanczosResult(e0.value, info.steps, info.matvecs, info.ritz, info.residual,
                          info.matvec_ms)
+
+
+def lanczos_multi(op: Operator, items, steps: int, mode: int = ED_LANCZOS_F64,
+                  stream=None) -> list:
+    """Lowest energy of every (basis, x0, vec_out or None) in ``items`` by one
+    batched Lanczos run; x0 (and vec_out) are float64 for every sector, or
+    complex128 for every sector."""
+    items = list(items)
+    if not items:
+        return []
+    code = _DTYPE_CODE[str(items[0][1].dtype).replace("torch.", "")]
+    arr = (Sector * len(items))()
+    for k, (b, x, v) in enumerate(items):
+        if x.dtype != items[0][1].dtype or (v is not None and v.dtype != x.dtype):
+            raise ValueError("all start and output vectors must share one dtype")
+        if not x.is_contiguous() or (v is not None and not v.is_contiguous()):
+            raise ValueError("vectors must be contiguous")
+        arr[k] = Sector(b.handle, x.data_ptr(), v.data_ptr() if v is not None else None)
+    e0 = (ctypes.c_double * len(items))()
+    info = (LanczosInfo * len(items))()
+    _check(_lib.ed_lanczos_multi(op.handle, arr, len(items), steps, mode, code, e0, info,
+                                 _stream(stream)), "ed_lanczos_multi")
+    return [LanczosResult(e0[k], info[k].steps, info[k].matvecs, info[k].ritz, info[k].residual,
+                          info[k].matvec_ms) for k in range(len(items))]
