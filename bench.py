@@ -589,7 +589,7 @@ def main():
         "matvec_kernel": mv,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_int, "unit": "TOP/s",
                      "frac": achieved / peak_int, "traffic": None,
-                     "kernel": "k_matvec (fp32, " + ("rotation x coset" if fact else "Benes")
+                     "kernel": "k_matvec_tp (term-parallel, fp32, " + ("rotation x coset" if fact else "Benes")
                                + f" group search, {'32' if n <= 32 else '64'}-bit words)",
                      "int_ops_per_launch": int_ops, "int_ops_per_term": ops_term,
                      "peak_basis": f"{SMS} SMs x {INT_LANES_PER_SM} INT32 lanes x "

@@ -201,6 +201,14 @@ void ed_operator_destroy(ed_operator *op);
  *   dtype     ED_F64 / ED_F32 (real sectors only) or ED_C128 / ED_C64;
  *             the arithmetic is done in that precision
  *
+ * Two kernels: rows handed to lanes (each lane walks its row's terms), and,
+ * for nvec = 1 in single precision with an operator whose off-diagonal
+ * entries only exchange antiparallel spins (|01> <-> |10>), a term-parallel
+ * kernel (a warp lays a tile's terms out flat, one term per lane per round,
+ * and sums each row with a segmented warp scan).  The two sum a row's terms in
+ * different orders, so a column of an nvec > 1 product may differ from the
+ * nvec = 1 product in the last bits.
+ *
  * No allocation and no host synchronisation.  Deterministic: the same inputs
  * give bit-identical y.  Errors: ED_ERR_INVALID_ARG (including a complex
  * sector with a real dtype, or operator/basis with different n_sites),

@@ -422,8 +422,16 @@ ed_operator *build_operator_host(int n_sites, int n_terms, const double *coeff,
 
 edk::OpView op_view(const ed_operator *op)
 {
+    // exchange only: no off-diagonal entry leaves configurations 1 and 2, and
+    // each of them only reaches the other
+    int exch = 1;
+    for (int k = 0; k < op->n_mats; ++k) {
+        const uint8_t *m = op->h_offmask.data() + (size_t)k * 4;
+        if (m[0] || m[3] || (m[1] & ~4u) || (m[2] & ~2u))
+            exch = 0;
+    }
     return edk::OpView{(int)op->h_fams.size(), op->n_mats, op->max_offdiag, op->d_fams, op->d_mats,
-                       op->d_matsf, op->d_offmask};
+                       op->d_matsf, op->d_offmask, exch};
 }
 
 }  // namespace

@@ -68,6 +68,7 @@ struct OpView {
     const double2 *mats;     // n_mats x 16, coeff * h
     const float2 *matsf;
     const uint8_t *offmask;  // n_mats x 4: bit c' set if h[c'][c] != 0, c' != c
+    int exchange_only;       // every off-diagonal entry couples |01> and |10>
 };
 
 // Host tables (generic group search) for counting a sector; validates the group.
@@ -88,5 +89,12 @@ cudaError_t launch_count_nnz(const OpView &op, const GroupView &g, const IndexVi
 
 cudaError_t launch_matvec(const OpView &op, const GroupView &g, const IndexView &ix, bool track,
                           const void *x, void *y, int nvec, ed_dtype dtype, cudaStream_t stream);
+
+// Kernel choice for one vector and an exchange-only operator: 0 = the
+// term-parallel kernel in single precision, the row-per-lane kernel in double
+// precision (where the term-parallel kernel's fp64 segmented sums cost more
+// than they save); 1 = always row-per-lane; 2 = always term-parallel.
+extern int g_kernel_policy;
+bool use_term_parallel(int nvec, const OpView &op, ed_dtype dtype);
 
 }  // namespace edk

@@ -564,9 +564,7 @@ ed_status run_multi(const ed_operator *op, const ed_sector *sectors, int ns, int
             tiles += (b->dim + 31) / 32;
         }
         a.total_tiles = tiles;
-        if (single)
-            return C ? multi_c64(a, track, s) : multi_f32(a, track, s);
-        return C ? multi_c128(a, track, s) : multi_f64(a, track, s);
+        return multi_launch_any(a, track, single ? (C ? ED_C64 : ED_F32) : (C ? ED_C128 : ED_F64), s);
     };
 
     // Lanczos step j (j on the device): w = H v - alpha_j v - beta_j vp,

@@ -1,11 +1,51 @@
-// ed_matvec.cu -- dtype dispatch of the matvec kernels.
-#include "ed_matvec_impl.cuh"
+// ed_matvec.cu -- kernel choice and dtype dispatch of the matvec.
+#include "ed_matvec_tp.cuh"
 
 namespace edk {
+
+int g_kernel_policy = 0;
+
+bool use_term_parallel(int nvec, const OpView &op, ed_dtype dtype)
+{
+    if (nvec != 1 || !op.exchange_only || g_kernel_policy == 1)
+        return false;
+    return g_kernel_policy == 2 || dtype == ED_F32 || dtype == ED_C64;
+}
 
 cudaError_t launch_matvec(const OpView &op, const GroupView &g, const IndexView &ix, bool track,
                           const void *x, void *y, int nvec, ed_dtype dtype, cudaStream_t stream)
 {
+    if (ix.htab && use_term_parallel(nvec, op, dtype)) {
+        TpArgs<1> t;
+        t.op = op;
+        t.g = g;
+        t.n_sectors = 1;
+        t.max_order = g.order;
+        t.total_tiles = (ix.dim + 31) / 32;
+        SectorDesc &d = t.sec[0];
+        d.keys = ix.keys;
+        d.states = ix.states;
+        d.norms = ix.norms;
+        d.htab = ix.htab;
+        d.hent = ix.hent;
+        d.chi = g.fact ? g.fchi : g.chi;
+        d.chif = g.fact ? g.fchif : g.chif;
+        d.x = x;
+        d.y = y;
+        d.dim = ix.dim;
+        d.tile_begin = 0;
+        d.hbits = ix.hbits;
+        d.hwide = ix.hwide;
+        d.norm_bits = ix.norm_bits;
+        d.flip = g.flip;
+        switch (dtype) {
+        case ED_F64: return tp_single_f64(t, track, ix.hwide != 0, stream);
+        case ED_F32: return tp_single_f32(t, track, ix.hwide != 0, stream);
+        case ED_C128: return tp_single_c128(t, track, ix.hwide != 0, stream);
+        case ED_C64: return tp_single_c64(t, track, ix.hwide != 0, stream);
+        }
+        return cudaErrorInvalidValue;
+    }
     const MatvecArgs a{op, g, ix, x, y, nvec};
     switch (dtype) {
     case ED_F64: return matvec_f64(a, track, stream);
@@ -120,3 +160,5 @@ cudaError_t launch_count_nnz(const OpView &op, const GroupView &g, const IndexVi
 }
 
 }  // namespace edk
+
+extern "C" void edx_kernel_policy(int policy) { edk::g_kernel_policy = policy; }

@@ -4,13 +4,48 @@
 #include <mutex>
 #include <vector>
 
-#include "ed_matvec_multi_impl.cuh"
+#include "ed_matvec_tp.cuh"
 
 namespace edk {
 cudaError_t multi_f64(const MultiArgs &a, bool track, cudaStream_t s) { return multi_dispatch_prec<double, false>(a, track, s); }
 cudaError_t multi_f32(const MultiArgs &a, bool track, cudaStream_t s) { return multi_dispatch_prec<float, false>(a, track, s); }
 cudaError_t multi_c128(const MultiArgs &a, bool track, cudaStream_t s) { return multi_dispatch_prec<double, true>(a, track, s); }
 cudaError_t multi_c64(const MultiArgs &a, bool track, cudaStream_t s) { return multi_dispatch_prec<float, true>(a, track, s); }
+
+// The batched product: the term-parallel kernel where use_term_parallel
+// chooses it (its warps take tiles of one sector each), else the row-per-lane
+// multi-sector kernel.
+cudaError_t multi_launch_any(const MultiArgs &a, bool track, ed_dtype dtype, cudaStream_t s)
+{
+    bool same_width = true;
+    for (int k = 1; k < a.n_sectors; ++k)
+        same_width = same_width && (a.sec[k].hwide != 0) == (a.sec[0].hwide != 0);
+    if (same_width && use_term_parallel(a.nvec, a.op, dtype)) {
+        const bool wide = a.n_sectors > 0 && a.sec[0].hwide != 0;
+        static thread_local TpArgs<kMaxSectors> t;  // host staging (17 KB); copied at launch
+        t.op = a.op;
+        t.g = a.g;
+        t.n_sectors = a.n_sectors;
+        t.max_order = a.max_order;
+        t.total_tiles = a.total_tiles;
+        for (int k = 0; k < a.n_sectors; ++k)
+            t.sec[k] = a.sec[k];
+        switch (dtype) {
+        case ED_F64: return tp_multi_f64(t, track, wide, s);
+        case ED_F32: return tp_multi_f32(t, track, wide, s);
+        case ED_C128: return tp_multi_c128(t, track, wide, s);
+        case ED_C64: return tp_multi_c64(t, track, wide, s);
+        }
+        return cudaErrorInvalidValue;
+    }
+    switch (dtype) {
+    case ED_F64: return multi_f64(a, track, s);
+    case ED_F32: return multi_f32(a, track, s);
+    case ED_C128: return multi_c128(a, track, s);
+    case ED_C64: return multi_c64(a, track, s);
+    }
+    return cudaErrorInvalidValue;
+}
 }  // namespace edk
 
 extern "C" ed_status ed_matvec_multi(const ed_operator *op, const ed_sector *sectors, int n_sectors, int nvec,
@@ -81,13 +116,7 @@ extern "C" ed_status ed_matvec_multi(const ed_operator *op, const ed_sector *sec
     // the shared search uses the larger flip-expanded order only for the
     // characters, which are per sector; the group view's own flip is unused
     args.g.flip = 0;
-    cudaError_t e;
-    switch (dtype) {
-    case ED_F64: e = multi_f64(args, track, (cudaStream_t)stream); break;
-    case ED_F32: e = multi_f32(args, track, (cudaStream_t)stream); break;
-    case ED_C128: e = multi_c128(args, track, (cudaStream_t)stream); break;
-    default: e = multi_c64(args, track, (cudaStream_t)stream); break;
-    }
+    const cudaError_t e = multi_launch_any(args, track, dtype, (cudaStream_t)stream);
     if (e != cudaSuccess) {
         (void)cudaGetLastError();
         return ED_ERR_CUDA;

@@ -399,5 +399,6 @@ cudaError_t multi_f64(const MultiArgs &a, bool track, cudaStream_t s);
 cudaError_t multi_f32(const MultiArgs &a, bool track, cudaStream_t s);
 cudaError_t multi_c128(const MultiArgs &a, bool track, cudaStream_t s);
 cudaError_t multi_c64(const MultiArgs &a, bool track, cudaStream_t s);
+cudaError_t multi_launch_any(const MultiArgs &a, bool track, ed_dtype dtype, cudaStream_t s);
 
 }  // namespace edk

@@ -69,6 +69,7 @@ _SIGS = {
     "edx_force_generic": (None, [_i32]),
     "edx_count_nnz": (_i32, [_P, _P, ctypes.POINTER(ctypes.c_ulonglong)]),
     "edx_force_prefix_search": (None, [_i32]),
+    "edx_kernel_policy": (None, [_i32]),
     "edx_basis_hash": (_i32, [_P, ctypes.POINTER(_i32), ctypes.POINTER(ctypes.c_uint32), ctypes.POINTER(_i32)]),
     "edx_basis_table": (_i32, [_P, ctypes.POINTER(_u64), ctypes.POINTER(ctypes.c_uint32), ctypes.POINTER(_i32)]),
     "edx_basis_factored": (_i32, [_P, ctypes.POINTER(_i32), ctypes.POINTER(_i32), ctypes.POINTER(_i32)]),
@@ -270,6 +271,16 @@ def count_nnz(op: Operator, basis: Basis) -> int:
     if _lib.edx_count_nnz(op.handle, basis.handle, ctypes.byref(v)) != 0:
         raise RuntimeError("edx_count_nnz failed")
     return int(v.value)
+
+
+KERNEL_POLICIES = {"auto": 0, "rowwise": 1, "term_parallel": 2}
+
+
+def kernel_policy(policy: str) -> None:
+    """Testing aid: which matvec kernel serves one vector of an exchange-only
+    operator: "auto" (term-parallel in single precision, row-per-lane in double),
+    "rowwise" or "term_parallel" (both precisions).  Affects later launches."""
+    _lib.edx_kernel_policy(KERNEL_POLICIES[policy])
 
 
 def force_prefix_search(on: bool) -> None:

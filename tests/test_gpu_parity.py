@@ -19,6 +19,22 @@ pytestmark = pytest.mark.gpu
 F64_TOL = 1e-12
 F32_TOL = 2e-6
 
+def xx_ring(n):
+    """J Sx_i Sx_{i+1} (no U(1) symmetry: couples |00> <-> |11> as well)."""
+    h = np.zeros((4, 4))
+    h[0, 3] = h[3, 0] = h[1, 2] = h[2, 1] = 0.25
+    return ei.make_operator([(i, (i + 1) % n) for i in range(n)], [1.0] * n, h)
+
+
+def dm_ring(n, d):
+    """Heisenberg ring plus a uniform Dzyaloshinskii-Moriya coupling
+    d (Sx_i Sy_j - Sy_i Sx_j): exchange-only, with imaginary matrix entries."""
+    op = ei.heisenberg_ring(n)
+    op["local"][:, 4 * 2 + 1, 1] = 0.5 * d   # h[2][1] = +i d/2 (row-major 4x4)
+    op["local"][:, 4 * 1 + 2, 1] = -0.5 * d  # h[1][2] = -i d/2
+    return op
+
+
 SECTORS = [
     # name, n, n_up, z, group builder, operator
     ("ring16_k0_p+_z+", 16, 8, +1, lambda: ei.ring_group(16, 0, +1), lambda: ei.heisenberg_ring(16)),
@@ -37,6 +53,8 @@ SECTORS = [
     ("ring8_nup0", 8, 0, 0, lambda: ei.ring_group(8, 0), lambda: ei.heisenberg_ring(8)),
     ("ring8_nup8", 8, 8, 0, lambda: ei.ring_group(8, 0), lambda: ei.heisenberg_ring(8)),
     ("ring8_empty", 8, 4, -1, lambda: ei.ring_group(8, 4, -1), lambda: ei.heisenberg_ring(8)),
+    ("ring10_noU1_xx_z-", 10, -1, -1, lambda: ei.ring_group(10, 0, +1), lambda: xx_ring(10)),
+    ("ring11_dm_k2", 11, 5, 0, lambda: ei.ring_group(11, 2), lambda: dm_ring(11, 0.3)),
 ]
 
 
@@ -46,17 +64,23 @@ def make(case, with_oracle=True):
     return build_pair(n, n_up, z, p, c, opf(), with_oracle)
 
 
-@pytest.fixture(params=["factored", "generic", "prefix"], autouse=True)
+@pytest.fixture(params=["factored", "generic", "prefix", "rowwise", "term_parallel"], autouse=True)
 def search_mode(request):
-    """Run every parity test three times: factored (rotation x coset) group
+    """Run every parity test five times: factored (rotation x coset) group
     search with the hash index; generic Benes search over every element with
-    the hash index; factored search with the prefix-table binary search."""
+    the hash index; factored search with the prefix-table binary search (the
+    row-per-lane kernel); factored search and hash index with the row-per-lane
+    kernel forced; and with the term-parallel kernel forced in both precisions
+    (it otherwise serves single vectors of exchange-only operators in single
+    precision only)."""
     torch, ed = gpu()
     ed.force_generic(request.param == "generic")
     ed.force_prefix_search(request.param == "prefix")
+    ed.kernel_policy(request.param if request.param in ("rowwise", "term_parallel") else "auto")
     yield request.param
     ed.force_generic(False)
     ed.force_prefix_search(False)
+    ed.kernel_policy("auto")
 
 
 @pytest.mark.parametrize("case", SECTORS, ids=[s[0] for s in SECTORS])
@@ -131,7 +155,10 @@ def test_matvec_f32_error_bounded(case, nvec):
     assert err < F32_TOL, err
 
 
-def test_matvec_nvec_columns_equal_single_products():
+def test_matvec_nvec_columns_equal_single_products(search_mode):
+    """Block products equal the single products of the row-per-lane kernel bit
+    for bit (same per-row summation order), and those of the term-parallel
+    kernel to rounding."""
     torch, ed = gpu()
     S = make(SECTORS[7], with_oracle=False)
     x = ei.x_by_index(9, S["dim"], 5, True)
@@ -141,8 +168,39 @@ def test_matvec_nvec_columns_equal_single_products():
     for v in range(5):
         xv = xt[:, v].contiguous()
         yv = torch.empty_like(xv)
-        ed.matvec(S["O"], S["B"], xv, yv, 1)
+        ed.kernel_policy("rowwise")
+        try:
+            ed.matvec(S["O"], S["B"], xv, yv, 1)
+        finally:
+            ed.kernel_policy(search_mode if search_mode in ("rowwise", "term_parallel") else "auto")
         assert torch.equal(yv, yt[:, v])
+        ed.matvec(S["O"], S["B"], xv, yv, 1)
+        assert float((yv - yt[:, v]).abs().max()) <= 1e-13 * float(yt[:, v].abs().max())
+
+
+@pytest.mark.parametrize("case", SECTORS, ids=[s[0] for s in SECTORS])
+def test_term_parallel_matches_rowwise(case, search_mode):
+    """The term-parallel kernel (one vector) against the row-per-lane kernel:
+    fp64 to 1e-13 of max|y| (summation order only), fp32 to 1e-6."""
+    if search_mode != "factored":
+        pytest.skip("compared once")
+    torch, ed = gpu()
+    S = make(case, with_oracle=False)
+    if S["dim"] == 0:
+        pytest.skip("empty sector")
+    cplx = not ed.basis_is_real(S["B"])
+    for dt, tol in (((np.complex128 if cplx else np.float64), 1e-13), ((np.complex64 if cplx else np.float32), 1e-6)):
+        xt = to_torch(ei.x_by_index(29, S["dim"], 1, cplx)[:, 0], dt)
+        y_tp, y_rw = torch.empty_like(xt), torch.empty_like(xt)
+        ed.kernel_policy("term_parallel")
+        try:
+            ed.matvec(S["O"], S["B"], xt, y_tp, 1)
+            ed.kernel_policy("rowwise")
+            ed.matvec(S["O"], S["B"], xt, y_rw, 1)
+        finally:
+            ed.kernel_policy("auto")
+        scale = float(y_rw.abs().max())
+        assert float((y_tp - y_rw).abs().max()) <= tol * max(scale, 1e-300)
 
 
 def test_argument_errors():
