@@ -43,6 +43,11 @@ L2_BYTES = 129 * 1024 * 1024
 # maximum SM clock (GB300 SM: 4 sub-partitions x 16 INT32 lanes).
 SMS = 152
 INT_LANES_PER_SM = 64
+# DRAM bytes (read + write) of one launch of the timed kernel, from one ncu
+# capture of it (--set full, which starts every replay with a cold L2); keyed by
+# workload.  Retake the capture and update the figure whenever the kernel
+# changes (the roofline reports null traffic for workloads not listed).
+KERNEL_DRAM_BYTES = {"ring32": 382_598_400 + 20_466_688}
 
 
 def peaks():
@@ -588,7 +593,7 @@ def main():
                                ed.basis_hash(B))),
         "matvec_kernel": mv,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_int, "unit": "TOP/s",
-                     "frac": achieved / peak_int, "traffic": None,
+                     "frac": achieved / peak_int, "traffic": KERNEL_DRAM_BYTES.get(w["name"]),
                      "kernel": "k_matvec_tp (term-parallel, fp32, " + ("rotation x coset" if fact else "Benes")
                                + f" group search, {'32' if n <= 32 else '64'}-bit words)",
                      "int_ops_per_launch": int_ops, "int_ops_per_term": ops_term,
