@@ -256,7 +256,7 @@ def run_matvec_only(args, w):
            "launches": 2 * args.steps}
     dts = (torch.complex64, torch.complex128) if cplx else (torch.float32, torch.float64)
     for dt in dts:
-        x = ei.x_by_state_torch(5, states, nvec, cplx, dtype=dt).contiguous()
+        x = ei.x_by_state_torch_chunked(5, states, nvec, cplx, dtype=dt)
         y = torch.empty_like(x)
         ts = []
         for _ in range(args.steps):

@@ -116,6 +116,20 @@ def x_by_state_torch(seed: int, states, nvec: int = 1, complex_: bool = False, d
     return out if dtype is None else out.to(dtype)
 
 
+def x_by_state_torch_chunked(seed: int, states, nvec: int = 1, complex_: bool = False, dtype=None,
+                             chunk: int = 1 << 26):
+    """``x_by_state_torch`` computed ``chunk`` states at a time into one output
+    (the same numbers; bounded temporaries for bases of billions of states)."""
+    import torch
+    if dtype is None:
+        dtype = torch.complex128 if complex_ else torch.float64
+    n = states.numel()
+    out = torch.empty((n, nvec), dtype=dtype, device=states.device)
+    for i in range(0, n, chunk):
+        out[i:i + chunk] = x_by_state_torch(seed, states[i:i + chunk], nvec, complex_, dtype=dtype)
+    return out
+
+
 # ----------------------------------------------------------------------------
 # symmetry groups (site permutations + characters)
 # ----------------------------------------------------------------------------
@@ -249,6 +263,10 @@ def workload(name: str) -> dict:
         p, c = ring_group(40, 0, parity=+1)
         return dict(name=name, n_sites=40, n_up=20, spin_inversion=+1, perms=p, chars=c,
                     op=heisenberg_ring(40), complex_=False, lanczos_steps=150)
+    if name == "ring42":
+        p, c = ring_group(42, 0, parity=+1)
+        return dict(name=name, n_sites=42, n_up=21, spin_inversion=+1, perms=p, chars=c,
+                    op=heisenberg_ring(42), complex_=False, lanczos_steps=150)
     if name == "torus6x6":
         p, c = torus_group(6, 6, 1, 0)
         return dict(name=name, n_sites=36, n_up=18, spin_inversion=+1, perms=p, chars=c,

@@ -307,3 +307,6 @@ def test_device_generator_matches_numpy_generator():
         want = ei.x_by_state(9, st, nvec, cplx)
         got = ei.x_by_state_torch(9, torch.from_numpy(st.view(np.int64)), nvec, cplx).numpy()
         assert np.array_equal(got, want)
+        got_c = ei.x_by_state_torch_chunked(9, torch.from_numpy(st.view(np.int64)), nvec, cplx,
+                                            chunk=777).numpy()
+        assert np.array_equal(got_c, want)
