@@ -346,6 +346,57 @@ def run_solve(args, w):
     print(json.dumps(out), flush=True)
 
 
+def run_push(args, w):
+    """Ablation: the pull product (default kernel choice) against the push form
+    (atomic scatter into y), one vector, L2 flushed before each launch; the
+    push form's run-to-run variation of y (order of the atomic adds)."""
+    import torch
+    from paper_2308_16712_gb300 import ed
+    n = w["n_sites"]
+    O = ed.operator_create(n, w["op"]["sites"], w["op"]["coeff"], w["op"]["local"])
+    B = ed.basis_build(n, w["n_up"], w["spin_inversion"], w["perms"], w["chars"])
+    dim = ed.basis_size(B)
+    cplx = not ed.basis_is_real(B)
+    states, _ = ed.basis_states(B)
+    flush = torch.empty(L2_BYTES // 2, dtype=torch.float32, device="cuda")
+
+    def timed(fn, reps=5):
+        fn()
+        best = 1e30
+        for _ in range(reps):
+            flush.fill_(1.0)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            fn()
+            b.record()
+            torch.cuda.synchronize()
+            best = min(best, a.elapsed_time(b))
+        return best
+
+    out = {"mode": "push", "workload": w["name"], "dim": dim}
+    for dt in ((torch.complex64, torch.complex128) if cplx else (torch.float32, torch.float64)):
+        x = ei.x_by_state_torch_chunked(5, states, 1, cplx, dtype=dt).reshape(-1)
+        y_pull = torch.empty_like(x)
+        y_push = torch.empty_like(x)
+        ms_pull = timed(lambda: ed.matvec(O, B, x, y_pull, 1))
+        ms_push = timed(lambda: ed.matvec_push(O, B, x, y_push))
+        runs = []
+        for _ in range(5):
+            ed.matvec_push(O, B, x, y_push)
+            runs.append(y_push.clone())
+        scale = float(y_pull.abs().max())
+        distinct = len({r.cpu().numpy().tobytes() for r in runs})
+        out[str(dt).replace("torch.", "")] = {
+            "pull_ms": ms_pull, "push_ms": ms_push,
+            "pull_rows_per_s": dim / (ms_pull * 1e-3), "push_rows_per_s": dim / (ms_push * 1e-3),
+            "push_distinct_results_of_5": distinct,
+            "push_max_run_to_run_rel": max(float((r - runs[0]).abs().max()) for r in runs) / scale,
+            "push_vs_pull_max_rel": float((runs[0] - y_pull).abs().max()) / scale}
+        del x, y_pull, y_push, runs
+        torch.cuda.empty_cache()
+    print(json.dumps(out), flush=True)
+
+
 def run_multi(args):
     """The XXZ ring N=28 (Jxy=1, Delta=1.5) in all 140 sectors: one
     ed_matvec_multi launch over every sector against one ed_matvec per sector,
@@ -431,7 +482,7 @@ def main():
     ap.add_argument("--lanczos-steps", type=int, default=100,
                     help="Lanczos steps of the batched solve in --mode multi (0: skip)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--mode", default="job", choices=["job", "matvec", "step", "solve", "multi"],
+    ap.add_argument("--mode", default="job", choices=["job", "matvec", "step", "solve", "multi", "push"],
                     help="job: the benchmark; matvec: only the basis build and --steps matvec "
                          "launches per dtype; step: one untimed and one more whole step "
                          "(short programs for profiler captures)")
@@ -446,6 +497,8 @@ def main():
         return run_one_step(args, w)
     if args.mode == "solve":
         return run_solve(args, w)
+    if args.mode == "push":
+        return run_push(args, ei.workload(args.workload))
     if args.mode == "multi":
         return run_multi(args)
 
@@ -503,6 +556,9 @@ def main():
     ms32, r32, mv32_ms, mv32_n, launches = timed_steps(ed.ED_LANCZOS_F32_MATVEC, args.steps, args.warmup)
     clocks = sampler.stop() if sampler else None
     ms64, r64, mv64_ms, mv64_n, _ = timed_steps(ed.ED_LANCZOS_F64, max(1, args.steps), 1)
+    # the same job with push-form products (opt-in, not bit-reproducible)
+    msp, rp, _, _, _ = timed_steps(ed.ED_LANCZOS_F32_MATVEC | ed.ED_LANCZOS_PUSH, max(1, args.steps), 1)
+    msp = max_over_ranks(msp, world)
     ms32 = max_over_ranks(ms32, world)
     ms64 = max_over_ranks(ms64, world)
     per32 = ms32 / args.steps
@@ -583,6 +639,9 @@ def main():
         "fp64_plain": {"value": rows64, "ms_per_step": per64, "e0": r64.e0, "residual": r64.residual,
                        "matvecs_per_step": r64.matvecs},
         "dE0": abs(r32.e0 - r64.e0),
+        "push_mode": {"value": dim * rp.matvecs / (msp / max(1, args.steps) * 1e-3),
+                      "ms_per_step": msp / max(1, args.steps), "e0": rp.e0, "dE0": abs(rp.e0 - r64.e0),
+                      "note": "ED_LANCZOS_PUSH: atomic scatter products, E0 varies in the last bits"},
         "speedup_fp32_vs_fp64": rows32 / rows64,
         "nonzeros_per_s": value * nnz_row,
         "nnz_per_row": nnz_row,

@@ -247,8 +247,17 @@ ed_status ed_matvec_multi(const ed_operator *op, const ed_sector *sectors, int n
 typedef enum {
     ED_LANCZOS_F64 = 0,        /* fp64 matvec, fp64 recurrence                     */
     ED_LANCZOS_F32_MATVEC = 1, /* fp32 matvec, fp64 recurrence and fp64 refinement */
-    ED_LANCZOS_RECOMPUTE = 16  /* flag: form the Ritz vector by a second pass even
+    ED_LANCZOS_RECOMPUTE = 16, /* flag: form the Ritz vector by a second pass even
                                   when the Krylov vectors would fit in memory      */
+    ED_LANCZOS_PUSH = 32       /* flag (ed_lanczos only): products by the transposed
+                                  ("push") form -- every term added to y at its
+                                  representative's index with an atomic add, the
+                                  paper's distributed product.  Faster on GB300 (no
+                                  x gather, no per-row sums) but y, and so E0, vary
+                                  in the last bits from run to run.  Needs the
+                                  Krylov vectors kept in memory and an operator
+                                  whose off-diagonal entries only exchange
+                                  antiparallel spins; ED_ERR_UNSUPPORTED otherwise */
 } ed_lanczos_mode;
 
 typedef struct {
@@ -269,7 +278,7 @@ typedef struct {
  *             (re, im) double pairs for complex ones; need not be normalised
  *   steps     1..10000 Lanczos steps (no restart)
  *   mode      ED_LANCZOS_F64 or ED_LANCZOS_F32_MATVEC, optionally OR-ed with
- *             ED_LANCZOS_RECOMPUTE
+ *             ED_LANCZOS_RECOMPUTE or ED_LANCZOS_PUSH
  *   e0_out    host, receives the energy (may be NULL)
  *   d_vec_out device, dim values as d_x0, receives the normalised ground-state
  *             approximation (may be NULL)
@@ -282,7 +291,8 @@ typedef struct {
  * fp64 Lanczos steps started from it, whose lowest Ritz value is returned
  * together with its residual.  Allocates its work vectors; synchronises
  * `stream` before returning.
- * Errors: ED_ERR_INVALID_ARG, ED_ERR_SYMMETRY_MISMATCH, ED_ERR_OOM, ED_ERR_CUDA.
+ * Errors: ED_ERR_INVALID_ARG, ED_ERR_SYMMETRY_MISMATCH, ED_ERR_UNSUPPORTED
+ * (ED_LANCZOS_PUSH not applicable), ED_ERR_OOM, ED_ERR_CUDA.
  */
 ed_status ed_lanczos(const ed_operator *op, const ed_basis *basis, const void *d_x0, int steps,
                      int mode, double *e0_out, void *d_vec_out, ed_lanczos_info *info,

@@ -978,8 +978,8 @@ void ed_operator_destroy(ed_operator *op)
     delete op;
 }
 
-ed_status ed_matvec(const ed_operator *op, const ed_basis *b, const void *x, void *y, int nvec,
-                    ed_dtype dtype, void *stream)
+static ed_status check_matvec_args(const ed_operator *op, const ed_basis *b, const void *x, const void *y,
+                                   int nvec, ed_dtype dtype)
 {
     if (!op || !b)
         return ED_ERR_INVALID_ARG;
@@ -996,13 +996,37 @@ ed_status ed_matvec(const ed_operator *op, const ed_basis *b, const void *x, voi
         return ED_ERR_INVALID_ARG;
     if (x == y && b->dim)
         return ED_ERR_INVALID_ARG;
-    ed_status st = edk::check_pair(op, b);
+    return edk::check_pair(op, b);
+}
+
+ed_status ed_matvec(const ed_operator *op, const ed_basis *b, const void *x, void *y, int nvec,
+                    ed_dtype dtype, void *stream)
+{
+    const ed_status st = check_matvec_args(op, b, x, y, nvec, dtype);
     if (st != ED_OK)
         return st;
     if (!b->dim)
         return ED_OK;
     ED_CUDA_TRY(edk::launch_matvec(op_view(op), b->group_view(), b->index_view(), !b->trivial_chars,
                                    x, y, nvec, dtype, (cudaStream_t)stream));
+    return ED_OK;
+}
+
+// Ablation hook (not part of the public header): y = H x by the transposed
+// (push) form, one vector, atomic adds into y.  Same arguments as ed_matvec
+// with nvec = 1; needs the hash index and an exchange-only operator
+// (ED_ERR_UNSUPPORTED otherwise).  Not deterministic in the last bits.
+ed_status edx_matvec_push(const ed_operator *op, const ed_basis *b, const void *x, void *y, ed_dtype dtype,
+                          void *stream)
+{
+    const ed_status st = check_matvec_args(op, b, x, y, 1, dtype);
+    if (st != ED_OK || !b->dim)
+        return st;
+    const edk::OpView ov = op_view(op);
+    if (!b->d_htab || !ov.exchange_only)
+        return ED_ERR_UNSUPPORTED;
+    ED_CUDA_TRY(edk::launch_matvec_push(ov, b->group_view(), b->index_view(), !b->trivial_chars, x, y, dtype,
+                                        (cudaStream_t)stream));
     return ED_OK;
 }
 

@@ -89,6 +89,10 @@ cudaError_t launch_count_nnz(const OpView &op, const GroupView &g, const IndexVi
 
 cudaError_t launch_matvec(const OpView &op, const GroupView &g, const IndexView &ix, bool track,
                           const void *x, void *y, int nvec, ed_dtype dtype, cudaStream_t stream);
+// The transposed (push) form, one vector, for the ablation hook: y zeroed,
+// then every contribution added atomically (order-dependent rounding).
+cudaError_t launch_matvec_push(const OpView &op, const GroupView &g, const IndexView &ix, bool track,
+                               const void *x, void *y, ed_dtype dtype, cudaStream_t stream);
 
 // Kernel choice for one vector and an exchange-only operator: 0 = the
 // term-parallel kernel in single precision, the row-per-lane kernel in double

@@ -471,7 +471,7 @@ struct Scratch {
 
 template <bool kC>
 ed_status run_lanczos(const ed_operator *op, const ed_basis *b, const void *x0, int steps,
-                      ed_lanczos_mode mode, bool recompute, double *e0_out, void *vec_out,
+                      ed_lanczos_mode mode, bool recompute, bool push, double *e0_out, void *vec_out,
                       ed_lanczos_info *info, cudaStream_t st)
 {
     using D = typename Vec<kC>::D;
@@ -494,6 +494,10 @@ ed_status run_lanczos(const ed_operator *op, const ed_basis *b, const void *x0, 
     cudaMemGetInfo(&free_b, &total_b);
     const size_t vec_bytes = n * sizeof(D);
     const bool store = !recompute && (double)(steps + 1) * vec_bytes < 0.5 * (double)free_b;
+    // push products are not bit-reproducible, so a recomputed pass would not
+    // retrace the first one
+    if (push && (!store || !ov.exchange_only || !iv.htab))
+        return ED_ERR_UNSUPPORTED;
 
     Scratch S;
     D *V = nullptr, *w = nullptr, *ring[2] = {nullptr, nullptr}, *psi = nullptr;
@@ -532,7 +536,8 @@ ed_status run_lanczos(const ed_operator *op, const ed_basis *b, const void *x0, 
         ++matvecs;
         cudaError_t e = timer.mark(st);
         if (e == cudaSuccess)
-            e = launch_matvec(ov, gv, iv, track, in, out, 1, dt, st);
+            e = push ? launch_matvec_push(ov, gv, iv, track, in, out, dt, st)
+                     : launch_matvec(ov, gv, iv, track, in, out, 1, dt, st);
         if (e == cudaSuccess)
             e = timer.mark(st);
         return e;
@@ -639,11 +644,12 @@ extern "C" ed_status ed_lanczos(const ed_operator *op, const ed_basis *b, const 
 {
     if (!op || !b || steps < 1 || steps > 10000)
         return ED_ERR_INVALID_ARG;
-    const int base = mode_flags & ~ED_LANCZOS_RECOMPUTE;
+    const int base = mode_flags & ~(ED_LANCZOS_RECOMPUTE | ED_LANCZOS_PUSH);
     if (base != ED_LANCZOS_F64 && base != ED_LANCZOS_F32_MATVEC)
         return ED_ERR_INVALID_ARG;
     const ed_lanczos_mode mode = (ed_lanczos_mode)base;
     const bool recompute = (mode_flags & ED_LANCZOS_RECOMPUTE) != 0;
+    const bool push = (mode_flags & ED_LANCZOS_PUSH) != 0;
     if (b->dim == 0 || !x0)
         return ED_ERR_INVALID_ARG;
     if (((uintptr_t)x0 | (uintptr_t)vec_out) & 15)
@@ -653,8 +659,8 @@ extern "C" ed_status ed_lanczos(const ed_operator *op, const ed_basis *b, const 
         return st;
     const bool cplx = !(b->real_chars && op->real);
     if (cplx)
-        return edk::run_lanczos<true>(op, b, x0, steps, mode, recompute, e0_out, vec_out, info,
+        return edk::run_lanczos<true>(op, b, x0, steps, mode, recompute, push, e0_out, vec_out, info,
                                       (cudaStream_t)stream);
-    return edk::run_lanczos<false>(op, b, x0, steps, mode, recompute, e0_out, vec_out, info,
+    return edk::run_lanczos<false>(op, b, x0, steps, mode, recompute, push, e0_out, vec_out, info,
                                    (cudaStream_t)stream);
 }

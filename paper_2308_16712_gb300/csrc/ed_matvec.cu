@@ -12,32 +12,50 @@ bool use_term_parallel(int nvec, const OpView &op, ed_dtype dtype)
     return g_kernel_policy == 2 || dtype == ED_F32 || dtype == ED_C64;
 }
 
+static TpArgs<1> single_tp_args(const OpView &op, const GroupView &g, const IndexView &ix, const void *x,
+                                void *y)
+{
+    TpArgs<1> t;
+    t.op = op;
+    t.g = g;
+    t.n_sectors = 1;
+    t.max_order = g.order;
+    t.total_tiles = (ix.dim + 31) / 32;
+    SectorDesc &d = t.sec[0];
+    d.keys = ix.keys;
+    d.states = ix.states;
+    d.norms = ix.norms;
+    d.htab = ix.htab;
+    d.hent = ix.hent;
+    d.chi = g.fact ? g.fchi : g.chi;
+    d.chif = g.fact ? g.fchif : g.chif;
+    d.x = x;
+    d.y = y;
+    d.dim = ix.dim;
+    d.tile_begin = 0;
+    d.hbits = ix.hbits;
+    d.hwide = ix.hwide;
+    d.norm_bits = ix.norm_bits;
+    d.flip = g.flip;
+    return t;
+}
+
+// The push form (ablation): y = 0, then every term scattered atomically.
+cudaError_t launch_matvec_push(const OpView &op, const GroupView &g, const IndexView &ix, bool track,
+                               const void *x, void *y, ed_dtype dtype, cudaStream_t stream)
+{
+    const size_t vb = (dtype == ED_F64 || dtype == ED_C64) ? 8 : dtype == ED_F32 ? 4 : 16;
+    cudaError_t e = cudaMemsetAsync(y, 0, ix.dim * vb, stream);
+    if (e != cudaSuccess)
+        return e;
+    return tp_push(single_tp_args(op, g, ix, x, y), track, ix.hwide != 0, dtype, stream);
+}
+
 cudaError_t launch_matvec(const OpView &op, const GroupView &g, const IndexView &ix, bool track,
                           const void *x, void *y, int nvec, ed_dtype dtype, cudaStream_t stream)
 {
     if (ix.htab && use_term_parallel(nvec, op, dtype)) {
-        TpArgs<1> t;
-        t.op = op;
-        t.g = g;
-        t.n_sectors = 1;
-        t.max_order = g.order;
-        t.total_tiles = (ix.dim + 31) / 32;
-        SectorDesc &d = t.sec[0];
-        d.keys = ix.keys;
-        d.states = ix.states;
-        d.norms = ix.norms;
-        d.htab = ix.htab;
-        d.hent = ix.hent;
-        d.chi = g.fact ? g.fchi : g.chi;
-        d.chif = g.fact ? g.fchif : g.chif;
-        d.x = x;
-        d.y = y;
-        d.dim = ix.dim;
-        d.tile_begin = 0;
-        d.hbits = ix.hbits;
-        d.hwide = ix.hwide;
-        d.norm_bits = ix.norm_bits;
-        d.flip = g.flip;
+        const TpArgs<1> t = single_tp_args(op, g, ix, x, y);
         switch (dtype) {
         case ED_F64: return tp_single_f64(t, track, ix.hwide != 0, stream);
         case ED_F32: return tp_single_f32(t, track, ix.hwide != 0, stream);

@@ -107,6 +107,14 @@ template <typename T> __device__ __forceinline__ Cplx<T> vshfl_up(Cplx<T> v, int
     return {__shfl_up_sync(0xffffffffu, v.re, o), __shfl_up_sync(0xffffffffu, v.im, o)};
 }
 
+__device__ __forceinline__ void atomic_add(float *p, float v) { atomicAdd(p, v); }
+__device__ __forceinline__ void atomic_add(double *p, double v) { atomicAdd(p, v); }
+template <typename T> __device__ __forceinline__ void atomic_add(Cplx<T> *p, Cplx<T> v)
+{
+    atomicAdd(&p->re, v.re);
+    atomicAdd(&p->im, v.im);
+}
+
 // hash index entries: 8 bytes {state, index << norm_bits | norm} or 16 bytes
 // {state, index | norm << 32}
 template <typename W> __device__ __forceinline__ W ent_state(uint2 v) { return (W)v.x; }
@@ -116,7 +124,7 @@ __device__ __forceinline__ uint32_t ent_norm(uint2 v, int nb) { return v.y & ((1
 __device__ __forceinline__ uint32_t ent_index(ulonglong2 v, int) { return (uint32_t)v.y; }
 __device__ __forceinline__ uint32_t ent_norm(ulonglong2 v, int) { return (uint32_t)(v.y >> 32); }
 
-template <typename W, typename T, bool kC, bool kTrack, bool kFact, bool kWide, int kSec>
+template <typename W, typename T, bool kC, bool kTrack, bool kFact, bool kWide, int kSec, bool kPush = false>
 __global__ void __launch_bounds__(kTpThreads) k_matvec_tp(const __grid_constant__ TpArgs<kSec> a)
 {
     using V = typename ValT<T, kC>::type;
@@ -223,10 +231,21 @@ __global__ void __launch_bounds__(kTpThreads) k_matvec_tp(const __grid_constant_
                 }
             }
             const V xv = x[row];
-            if constexpr (kC)
+            if constexpr (kPush) {
+                // push form: the row's x is scattered, not gathered; the
+                // diagonal goes to y like every other contribution
+                acc = xv;
+                V dv;
+                if constexpr (kC)
+                    dv = cmul(conjc(d), xv);
+                else
+                    dv = d.re * xv;
+                atomic_add(reinterpret_cast<V *>(sd.y) + row, dv);
+            } else if constexpr (kC) {
                 acc = cmul(conjc(d), xv);
-            else
+            } else {
                 acc = d.re * xv;
+            }
         }
         // flat layout of the tile's terms: exclusive scan of the counts
         uint32_t incl = nt;
@@ -327,38 +346,52 @@ __global__ void __launch_bounds__(kTpThreads) k_matvec_tp(const __grid_constant_
                                 ch = load_cf<T>(sd.chif + gbest);
                             coef = cmul(coef, ch);
                         }
-                        const V xv = x[ent_index(v, norm_bits)];
-                        if constexpr (kC)
-                            val = cmul(coef, xv);
-                        else
-                            val = coef.re * xv;
+                        if constexpr (kPush) {
+                            // H Hermitian: H[r'][r] = conj(H[r][r']); this term adds
+                            // conj(coef) x_r to y_r'
+                            const V xr = ws.acc[rho];
+                            V pv;
+                            if constexpr (kC)
+                                pv = cmul(conjc(coef), xr);
+                            else
+                                pv = coef.re * xr;
+                            atomic_add(reinterpret_cast<V *>(sd.y) + ent_index(v, norm_bits), pv);
+                        } else {
+                            const V xv = x[ent_index(v, norm_bits)];
+                            if constexpr (kC)
+                                val = cmul(coef, xv);
+                            else
+                                val = coef.re * xv;
+                        }
                         break;
                     }
                 }
             }
-            // segmented inclusive scan: lanes spos..lane belong to the same row
+            if constexpr (!kPush) {
+                // segmented inclusive scan: lanes spos..lane belong to the same row
 #pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const V up = vshfl_up(val, o);
-                if (lane >= o && lane - o >= spos)
-                    val = vadd(val, up);
+                for (int o = 1; o < 32; o <<= 1) {
+                    const V up = vshfl_up(val, o);
+                    if (lane >= o && lane - o >= spos)
+                        val = vadd(val, up);
+                }
+                const bool seg_end = act && (lane == 31 || t + 1 == total || ((M >> (lane + 1)) & 1u));
+                if (seg_end)
+                    ws.acc[rho] = vadd(ws.acc[rho], val);
             }
-            const bool seg_end = act && (lane == 31 || t + 1 == total || ((M >> (lane + 1)) & 1u));
-            if (seg_end)
-                ws.acc[rho] = vadd(ws.acc[rho], val);
             __syncwarp();
         }
-        if (valid)
+        if (!kPush && valid)
             store_cs(reinterpret_cast<V *>(sd.y) + row, ws.acc[lane]);
         __syncwarp();
     }
 }
 
-template <typename W, typename T, bool kC, bool kTrack, bool kFact, bool kWide, int kSec>
+template <typename W, typename T, bool kC, bool kTrack, bool kFact, bool kWide, int kSec, bool kPush = false>
 cudaError_t tp_launch(const TpArgs<kSec> &a, cudaStream_t stream)
 {
     using V = typename ValT<T, kC>::type;
-    auto kern = k_matvec_tp<W, T, kC, kTrack, kFact, kWide, kSec>;
+    auto kern = k_matvec_tp<W, T, kC, kTrack, kFact, kWide, kSec, kPush>;
     const size_t smem = tp_smem_bytes<W, T, V, kFact>(a.g, a.op, a.n_sectors, a.max_order);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess)
@@ -375,16 +408,17 @@ cudaError_t tp_launch(const TpArgs<kSec> &a, cudaStream_t stream)
     return cudaGetLastError();
 }
 
-// wide: 16-byte hash entries (every sector of the batch must agree)
-template <typename T, bool kC, int kSec>
+// wide: 16-byte hash entries (every sector of the batch must agree); kPush:
+// the transposed (push) form with atomic scatter into y, which must be zero
+template <typename T, bool kC, int kSec, bool kPush = false>
 cudaError_t tp_dispatch(const TpArgs<kSec> &a, bool track, bool wide, cudaStream_t stream)
 {
     const bool w32 = a.g.n_sites <= 32;
     const bool fact = a.g.fact != 0;
-#define ED_TP_FA(W, TR, WD)                                                     \
-    do {                                                                        \
-        if (fact) return tp_launch<W, T, kC, TR, true, WD, kSec>(a, stream);    \
-        return tp_launch<W, T, kC, TR, false, WD, kSec>(a, stream);             \
+#define ED_TP_FA(W, TR, WD)                                                             \
+    do {                                                                                \
+        if (fact) return tp_launch<W, T, kC, TR, true, WD, kSec, kPush>(a, stream);     \
+        return tp_launch<W, T, kC, TR, false, WD, kSec, kPush>(a, stream);              \
     } while (0)
     if (w32) {
         if (wide) {
@@ -412,5 +446,7 @@ cudaError_t tp_multi_f64(const TpArgs<kMaxSectors> &a, bool track, bool wide, cu
 cudaError_t tp_multi_f32(const TpArgs<kMaxSectors> &a, bool track, bool wide, cudaStream_t s);
 cudaError_t tp_multi_c128(const TpArgs<kMaxSectors> &a, bool track, bool wide, cudaStream_t s);
 cudaError_t tp_multi_c64(const TpArgs<kMaxSectors> &a, bool track, bool wide, cudaStream_t s);
+// push form (ablation), one sector, y zeroed by the caller
+cudaError_t tp_push(const TpArgs<1> &a, bool track, bool wide, ed_dtype dtype, cudaStream_t s);
 
 }  // namespace edk

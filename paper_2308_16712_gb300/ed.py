@@ -19,7 +19,7 @@ LIB_PATH = os.path.join(_HERE, "libed.so")
 
 ED_OK = 0
 ED_F64, ED_F32, ED_C128, ED_C64 = 0, 1, 2, 3
-ED_LANCZOS_F64, ED_LANCZOS_F32_MATVEC, ED_LANCZOS_RECOMPUTE = 0, 1, 16
+ED_LANCZOS_F64, ED_LANCZOS_F32_MATVEC, ED_LANCZOS_RECOMPUTE, ED_LANCZOS_PUSH = 0, 1, 16, 32
 
 STATUS_NAMES = {
     0: "ED_OK", 1: "ED_ERR_INVALID_ARG", 2: "ED_ERR_NOT_A_GROUP", 3: "ED_ERR_BAD_CHARACTER",
@@ -70,6 +70,7 @@ _SIGS = {
     "edx_count_nnz": (_i32, [_P, _P, ctypes.POINTER(ctypes.c_ulonglong)]),
     "edx_force_prefix_search": (None, [_i32]),
     "edx_kernel_policy": (None, [_i32]),
+    "edx_matvec_push": (_i32, [_P, _P, _P, _P, _i32, _P]),
     "edx_basis_hash": (_i32, [_P, ctypes.POINTER(_i32), ctypes.POINTER(ctypes.c_uint32), ctypes.POINTER(_i32)]),
     "edx_basis_table": (_i32, [_P, ctypes.POINTER(_u64), ctypes.POINTER(ctypes.c_uint32), ctypes.POINTER(_i32)]),
     "edx_basis_factored": (_i32, [_P, ctypes.POINTER(_i32), ctypes.POINTER(_i32), ctypes.POINTER(_i32)]),
@@ -271,6 +272,18 @@ def count_nnz(op: Operator, basis: Basis) -> int:
     if _lib.edx_count_nnz(op.handle, basis.handle, ctypes.byref(v)) != 0:
         raise RuntimeError("edx_count_nnz failed")
     return int(v.value)
+
+
+def matvec_push(op: Operator, basis: Basis, x, y, stream=None):
+    """Ablation: y = H x (one vector) by the transposed (push) form with atomic
+    adds into y -- the paper's distributed product on one GPU.  The rounding
+    of y depends on the order of the atomics, so repeated calls may differ in
+    the last bits."""
+    code = _DTYPE_CODE[str(x.dtype).replace("torch.", "")]
+    if y.dtype != x.dtype or not (x.is_contiguous() and y.is_contiguous()):
+        raise ValueError("x and y must be contiguous with one dtype")
+    _check(_lib.edx_matvec_push(op.handle, basis.handle, _ptr(x), _ptr(y), code, _stream(stream)),
+           "edx_matvec_push")
 
 
 KERNEL_POLICIES = {"auto": 0, "rowwise": 1, "term_parallel": 2}

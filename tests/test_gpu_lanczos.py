@@ -81,3 +81,20 @@ def test_ring32_fp32_matvec_lanczos_reaches_fp64():
     assert abs(r64.e0 - e_bethe) < 1e-9
     assert abs(r32.e0 - e_bethe) < 1e-9
     assert abs(r64.e0 - r32.e0) < 1e-10
+
+
+def test_push_mode_lanczos():
+    """ED_LANCZOS_PUSH (transposed products with atomic adds): the same energy
+    as the dense spectrum within the bar; refused where a recomputed pass
+    would be needed."""
+    torch, ed = gpu()
+    w = ei.workload("ring16")
+    S = build_pair(16, 8, +1, w["perms"], w["chars"], w["op"])
+    e_dense = np.linalg.eigvalsh(oracle.dense_matrix(S["G"], S["H"], S["st"], S["nm"]).real)[0]
+    x0 = to_torch(ei.x_by_index(0, S["dim"])[:, 0], np.float64)
+    for mode in (ed.ED_LANCZOS_F64, ed.ED_LANCZOS_F32_MATVEC):
+        r = ed.lanczos(S["O"], S["B"], x0, 50, mode | ed.ED_LANCZOS_PUSH)
+        assert abs(r.e0 - e_dense) < 1e-10
+        assert r.residual < 1e-6
+    with pytest.raises(ed.EDError):
+        ed.lanczos(S["O"], S["B"], x0, 50, ed.ED_LANCZOS_F64 | ed.ED_LANCZOS_PUSH | ed.ED_LANCZOS_RECOMPUTE)
