@@ -125,7 +125,7 @@ __device__ __forceinline__ uint32_t ent_index(ulonglong2 v, int) { return (uint3
 __device__ __forceinline__ uint32_t ent_norm(ulonglong2 v, int) { return (uint32_t)(v.y >> 32); }
 
 template <typename W, typename T, bool kC, bool kTrack, bool kFact, bool kWide, int kSec, bool kPush = false>
-__global__ void __launch_bounds__(kTpThreads) k_matvec_tp(const __grid_constant__ TpArgs<kSec> a)
+__global__ void __launch_bounds__(kTpThreads, 8) k_matvec_tp(const __grid_constant__ TpArgs<kSec> a)
 {
     using V = typename ValT<T, kC>::type;
     using E = std::conditional_t<kWide, ulonglong2, uint2>;
