@@ -249,7 +249,7 @@ typedef enum {
     ED_LANCZOS_F32_MATVEC = 1, /* fp32 matvec, fp64 recurrence and fp64 refinement */
     ED_LANCZOS_RECOMPUTE = 16, /* flag: form the Ritz vector by a second pass even
                                   when the Krylov vectors would fit in memory      */
-    ED_LANCZOS_PUSH = 32       /* flag (ed_lanczos only): products by the transposed
+    ED_LANCZOS_PUSH = 32,      /* flag (ed_lanczos only): products by the transposed
                                   ("push") form -- every term added to y at its
                                   representative's index with an atomic add, the
                                   paper's distributed product.  Faster on GB300 (no
@@ -258,6 +258,13 @@ typedef enum {
                                   Krylov vectors kept in memory and an operator
                                   whose off-diagonal entries only exchange
                                   antiparallel spins; ED_ERR_UNSUPPORTED otherwise */
+    ED_LANCZOS_REORTH = 64     /* flag (ed_lanczos, ed_lanczos_eigs): reorthogonalise
+                                  every new Lanczos vector against all earlier ones
+                                  (classical Gram-Schmidt, twice, fp64), which keeps
+                                  the Ritz values free of spurious copies so that the
+                                  low excited states come out too; costs about
+                                  4 j vector reads at step j.  Needs the Krylov
+                                  vectors kept in memory; ED_ERR_UNSUPPORTED otherwise */
 } ed_lanczos_mode;
 
 typedef struct {
@@ -297,6 +304,27 @@ typedef struct {
 ed_status ed_lanczos(const ed_operator *op, const ed_basis *basis, const void *d_x0, int steps,
                      int mode, double *e0_out, void *d_vec_out, ed_lanczos_info *info,
                      void *stream);
+
+/*
+ * ed_lanczos_eigs -- ed_lanczos that also returns the lowest n_eig Ritz values
+ * of the main run's tridiagonal matrix (Sturm-count multisection for each),
+ * the estimates of the lowest n_eig eigenvalues of H in the sector.
+ *
+ *   n_eig     0..steps
+ *   eigs_out  host, n_eig values, ascending; NaN past the dimension of the
+ *             Krylov space actually built (a sector smaller than `steps`)
+ *   other arguments as ed_lanczos (the refined lowest energy is in info->e0)
+ *
+ * Without ED_LANCZOS_REORTH the plain recurrence loses orthogonality once the
+ * lowest Ritz value has converged and may then repeat converged values
+ * ("ghosts") among the higher ones; with it, the values are those of an
+ * orthonormal Krylov basis.  In the fp32-matvec mode the values carry the fp32
+ * products' error (about 1e-7 relative); only the lowest is refined.
+ * Errors as ed_lanczos, and ED_ERR_INVALID_ARG for n_eig out of range.
+ */
+ed_status ed_lanczos_eigs(const ed_operator *op, const ed_basis *basis, const void *d_x0, int steps,
+                          int mode, int n_eig, double *eigs_out, void *d_vec_out, ed_lanczos_info *info,
+                          void *stream);
 
 /*
  * ed_lanczos_multi -- lowest eigenvalue of H in each of up to 160 symmetry

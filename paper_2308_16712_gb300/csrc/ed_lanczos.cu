@@ -311,6 +311,88 @@ __global__ void k_finish_residual(const double2 *res_part, const double2 *den_pa
         *out = sqrt(fmax(r, 0.0) / d);
 }
 
+// ---- full reorthogonalisation against the kept Krylov vectors ----------------
+struct Part4 {  // compensated real and imaginary parts of one block's partial
+    double rs, rc, is, ic;
+};
+// Classical Gram-Schmidt applied twice: c_k = <V_k, w> for k < kcount, then
+// w -= sum_k c_k V_k.  Complex vectors use the Hermitian product.
+// part[k * gridDim.x + b] = block b's slice of c_k as (re.s, re.c, im.s, im.c).
+template <bool kC>
+__global__ void __launch_bounds__(kRedThreads) k_reorth_dot(const typename Vec<kC>::D *V,
+                                                             const typename Vec<kC>::D *w, uint64_t n,
+                                                             int kcount, Part4 *part)
+{
+    const uint64_t per = (n + gridDim.x - 1) / gridDim.x;
+    const uint64_t lo = min(n, blockIdx.x * per), hi = min(n, lo + per);
+    for (int k = 0; k < kcount; ++k) {
+        const typename Vec<kC>::D *vk = V + (uint64_t)k * n;
+        double sr = 0.0, si = 0.0;
+        for (uint64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+            if constexpr (kC) {
+                const double2 a = vk[i], b = w[i];
+                sr = fma(a.x, b.x, fma(a.y, b.y, sr));
+                si = fma(a.x, b.y, fma(-a.y, b.x, si));
+            } else {
+                sr = fma(vk[i], w[i], sr);
+            }
+        }
+        const KSum kr = block_ksum(KSum{sr, 0.0});
+        KSum ki{0.0, 0.0};
+        if constexpr (kC)
+            ki = block_ksum(KSum{si, 0.0});
+        if (threadIdx.x == 0)
+            part[(uint64_t)k * gridDim.x + blockIdx.x] = Part4{kr.s, kr.c, ki.s, ki.c};
+    }
+}
+
+// c[k] = sum of the block partials of coefficient k (one block per k)
+__global__ void __launch_bounds__(kRedThreads) k_reorth_coef(const Part4 *part, int nparts, double2 *c)
+{
+    const int k = blockIdx.x;
+    KSum r{0.0, 0.0}, im{0.0, 0.0};
+    for (int b = threadIdx.x; b < nparts; b += blockDim.x) {
+        const Part4 p = part[(uint64_t)k * nparts + b];
+        r = ksum_merge(r, KSum{p.rs, p.rc});
+        im = ksum_merge(im, KSum{p.is, p.ic});
+    }
+    r = block_ksum(r);
+    im = block_ksum(im);
+    if (threadIdx.x == 0)
+        c[k] = make_double2(r.s + r.c, im.s + im.c);
+}
+
+// w -= sum_k c_k V_k; norm partials of the result
+template <bool kC>
+__global__ void __launch_bounds__(kRedThreads) k_reorth_update(const typename Vec<kC>::D *V,
+                                                                typename Vec<kC>::D *w, uint64_t n,
+                                                                int kcount, const double2 *c,
+                                                                double2 *norm_part)
+{
+    using VT = Vec<kC>;
+    const uint64_t per = (n + gridDim.x - 1) / gridDim.x;
+    const uint64_t lo = min(n, blockIdx.x * per), hi = min(n, lo + per);
+    double s0 = 0.0;
+    for (uint64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+        typename VT::D acc = w[i];
+        for (int k = 0; k < kcount; ++k) {
+            const double2 ck = c[k];
+            const typename VT::D vk = V[(uint64_t)k * n + i];
+            if constexpr (kC) {
+                acc.x -= ck.x * vk.x - ck.y * vk.y;
+                acc.y -= ck.x * vk.y + ck.y * vk.x;
+            } else {
+                acc -= ck.x * vk;
+            }
+        }
+        w[i] = acc;
+        s0 += VT::norm2(acc);
+    }
+    const KSum k = block_ksum(KSum{s0, 0.0});
+    if (threadIdx.x == 0)
+        norm_part[blockIdx.x] = make_double2(k.s, k.c);
+}
+
 // ---- tridiagonal eigensolver (one thread) ------------------------------------
 // Number of eigenvalues of T (diag a, offdiag b) below x (Sturm sequence).
 __device__ int sturm_count(const double *a, const double *b, int m, double x)
@@ -408,6 +490,46 @@ __global__ void k_tridiag_lowest(const double *alpha, const double *beta, int m,
     *m_eff_out = me;
 }
 
+// Eigenvalue number blockIdx.x (0 = lowest) of the leading m_eff x m_eff block
+// (m_eff as found by k_tridiag_lowest), by the same 32-point multisection with
+// the criterion "at least blockIdx.x + 1 eigenvalues below x"; NaN beyond m_eff.
+// Launch with 32 threads per block, one block per eigenvalue.
+__global__ void k_tridiag_kth(const double *alpha, const double *beta, int m, const int *m_eff, double *out)
+{
+    const int lane = threadIdx.x & 31;
+    const int e = blockIdx.x;
+    const int me = *m_eff;
+    if (e >= me) {
+        if (lane == 0)
+            out[e] = __longlong_as_double(0x7ff8000000000000LL);
+        return;
+    }
+    double lo = 1e300, hi = -1e300;
+    if (lane == 0) {
+        for (int i = 0; i < me; ++i) {  // Gershgorin interval
+            const double r = (i ? fabs(beta[i]) : 0.0) + (i + 1 < me ? fabs(beta[i + 1]) : 0.0);
+            lo = fmin(lo, alpha[i] - r);
+            hi = fmax(hi, alpha[i] + r);
+        }
+    }
+    lo = __shfl_sync(0xffffffffu, lo, 0);
+    hi = __shfl_sync(0xffffffffu, hi, 0);
+    for (int it = 0; it < 24; ++it) {
+        const double width = hi - lo;
+        if (!(width > 2e-16 * fmax(fabs(lo), fabs(hi))))
+            break;
+        const double x = lo + width * (double)(lane + 1) / 33.0;
+        const unsigned below = __ballot_sync(0xffffffffu, sturm_count(alpha, beta, me, x) >= e + 1);
+        const int f = below ? __ffs(below) - 1 : 32;
+        const double nlo = f == 0 ? lo : lo + width * (double)f / 33.0;
+        const double nhi = f == 32 ? hi : lo + width * (double)(f + 1) / 33.0;
+        lo = nlo;
+        hi = nhi;
+    }
+    if (lane == 0)
+        out[e] = 0.5 * (lo + hi);
+}
+
 template <typename T>
 cudaError_t dalloc(T **p, size_t count)
 {
@@ -471,7 +593,8 @@ struct Scratch {
 
 template <bool kC>
 ed_status run_lanczos(const ed_operator *op, const ed_basis *b, const void *x0, int steps,
-                      ed_lanczos_mode mode, bool recompute, bool push, double *e0_out, void *vec_out,
+                      ed_lanczos_mode mode, bool recompute, bool push, bool reorth, int n_eig,
+                      double *eigs_out, double *e0_out, void *vec_out,
                       ed_lanczos_info *info, cudaStream_t st)
 {
     using D = typename Vec<kC>::D;
@@ -497,6 +620,9 @@ ed_status run_lanczos(const ed_operator *op, const ed_basis *b, const void *x0, 
     // push products are not bit-reproducible, so a recomputed pass would not
     // retrace the first one
     if (push && (!store || !ov.exchange_only || !iv.htab))
+        return ED_ERR_UNSUPPORTED;
+    // reorthogonalisation needs every earlier Lanczos vector
+    if (reorth && !store)
         return ED_ERR_UNSUPPORTED;
 
     Scratch S;
@@ -528,6 +654,15 @@ ed_status run_lanczos(const ed_operator *op, const ed_basis *b, const void *x0, 
     ED_L_TRY(S.get(&part_a, nparts));
     ED_L_TRY(S.get(&part_b, nparts));
     ED_L_TRY(S.get(&part_c, nparts));
+    Part4 *rpart = nullptr;
+    double2 *rcoef = nullptr;
+    double *d_eigs = nullptr;
+    if (reorth) {
+        ED_L_TRY(S.get(&rpart, (size_t)(mmax + 2) * nparts));
+        ED_L_TRY(S.get(&rcoef, mmax + 2));
+    }
+    if (n_eig > 0)
+        ED_L_TRY(S.get(&d_eigs, n_eig));
     ED_L_TRY(cudaMemsetAsync(beta, 0, (mmax + 2) * sizeof(double), st));
 
     int matvecs = 0;
@@ -573,6 +708,13 @@ ed_status run_lanczos(const ed_operator *op, const ed_basis *b, const void *x0, 
                 k_update<kC, false><<<nparts, kRedThreads, 0, st>>>(w, w, v, vp, n, alpha + j, beta + j,
                                                                      part_b); count_launch();
             }
+            if (reorth && Vs) {  // against v_0 .. v_j, twice
+                for (int pass = 0; pass < 2; ++pass) {
+                    k_reorth_dot<kC><<<nparts, kRedThreads, 0, st>>>(Vs, w, n, j + 1, rpart); count_launch();
+                    k_reorth_coef<<<j + 1, kRedThreads, 0, st>>>(rpart, nparts, rcoef); count_launch();
+                    k_reorth_update<kC><<<nparts, kRedThreads, 0, st>>>(Vs, w, n, j + 1, rcoef, part_b); count_launch();
+                }
+            }
             D *vn = Vs ? Vs + (uint64_t)(j + 1) * n : (vp ? vp : ring[1]);
             k_finalize<<<1, kRedThreads, 0, st>>>(part_b, nparts, beta + j + 1, 1); count_launch();
             k_normalize<kC><<<vgrid, kRedThreads, 0, st>>>(w, vn, use_f32 ? x32 : nullptr, n,
@@ -587,6 +729,9 @@ ed_status run_lanczos(const ed_operator *op, const ed_basis *b, const void *x0, 
     ED_L_TRY(run((const D *)x0, steps, f32, store ? V : nullptr, nullptr));
     ED_L_TRY(cudaMemsetAsync(y, 0, (mmax + 1) * sizeof(double), st));
     k_tridiag_lowest<<<1, 32, 0, st>>>(alpha, beta, steps, y, scal + 0, m_eff, work); count_launch();
+    if (n_eig > 0) {
+        k_tridiag_kth<<<n_eig, 32, 0, st>>>(alpha, beta, steps, m_eff, d_eigs); count_launch();
+    }
     if (store) {
         k_combine<kC><<<vgrid, kRedThreads, 0, st>>>(psi, V, y, m_eff, n); count_launch();
     } else {
@@ -621,6 +766,8 @@ ed_status run_lanczos(const ed_operator *op, const ed_basis *b, const void *x0, 
     ED_L_TRY(cudaGetLastError());
     double res[2] = {0.0, 0.0};
     ED_L_TRY(cudaMemcpyAsync(res, scal + 2, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
+    if (n_eig > 0 && eigs_out)
+        ED_L_TRY(cudaMemcpyAsync(eigs_out, d_eigs, n_eig * sizeof(double), cudaMemcpyDeviceToHost, st));
     ED_L_TRY(cudaStreamSynchronize(st));
     if (e0_out)
         *e0_out = res[0];
@@ -638,18 +785,22 @@ ed_status run_lanczos(const ed_operator *op, const ed_basis *b, const void *x0, 
 }  // namespace
 }  // namespace edk
 
-extern "C" ed_status ed_lanczos(const ed_operator *op, const ed_basis *b, const void *x0, int steps,
-                                int mode_flags, double *e0_out, void *vec_out,
-                                ed_lanczos_info *info, void *stream)
+namespace {
+ed_status lanczos_entry(const ed_operator *op, const ed_basis *b, const void *x0, int steps, int mode_flags,
+                        int n_eig, double *eigs_out, double *e0_out, void *vec_out, ed_lanczos_info *info,
+                        void *stream)
 {
     if (!op || !b || steps < 1 || steps > 10000)
         return ED_ERR_INVALID_ARG;
-    const int base = mode_flags & ~(ED_LANCZOS_RECOMPUTE | ED_LANCZOS_PUSH);
+    const int base = mode_flags & ~(ED_LANCZOS_RECOMPUTE | ED_LANCZOS_PUSH | ED_LANCZOS_REORTH);
     if (base != ED_LANCZOS_F64 && base != ED_LANCZOS_F32_MATVEC)
+        return ED_ERR_INVALID_ARG;
+    if (n_eig < 0 || n_eig > steps || (n_eig > 0 && !eigs_out))
         return ED_ERR_INVALID_ARG;
     const ed_lanczos_mode mode = (ed_lanczos_mode)base;
     const bool recompute = (mode_flags & ED_LANCZOS_RECOMPUTE) != 0;
     const bool push = (mode_flags & ED_LANCZOS_PUSH) != 0;
+    const bool reorth = (mode_flags & ED_LANCZOS_REORTH) != 0;
     if (b->dim == 0 || !x0)
         return ED_ERR_INVALID_ARG;
     if (((uintptr_t)x0 | (uintptr_t)vec_out) & 15)
@@ -659,8 +810,23 @@ extern "C" ed_status ed_lanczos(const ed_operator *op, const ed_basis *b, const 
         return st;
     const bool cplx = !(b->real_chars && op->real);
     if (cplx)
-        return edk::run_lanczos<true>(op, b, x0, steps, mode, recompute, push, e0_out, vec_out, info,
-                                      (cudaStream_t)stream);
-    return edk::run_lanczos<false>(op, b, x0, steps, mode, recompute, push, e0_out, vec_out, info,
-                                   (cudaStream_t)stream);
+        return edk::run_lanczos<true>(op, b, x0, steps, mode, recompute, push, reorth, n_eig, eigs_out, e0_out,
+                                      vec_out, info, (cudaStream_t)stream);
+    return edk::run_lanczos<false>(op, b, x0, steps, mode, recompute, push, reorth, n_eig, eigs_out, e0_out,
+                                   vec_out, info, (cudaStream_t)stream);
+}
+}  // namespace
+
+extern "C" ed_status ed_lanczos(const ed_operator *op, const ed_basis *b, const void *x0, int steps,
+                                int mode_flags, double *e0_out, void *vec_out,
+                                ed_lanczos_info *info, void *stream)
+{
+    return lanczos_entry(op, b, x0, steps, mode_flags, 0, nullptr, e0_out, vec_out, info, stream);
+}
+
+extern "C" ed_status ed_lanczos_eigs(const ed_operator *op, const ed_basis *b, const void *x0, int steps,
+                                     int mode_flags, int n_eig, double *eigs_out, void *vec_out,
+                                     ed_lanczos_info *info, void *stream)
+{
+    return lanczos_entry(op, b, x0, steps, mode_flags, n_eig, eigs_out, nullptr, vec_out, info, stream);
 }

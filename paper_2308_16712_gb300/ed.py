@@ -20,6 +20,7 @@ LIB_PATH = os.path.join(_HERE, "libed.so")
 ED_OK = 0
 ED_F64, ED_F32, ED_C128, ED_C64 = 0, 1, 2, 3
 ED_LANCZOS_F64, ED_LANCZOS_F32_MATVEC, ED_LANCZOS_RECOMPUTE, ED_LANCZOS_PUSH = 0, 1, 16, 32
+ED_LANCZOS_REORTH = 64
 
 STATUS_NAMES = {
     0: "ED_OK", 1: "ED_ERR_INVALID_ARG", 2: "ED_ERR_NOT_A_GROUP", 3: "ED_ERR_BAD_CHARACTER",
@@ -62,6 +63,8 @@ _SIGS = {
     "ed_matvec_multi": (_i32, [_P, _P, _i32, _i32, _i32, _P]),
     "ed_lanczos": (_i32, [_P, _P, _P, _i32, _i32, ctypes.POINTER(_d), _P,
                           ctypes.POINTER(LanczosInfo), _P]),
+    "ed_lanczos_eigs": (_i32, [_P, _P, _P, _i32, _i32, _i32, ctypes.POINTER(_d), _P,
+                               ctypes.POINTER(LanczosInfo), _P]),
     "ed_lanczos_multi": (_i32, [_P, _P, _i32, _i32, _i32, _i32, ctypes.POINTER(_d),
                                 ctypes.POINTER(LanczosInfo), _P]),
     "ed_basis_count_noalloc": (_i32, [_i32, _i32, _i32, _i32, _P, _P, _P, ctypes.POINTER(_u64)]),
@@ -360,6 +363,18 @@ def lanczos(op: Operator, basis: Basis, x0, steps: int, mode: int = ED_LANCZOS_F
                            _stream(stream)), "ed_lanczos")
     return LanczosResult(e0.value, info.steps, info.matvecs, info.ritz, info.residual,
                          info.matvec_ms)
+
+
+def lanczos_eigs(op: Operator, basis: Basis, x0, steps: int, n_eig: int, mode: int = ED_LANCZOS_F64,
+                 vec_out=None, stream=None):
+    """(lowest n_eig Ritz values as a list, LanczosResult of the lowest state)."""
+    eigs = (ctypes.c_double * max(n_eig, 1))()
+    info = LanczosInfo()
+    _check(_lib.ed_lanczos_eigs(op.handle, basis.handle, _ptr(x0), steps, mode, n_eig, eigs,
+                                _ptr(vec_out) if vec_out is not None else None, ctypes.byref(info),
+                                _stream(stream)), "ed_lanczos_eigs")
+    return list(eigs[:n_eig]), LanczosResult(info.e0, info.steps, info.matvecs, info.ritz, info.residual,
+                                             info.matvec_ms)
 
 
 def lanczos_multi(op: Operator, items, steps: int, mode: int = ED_LANCZOS_F64,

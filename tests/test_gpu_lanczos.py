@@ -98,3 +98,72 @@ def test_push_mode_lanczos():
         assert r.residual < 1e-6
     with pytest.raises(ed.EDError):
         ed.lanczos(S["O"], S["B"], x0, 50, ed.ED_LANCZOS_F64 | ed.ED_LANCZOS_PUSH | ed.ED_LANCZOS_RECOMPUTE)
+
+
+def _heisenberg12_real_sectors(ed):
+    n = 12
+    op = ei.heisenberg_ring(n)
+    out = []
+    for k in (0, 6):
+        for par in (1, -1):
+            p, c = ei.ring_group(n, k, par)
+            out.append(build_pair(n, n // 2, +1, p, c, op))
+    return out
+
+
+@pytest.mark.parametrize("reorth", [False, True], ids=["plain", "reorth"])
+@pytest.mark.parametrize("steps", [3, 6, 10])
+def test_eigs_short_runs_match_oracle(steps, reorth):
+    """The lowest Ritz values after `steps` steps against the eigenvalues of the
+    oracle's tridiagonal matrix from the same start vector (plain recurrence, or
+    classical Gram-Schmidt twice against all earlier vectors)."""
+    from scipy.linalg import eigh_tridiagonal
+    torch, ed = gpu()
+    flags = ed.ED_LANCZOS_F64 | (ed.ED_LANCZOS_REORTH if reorth else 0)
+    for S in _heisenberg12_real_sectors(ed):
+        if S["dim"] <= steps:
+            continue
+        Hd = oracle.dense_matrix(S["G"], S["H"], S["st"], S["nm"]).real
+        x0 = ei.x_by_state(3, S["st"])[:, 0]
+        a, b, _ = oracle.lanczos(lambda v: Hd @ v, x0, steps, reorth=reorth)
+        want = eigh_tridiagonal(a, b, eigvals_only=True)
+        n_eig = min(3, steps)
+        eigs, r = ed.lanczos_eigs(S["O"], S["B"], to_torch(x0, np.float64), steps, n_eig, flags)
+        for g, e in zip(eigs, want[:n_eig]):
+            assert abs(g - e) <= 1e-12 * max(1.0, abs(e)), (steps, reorth, eigs, want[:n_eig])
+
+
+def test_eigs_low_spectrum_with_reorthogonalisation():
+    """ring N=16 sector (dimension 257), 120 steps with full reorthogonalisation:
+    the five lowest Ritz values are the five lowest eigenvalues of the dense
+    sector matrix (fp64 within 1e-9; fp32 products within 2e-6 relative)."""
+    torch, ed = gpu()
+    w = ei.workload("ring16")
+    S = build_pair(16, 8, +1, w["perms"], w["chars"], w["op"])
+    ev = np.linalg.eigvalsh(oracle.dense_matrix(S["G"], S["H"], S["st"], S["nm"]).real)
+    x0 = to_torch(ei.x_by_index(0, S["dim"])[:, 0], np.float64)
+    eigs, r = ed.lanczos_eigs(S["O"], S["B"], x0, 120, 5, ed.ED_LANCZOS_F64 | ed.ED_LANCZOS_REORTH)
+    assert np.max(np.abs(np.array(eigs) - ev[:5])) < 1e-9
+    assert abs(r.e0 - ev[0]) < 1e-10
+    eigs32, r32 = ed.lanczos_eigs(S["O"], S["B"], x0, 120, 5, ed.ED_LANCZOS_F32_MATVEC | ed.ED_LANCZOS_REORTH)
+    assert np.max(np.abs(np.array(eigs32) - ev[:5]) / np.abs(ev[:5])) < 2e-6
+    assert abs(r32.e0 - ev[0]) < 1e-10
+    # beyond the Krylov space (29 states, 28 distinct eigenvalues: a single start
+    # vector spans 28 dimensions): the 28 distinct eigenvalues, then NaN
+    small = build_pair(12, 6, +1, *ei.ring_group(12, 6, -1), ei.heisenberg_ring(12))
+    ev_s = np.linalg.eigvalsh(oracle.dense_matrix(small["G"], small["H"], small["st"], small["nm"]).real)
+    distinct = [ev_s[0]]
+    for e in ev_s[1:]:
+        if e - distinct[-1] > 1e-8:
+            distinct.append(e)
+    xs = to_torch(ei.x_by_index(1, small["dim"])[:, 0], np.float64)
+    e_s, r_s = ed.lanczos_eigs(small["O"], small["B"], xs, 40, 40, ed.ED_LANCZOS_F64 | ed.ED_LANCZOS_REORTH)
+    nd = len(distinct)
+    assert small["dim"] == 29 and nd == 28 and r_s.steps == nd
+    assert np.max(np.abs(np.array(e_s[:nd]) - np.array(distinct))) < 1e-9
+    assert np.all(np.isnan(e_s[nd:]))
+    with pytest.raises(ed.EDError):
+        ed.lanczos_eigs(S["O"], S["B"], x0, 20, 21)
+    with pytest.raises(ed.EDError):
+        ed.lanczos_eigs(S["O"], S["B"], x0, 20, 2,
+                        ed.ED_LANCZOS_F64 | ed.ED_LANCZOS_REORTH | ed.ED_LANCZOS_RECOMPUTE)
