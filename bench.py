@@ -16,8 +16,9 @@ GPUs; with --gpus N every rank runs an independent replica (weak scaling,
 value = the sum over ranks), with a barrier and the max over ranks of the
 timed region.
 
---impl reference times the CPU oracle (plain C, one core) on a bounded sample
-of the same rows and prints the same JSON line with "impl": "reference".
+--impl reference times the CPU oracle (plain C, on all host cores through a
+spawned process pool) on a bounded sample of the same rows and prints the
+same JSON line with "impl": "reference".
 """
 from __future__ import annotations
 
@@ -172,17 +173,54 @@ def time_oracle_rows(G, H, rows):
     return time.perf_counter() - t0, nnz
 
 
-def cpu_baseline(w, budget_s=15.0):
+def _oracle_rows_worker(task):
+    """One worker of the all-cores oracle run (a spawned process): the oracle's
+    rows for a chunk of row states; returns the seconds it took."""
+    import oracle
+    n, perms, chars, z, op, rows = task
+    G = oracle.Group(n, perms, chars, z)
+    H = oracle.Operator(op)
+    t0 = time.perf_counter()
+    oracle.rows_statex(G, H, rows, 0)
+    return time.perf_counter() - t0
+
+
+def host_cores():
+    return len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
+
+
+def time_oracle_rows_all_cores(w, rows, cores):
+    """The unchanged oracle on all host cores: the rows split into one chunk per
+    core, each chunk run by a process of a spawn-started pool (wall time of the
+    parallel map, after a warm-up map that loads the oracle in every worker)."""
+    import multiprocessing as mp
+    task = (w["n_sites"], w["perms"], w["chars"], w["spin_inversion"], w["op"])
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(cores) as pool:
+        pool.map(_oracle_rows_worker, [task + (rows[:2],)] * cores)
+        t0 = time.perf_counter()
+        pool.map(_oracle_rows_worker, [task + (c,) for c in np.array_split(rows, cores)])
+        return time.perf_counter() - t0
+
+
+def cpu_baseline(w, budget_s=15.0, par_wall_s=5.0):
     G, H, rows = oracle_rows(w, 64)
     dt, _ = time_oracle_rows(G, H, rows[:8])
     per_row = max(dt / 8, 1e-6)
     n = int(min(max(budget_s / per_row, 16), 20000))
     G, H, rows = oracle_rows(w, n, seed=2)
     dt, nnz = time_oracle_rows(G, H, rows)
-    return {"value": len(rows) / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{len(rows)} rows of the {w['name']} sector (one H.x row each, x keyed "
-                      f"by state, no basis enumeration), single-threaded C oracle, {dt:.1f} s",
-            "nnz_per_row": float(nnz.mean())}
+    single = {"value": len(rows) / dt, "cores": 1,
+              "sample": f"{len(rows)} rows, single-threaded C oracle, {dt:.1f} s"}
+    cores = host_cores()
+    reps = max(1, int(par_wall_s * cores / (dt / len(rows)) / len(rows)))
+    rows_par = np.tile(rows, reps)
+    dtp = time_oracle_rows_all_cores(w, rows_par, cores)
+    return {"value": len(rows_par) / dtp, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{len(rows_par)} rows of the {w['name']} sector ({len(rows)} distinct, each an "
+                      f"H.x row with x keyed by state, no basis enumeration), the C oracle in {cores} "
+                      f"spawned processes, {dtp:.1f} s wall",
+            "single_core": single, "nnz_per_row": float(nnz.mean())}
 
 
 def run_reference(args, w, budget_s=150.0):
@@ -196,23 +234,26 @@ def run_reference(args, w, budget_s=150.0):
     dt, _ = time_oracle_rows(G, H, rows[:8])
     per_row = max(dt / 8, 1e-6)
     rows_per_step = int(min(max(budget_s / (args.steps + args.warmup) / per_row, 8), 20000))
-    G, H, rows = oracle_rows(w, rows_per_step * (args.steps + args.warmup), seed=3)
-    chunks = np.array_split(rows, args.steps + args.warmup)
-    for c in chunks[: args.warmup]:
-        time_oracle_rows(G, H, c)
+    # each step: the same number of rows per core as the single-core estimate
+    # allows in the budget, run by the oracle on all host cores
+    cores = host_cores()
+    G, H, rows = oracle_rows(w, rows_per_step, seed=3)
+    step_rows = np.tile(rows, cores)
+    for _ in range(args.warmup):
+        time_oracle_rows_all_cores(w, step_rows[: max(cores, len(step_rows) // 8)], cores)
     total, n_done = 0.0, 0
-    for c in chunks[args.warmup:]:
-        dt, _ = time_oracle_rows(G, H, c)
-        total += dt
-        n_done += len(c)
+    for _ in range(args.steps):
+        total += time_oracle_rows_all_cores(w, step_rows, cores)
+        n_done += len(step_rows)
     value = n_done / total
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": {"workload": w["name"], "rows_per_step": rows_per_step},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": f"{rows_per_step} rows per step of the {w['name']} sector, "
-                                       "single-threaded C oracle (x keyed by state)"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"{len(step_rows)} rows per step of the {w['name']} sector "
+                                       f"({rows_per_step} distinct), the C oracle in {cores} spawned "
+                                       "processes (x keyed by state)"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return line
