@@ -293,9 +293,11 @@ def run_matvec_only(args, w):
     cplx = not ed.basis_is_real(B)
     nvec = args.nvec
     states, _ = ed.basis_states(B)
+    nnz = ed.count_nnz(O, B)
     out = {"mode": "matvec", "workload": w["name"], "dim": dim, "nvec": nvec, "basis_build_ms": build_ms,
-           "launches": 2 * args.steps}
+           "launches": 2 * args.steps, "nnz_per_matvec": nnz, "nnz_per_row": nnz / max(dim, 1)}
     dts = (torch.complex64, torch.complex128) if cplx else (torch.float32, torch.float64)
+    y_single = None
     for dt in dts:
         x = ei.x_by_state_torch_chunked(5, states, nvec, cplx, dtype=dt)
         y = torch.empty_like(x)
@@ -307,9 +309,22 @@ def run_matvec_only(args, w):
             b.record()
             torch.cuda.synchronize()
             ts.append(a.elapsed_time(b))
-        out[str(dt).replace("torch.", "")] = {"ms": min(ts), "rows_per_s": dim / (min(ts) * 1e-3),
-                                             "vector_rows_per_s": nvec * dim / (min(ts) * 1e-3)}
+        ms = min(ts)
+        res = {"ms": ms, "rows_per_s": dim / (ms * 1e-3), "vector_rows_per_s": nvec * dim / (ms * 1e-3),
+               "nonzeros_per_s": nnz / (ms * 1e-3)}
+        if y_single is None:
+            y_single = y  # single precision first: kept for the error against double
+        else:
+            # max |y_single - y_double| / max |y_double| over the whole product
+            err, scale = 0.0, float(y.abs().max())
+            for lo in range(0, y.shape[0], 1 << 26):
+                d = y_single[lo:lo + (1 << 26)].to(y.dtype) - y[lo:lo + (1 << 26)]
+                err = max(err, float(d.abs().max()))
+            out["single_precision_max_rel_err"] = err / max(scale, 1e-300)
+            y_single = None
+        out[str(dt).replace("torch.", "")] = res
         del x, y
+        torch.cuda.empty_cache()
     print(json.dumps(out))
 
 

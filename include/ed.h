@@ -313,6 +313,9 @@ ed_status ed_lanczos(const ed_operator *op, const ed_basis *basis, const void *d
  *   n_eig     0..steps
  *   eigs_out  host, n_eig values, ascending; NaN past the dimension of the
  *             Krylov space actually built (a sector smaller than `steps`)
+ *   tol       > 0: return ED_ERR_NOT_CONVERGED (with every output filled) when
+ *             the fp64 residual |H psi - e0 psi| / |psi| of the returned state
+ *             exceeds tol; <= 0: no check
  *   other arguments as ed_lanczos (the refined lowest energy is in info->e0)
  *
  * Without ED_LANCZOS_REORTH the plain recurrence loses orthogonality once the
@@ -320,11 +323,12 @@ ed_status ed_lanczos(const ed_operator *op, const ed_basis *basis, const void *d
  * ("ghosts") among the higher ones; with it, the values are those of an
  * orthonormal Krylov basis.  In the fp32-matvec mode the values carry the fp32
  * products' error (about 1e-7 relative); only the lowest is refined.
- * Errors as ed_lanczos, and ED_ERR_INVALID_ARG for n_eig out of range.
+ * Errors as ed_lanczos, ED_ERR_INVALID_ARG for n_eig out of range,
+ * ED_ERR_NOT_CONVERGED as above.
  */
 ed_status ed_lanczos_eigs(const ed_operator *op, const ed_basis *basis, const void *d_x0, int steps,
-                          int mode, int n_eig, double *eigs_out, void *d_vec_out, ed_lanczos_info *info,
-                          void *stream);
+                          int mode, int n_eig, double *eigs_out, double tol, void *d_vec_out,
+                          ed_lanczos_info *info, void *stream);
 
 /*
  * ed_lanczos_multi -- lowest eigenvalue of H in each of up to 160 symmetry

@@ -787,8 +787,8 @@ ed_status run_lanczos(const ed_operator *op, const ed_basis *b, const void *x0, 
 
 namespace {
 ed_status lanczos_entry(const ed_operator *op, const ed_basis *b, const void *x0, int steps, int mode_flags,
-                        int n_eig, double *eigs_out, double *e0_out, void *vec_out, ed_lanczos_info *info,
-                        void *stream)
+                        int n_eig, double *eigs_out, double tol, double *e0_out, void *vec_out,
+                        ed_lanczos_info *info, void *stream)
 {
     if (!op || !b || steps < 1 || steps > 10000)
         return ED_ERR_INVALID_ARG;
@@ -809,11 +809,15 @@ ed_status lanczos_entry(const ed_operator *op, const ed_basis *b, const void *x0
     if (st != ED_OK)
         return st;
     const bool cplx = !(b->real_chars && op->real);
-    if (cplx)
-        return edk::run_lanczos<true>(op, b, x0, steps, mode, recompute, push, reorth, n_eig, eigs_out, e0_out,
-                                      vec_out, info, (cudaStream_t)stream);
-    return edk::run_lanczos<false>(op, b, x0, steps, mode, recompute, push, reorth, n_eig, eigs_out, e0_out,
-                                   vec_out, info, (cudaStream_t)stream);
+    ed_lanczos_info local{};
+    ed_lanczos_info *inf = info ? info : &local;
+    const ed_status r = cplx ? edk::run_lanczos<true>(op, b, x0, steps, mode, recompute, push, reorth, n_eig,
+                                                      eigs_out, e0_out, vec_out, inf, (cudaStream_t)stream)
+                             : edk::run_lanczos<false>(op, b, x0, steps, mode, recompute, push, reorth, n_eig,
+                                                       eigs_out, e0_out, vec_out, inf, (cudaStream_t)stream);
+    if (r == ED_OK && tol > 0.0 && !(inf->residual <= tol))
+        return ED_ERR_NOT_CONVERGED;
+    return r;
 }
 }  // namespace
 
@@ -821,12 +825,12 @@ extern "C" ed_status ed_lanczos(const ed_operator *op, const ed_basis *b, const 
                                 int mode_flags, double *e0_out, void *vec_out,
                                 ed_lanczos_info *info, void *stream)
 {
-    return lanczos_entry(op, b, x0, steps, mode_flags, 0, nullptr, e0_out, vec_out, info, stream);
+    return lanczos_entry(op, b, x0, steps, mode_flags, 0, nullptr, 0.0, e0_out, vec_out, info, stream);
 }
 
 extern "C" ed_status ed_lanczos_eigs(const ed_operator *op, const ed_basis *b, const void *x0, int steps,
-                                     int mode_flags, int n_eig, double *eigs_out, void *vec_out,
+                                     int mode_flags, int n_eig, double *eigs_out, double tol, void *vec_out,
                                      ed_lanczos_info *info, void *stream)
 {
-    return lanczos_entry(op, b, x0, steps, mode_flags, n_eig, eigs_out, nullptr, vec_out, info, stream);
+    return lanczos_entry(op, b, x0, steps, mode_flags, n_eig, eigs_out, tol, nullptr, vec_out, info, stream);
 }

@@ -63,7 +63,7 @@ _SIGS = {
     "ed_matvec_multi": (_i32, [_P, _P, _i32, _i32, _i32, _P]),
     "ed_lanczos": (_i32, [_P, _P, _P, _i32, _i32, ctypes.POINTER(_d), _P,
                           ctypes.POINTER(LanczosInfo), _P]),
-    "ed_lanczos_eigs": (_i32, [_P, _P, _P, _i32, _i32, _i32, ctypes.POINTER(_d), _P,
+    "ed_lanczos_eigs": (_i32, [_P, _P, _P, _i32, _i32, _i32, ctypes.POINTER(_d), _d, _P,
                                ctypes.POINTER(LanczosInfo), _P]),
     "ed_lanczos_multi": (_i32, [_P, _P, _i32, _i32, _i32, _i32, ctypes.POINTER(_d),
                                 ctypes.POINTER(LanczosInfo), _P]),
@@ -366,11 +366,12 @@ def lanczos(op: Operator, basis: Basis, x0, steps: int, mode: int = ED_LANCZOS_F
 
 
 def lanczos_eigs(op: Operator, basis: Basis, x0, steps: int, n_eig: int, mode: int = ED_LANCZOS_F64,
-                 vec_out=None, stream=None):
-    """(lowest n_eig Ritz values as a list, LanczosResult of the lowest state)."""
+                 vec_out=None, tol: float = 0.0, stream=None):
+    """(lowest n_eig Ritz values as a list, LanczosResult of the lowest state);
+    with tol > 0 an EDError (ED_ERR_NOT_CONVERGED) when the residual exceeds tol."""
     eigs = (ctypes.c_double * max(n_eig, 1))()
     info = LanczosInfo()
-    _check(_lib.ed_lanczos_eigs(op.handle, basis.handle, _ptr(x0), steps, mode, n_eig, eigs,
+    _check(_lib.ed_lanczos_eigs(op.handle, basis.handle, _ptr(x0), steps, mode, n_eig, eigs, float(tol),
                                 _ptr(vec_out) if vec_out is not None else None, ctypes.byref(info),
                                 _stream(stream)), "ed_lanczos_eigs")
     return list(eigs[:n_eig]), LanczosResult(info.e0, info.steps, info.matvecs, info.ritz, info.residual,

@@ -164,6 +164,11 @@ def test_eigs_low_spectrum_with_reorthogonalisation():
     assert np.all(np.isnan(e_s[nd:]))
     with pytest.raises(ed.EDError):
         ed.lanczos_eigs(S["O"], S["B"], x0, 20, 21)
+    # residual check: 5 steps cannot reach 1e-10; 120 steps reach 1e-6
+    with pytest.raises(ed.EDError) as err:
+        ed.lanczos_eigs(S["O"], S["B"], x0, 5, 1, tol=1e-10)
+    assert err.value.status == 8  # ED_ERR_NOT_CONVERGED
+    ed.lanczos_eigs(S["O"], S["B"], x0, 120, 1, ed.ED_LANCZOS_F64 | ed.ED_LANCZOS_REORTH, tol=1e-6)
     with pytest.raises(ed.EDError):
         ed.lanczos_eigs(S["O"], S["B"], x0, 20, 2,
                         ed.ED_LANCZOS_F64 | ed.ED_LANCZOS_REORTH | ed.ED_LANCZOS_RECOMPUTE)
