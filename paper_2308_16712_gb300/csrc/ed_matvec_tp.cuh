@@ -50,6 +50,13 @@ struct TpWarp {
     uint8_t p2r[32];    // row whose terms start at lane p of the current round
 };
 
+// One-family operators: each warp lists its rows' terms in shared memory once
+// per tile (site i, | 0x80 for configuration |10>), n_sites bytes per row.
+__host__ __device__ inline int tp_term_stride(const GroupView &g, const OpView &op)
+{
+    return op.n_fam == 1 ? (g.n_sites + 7) & ~7 : 0;
+}
+
 template <typename W, typename T, typename V, bool kFact>
 __host__ __device__ inline void tp_smem_layout(const GroupView &g, const OpView &op, int n_sectors,
                                                int max_order, size_t off[8])
@@ -65,13 +72,19 @@ __host__ __device__ inline void tp_smem_layout(const GroupView &g, const OpView 
     off[7] = align16(off[6] + (size_t)n_sectors * sizeof(SectorDesc));           // warps
 }
 
+template <typename W, typename T, typename V>
+__host__ __device__ inline size_t tp_terms_offset(size_t warps_off)
+{
+    return align16(warps_off + kTpWarps * sizeof(TpWarp<W, T, V>));
+}
+
 template <typename W, typename T, typename V, bool kFact>
 __host__ __device__ inline size_t tp_smem_bytes(const GroupView &g, const OpView &op, int n_sectors,
                                                 int max_order)
 {
     size_t off[8];
     tp_smem_layout<W, T, V, kFact>(g, op, n_sectors, max_order, off);
-    return off[7] + kTpWarps * sizeof(TpWarp<W, T, V>);
+    return tp_terms_offset<W, T, V>(off[7]) + (size_t)kTpWarps * 32 * tp_term_stride(g, op);
 }
 
 // position of the u-th set bit of b (u < popc(b)), branch-free halving
@@ -141,6 +154,8 @@ __global__ void __launch_bounds__(kTpThreads, 8) k_matvec_tp(const __grid_consta
     T *sm_isq = sm_sq + (a.max_order + 1);
     SectorDesc *sm_sec = reinterpret_cast<SectorDesc *>(smem + off[6]);
     TpWarp<W, T, V> *sm_warp = reinterpret_cast<TpWarp<W, T, V> *>(smem + off[7]);
+    const int tstride = tp_term_stride(a.g, a.op);
+    uint8_t *sm_terms = smem + tp_terms_offset<W, T, V>(off[7]) + (size_t)(threadIdx.x >> 5) * 32 * tstride;
     {
         const int nm = kFact ? a.g.n_cos : a.g.n_perm;
         const W *gm;
@@ -261,6 +276,21 @@ __global__ void __launch_bounds__(kTpThreads, 8) k_matvec_tp(const __grid_consta
         ws.r[lane] = r;
         ws.rinv[lane] = rinv;
         ws.off[lane] = offl;
+        if (n_fam == 1 && nt) {  // list the row's antiparallel bonds once per tile
+            const OpFamily fm = sm_fam[0];
+            const W tq = rot_down(r, (int)fm.delta, n, full);
+            int k = 0;
+#pragma unroll
+            for (int cc = 1; cc <= 2; ++cc) {
+                if (sm_off[fm.mat * 4 + cc]) {
+                    W bits = config_mask(r, tq, (W)fm.mask, cc);
+                    while (bits) {
+                        sm_terms[lane * tstride + k++] = (uint8_t)(lowest_bit(bits) | (cc == 2 ? 0x80 : 0));
+                        bits &= bits - 1;
+                    }
+                }
+            }
+        }
         __syncwarp();
 
         const E *__restrict__ hent = reinterpret_cast<const E *>(sd.hent);
@@ -284,7 +314,17 @@ __global__ void __launch_bounds__(kTpThreads, 8) k_matvec_tp(const __grid_consta
             // (family, configuration |01> then |10>, site) order
             W s = 0;
             int amp = 0;
-            if (act) {
+            if (act && n_fam == 1) {
+                const W rr = ws.r[rho];
+                const uint32_t code = sm_terms[rho * tstride + (t - ws.off[rho])];
+                const OpFamily fm = sm_fam[0];
+                const int i = (int)(code & 63u);
+                const int cc = code & 0x80u ? 2 : 1;
+                amp = (int)fm.mat * 16 + (3 - cc) * 4 + cc;
+                int j = i + (int)fm.delta;
+                j -= j >= n ? n : 0;
+                s = rr ^ (W(1) << i) ^ (W(1) << j);
+            } else if (act) {
                 const W rr = ws.r[rho];
                 int u = (int)(t - ws.off[rho]);
                 W sel = 0;
