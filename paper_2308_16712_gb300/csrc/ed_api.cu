@@ -661,6 +661,7 @@ ed_status basis_build_impl(int n_sites, int n_up, int spin_inversion, int n_elem
             (void)cudaGetLastError();            \
             free_basis(b);                       \
             cudaFree(d_counts);                  \
+            cudaFree(d_flags);                   \
             cudaFree(d_offsets);                 \
             cudaFree(d_tmp);                     \
             cudaFree(d_binom);                   \
@@ -668,7 +669,7 @@ ed_status basis_build_impl(int n_sites, int n_up, int spin_inversion, int n_elem
             return _e == cudaErrorMemoryAllocation ? ED_ERR_OOM : ED_ERR_CUDA; \
         }                                        \
     } while (0)
-    uint32_t *d_counts = nullptr;
+    uint32_t *d_counts = nullptr, *d_flags = nullptr;
     uint64_t *d_offsets = nullptr, *d_tmp = nullptr, *d_binom = nullptr;
     int *d_flag = nullptr;
     ED_B_TRY(upload(&b->d_masks32, m32.data(), m32.size()));
@@ -738,6 +739,17 @@ ed_status basis_build_impl(int n_sites, int n_up, int spin_inversion, int n_elem
     ED_B_TRY(cudaMalloc(&d_counts, plan.n_chunks * sizeof(uint32_t)));
     ED_B_TRY(cudaMalloc(&d_offsets, (plan.n_chunks + 1) * sizeof(uint64_t)));
     ED_B_TRY(cudaMalloc(&d_tmp, edk::scan_tmp_words(plan.n_chunks) * sizeof(uint64_t)));
+    if (!count_only) {  // kept-state bits for the write pass, when they take <= 1/8 of free memory
+        size_t free_b = 0, total_b = 0;
+        cudaMemGetInfo(&free_b, &total_b);
+        const uint64_t words = (plan.chunk + 31) / 32;
+        const uint64_t bytes = plan.n_chunks * words * sizeof(uint32_t);
+        if (bytes <= free_b / 8 && cudaMalloc(&d_flags, bytes) == cudaSuccess) {
+            plan.flags = d_flags;
+            plan.flag_words = (uint32_t)words;
+        }
+        (void)cudaGetLastError();
+    }
     ED_B_TRY(edk::launch_enum_count(plan, gv, d_counts, stream));
     ED_B_TRY(edk::launch_scan(d_counts, plan.n_chunks, d_offsets, d_tmp, stream));
     uint64_t dim = 0;
@@ -752,7 +764,7 @@ ed_status basis_build_impl(int n_sites, int n_up, int spin_inversion, int n_elem
     }
     if (dim >= (1ULL << 32)) {
         free_basis(b);
-        cudaFree(d_counts); cudaFree(d_offsets); cudaFree(d_tmp); cudaFree(d_binom);
+        cudaFree(d_counts); cudaFree(d_flags); cudaFree(d_offsets); cudaFree(d_tmp); cudaFree(d_binom);
         return ED_ERR_UNSUPPORTED;
     }
     b->dim = dim;
@@ -857,6 +869,7 @@ ed_status basis_build_impl(int n_sites, int n_up, int spin_inversion, int n_elem
         b->probe_iters = k;
     }
     cudaFree(d_counts);
+    cudaFree(d_flags);
     cudaFree(d_offsets);
     cudaFree(d_tmp);
     cudaFree(d_binom);

@@ -136,9 +136,21 @@ __global__ void __launch_bounds__(kEnumThreads) k_enumerate(EnumPlan plan, Group
         uint64_t s = kU1 ? unrank_colex(r0, plan.n_sites, plan.n_up, plan.binom) : r0;
         uint32_t kept = 0;
         uint64_t out = kWrite ? offsets[c] : 0;
+        uint32_t *cflags = plan.flags ? plan.flags + c * plan.flag_words : nullptr;
+        uint32_t word = 0;
         for (uint64_t q = 0; q < cnt; ++q) {
-            const int nrm = kFact ? rep_norm_fact<W>((W)s, sm_kind, sm_masks, sm_one, g, full)
-                                  : rep_norm<W>((W)s, sm_masks, sm_one, g.n_perm, g.flip, full);
+            int nrm;
+            if (kWrite && cflags) {  // only the states the count pass kept
+                if ((q & 31) == 0)
+                    word = cflags[q >> 5];
+                nrm = (word >> (q & 31)) & 1u
+                          ? (kFact ? rep_norm_fact<W>((W)s, sm_kind, sm_masks, sm_one, g, full)
+                                   : rep_norm<W>((W)s, sm_masks, sm_one, g.n_perm, g.flip, full))
+                          : 0;
+            } else {
+                nrm = kFact ? rep_norm_fact<W>((W)s, sm_kind, sm_masks, sm_one, g, full)
+                            : rep_norm<W>((W)s, sm_masks, sm_one, g.n_perm, g.flip, full);
+            }
             if (nrm) {
                 if (kWrite) {
                     states[out] = s;
@@ -146,6 +158,13 @@ __global__ void __launch_bounds__(kEnumThreads) k_enumerate(EnumPlan plan, Group
                     ++out;
                 }
                 ++kept;
+            }
+            if (!kWrite && cflags) {
+                word |= (nrm ? 1u : 0u) << (q & 31);
+                if ((q & 31) == 31 || q + 1 == cnt) {
+                    cflags[q >> 5] = word;
+                    word = 0;
+                }
             }
             if (q + 1 < cnt)
                 s = kU1 ? next_combination(s) : s + 1;

@@ -22,6 +22,11 @@ struct EnumPlan {
     uint64_t chunk;      // states per thread
     uint64_t n_chunks;
     const uint64_t *binom;  // device (65 x 65) binomial table
+    // Optional: one bit per visited state, set by the count pass for the
+    // states it keeps (flag_words 32-bit words per chunk); the write pass then
+    // tests only those states again (for their norms) instead of all of them.
+    uint32_t *flags = nullptr;
+    uint32_t flag_words = 0;
 };
 
 // Reads and clears the basis kernels' device status word (synchronous).
