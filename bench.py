@@ -623,6 +623,25 @@ def main():
     rows64 = dim * r64.matvecs / (per64 * 1e-3)
     value = sum_over_ranks(rows32, world) if world > 1 else rows32
 
+    # where a step's time goes: basis build alone (events, L2 flushed first),
+    # products (CUDA events around every product inside ed_lanczos), the rest
+    build_ts = []
+    for _ in range(3):
+        flush_l2()
+        b0, b1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        b0.record(stream)
+        bb = ed.basis_build(n, n_up, z, w["perms"], w["chars"])
+        b1.record(stream)
+        torch.cuda.synchronize()
+        build_ts.append(b0.elapsed_time(b1))
+        del bb
+    build_ms = statistics.median(build_ts)
+    mv_step_ms = mv32_ms / args.steps
+    breakdown = {"basis_build_ms": build_ms, "products_ms": mv_step_ms,
+                 "products": mv32_n // max(args.steps, 1),
+                 "lanczos_vectors_and_rest_ms": per32 - build_ms - mv_step_ms}
+
     # single matvec launches (kernel level), L2 flushed between launches
     def matvec_rate(dtype, nvec, reps=5):
         xx = torch.from_numpy(ei.x_by_index(5, dim, nvec)).to(dev).to(dtype)
@@ -695,6 +714,7 @@ def main():
         "fp64_plain": {"value": rows64, "ms_per_step": per64, "e0": r64.e0, "residual": r64.residual,
                        "matvecs_per_step": r64.matvecs},
         "dE0": abs(r32.e0 - r64.e0),
+        "step_breakdown": breakdown,
         "push_mode": {"value": dim * rp.matvecs / (msp / max(1, args.steps) * 1e-3),
                       "ms_per_step": msp / max(1, args.steps), "e0": rp.e0, "dE0": abs(rp.e0 - r64.e0),
                       "note": "ED_LANCZOS_PUSH: atomic scatter products, E0 varies in the last bits"},

@@ -71,6 +71,17 @@ typedef enum {
 typedef struct ed_basis ed_basis;
 typedef struct ed_operator ed_operator;
 
+/*
+ * ed_release_cached_memory -- the library takes the arrays it allocates itself
+ * (the solvers' work vectors, the basis build's temporaries, the large arrays
+ * of a basis) from a stream-ordered device memory pool of its own, which keeps
+ * up to min(8 GiB, 1/16 of the device memory) of freed memory cached for the
+ * next call (allocating and freeing gigabytes with cudaMalloc / cudaFree costs
+ * milliseconds and synchronises the device).  This call returns the cached
+ * memory to the device.  Errors: ED_ERR_CUDA.
+ */
+ed_status ed_release_cached_memory(void);
+
 /* Human-readable name of a status code (static string). */
 const char *ed_status_string(ed_status status);
 

@@ -243,18 +243,21 @@ void free_basis(ed_basis *b)
 {
     if (!b)
         return;
+    // every launch that may still read the arrays has finished before they
+    // go back to the pool (the large ones) or to the device
+    cudaDeviceSynchronize();
     cudaFree(b->d_cos_kind);
     cudaFree(b->d_cos_masks32);
     cudaFree(b->d_cos_masks64);
     cudaFree(b->d_fchi);
     cudaFree(b->d_fchif);
     cudaFree(b->d_fchi_one);
-    cudaFree(b->d_states);
-    cudaFree(b->d_norms);
-    cudaFree(b->d_keys);
-    cudaFree(b->d_htab);
-    cudaFree(b->d_hent);
-    cudaFree(b->d_tab);
+    edk::ws_free(b->d_states, 0);
+    edk::ws_free(b->d_norms, 0);
+    edk::ws_free(b->d_keys, 0);
+    edk::ws_free(b->d_htab, 0);
+    edk::ws_free(b->d_hent, 0);
+    edk::ws_free(b->d_tab, 0);
     cudaFree(b->d_masks32);
     cudaFree(b->d_masks64);
     cudaFree(b->d_chi);
@@ -660,10 +663,10 @@ ed_status basis_build_impl(int n_sites, int n_up, int spin_inversion, int n_elem
         if (_e != cudaSuccess) {                 \
             (void)cudaGetLastError();            \
             free_basis(b);                       \
-            cudaFree(d_counts);                  \
-            cudaFree(d_flags);                   \
-            cudaFree(d_offsets);                 \
-            cudaFree(d_tmp);                     \
+            edk::ws_free(d_counts, stream);      \
+            edk::ws_free(d_flags, stream);       \
+            edk::ws_free(d_offsets, stream);     \
+            edk::ws_free(d_tmp, stream);         \
             cudaFree(d_binom);                   \
             cudaFree(d_flag);                    \
             return _e == cudaErrorMemoryAllocation ? ED_ERR_OOM : ED_ERR_CUDA; \
@@ -736,15 +739,15 @@ ed_status basis_build_impl(int n_sites, int n_up, int spin_inversion, int n_elem
     plan.binom = d_binom;
     const edk::GroupView gv = b->group_view();
 
-    ED_B_TRY(cudaMalloc(&d_counts, plan.n_chunks * sizeof(uint32_t)));
-    ED_B_TRY(cudaMalloc(&d_offsets, (plan.n_chunks + 1) * sizeof(uint64_t)));
-    ED_B_TRY(cudaMalloc(&d_tmp, edk::scan_tmp_words(plan.n_chunks) * sizeof(uint64_t)));
+    ED_B_TRY(edk::ws_alloc((void **)&d_counts, plan.n_chunks * sizeof(uint32_t), stream));
+    ED_B_TRY(edk::ws_alloc((void **)&d_offsets, (plan.n_chunks + 1) * sizeof(uint64_t), stream));
+    ED_B_TRY(edk::ws_alloc((void **)&d_tmp, edk::scan_tmp_words(plan.n_chunks) * sizeof(uint64_t), stream));
     if (!count_only) {  // kept-state bits for the write pass, when they take <= 1/8 of free memory
         size_t free_b = 0, total_b = 0;
         cudaMemGetInfo(&free_b, &total_b);
         const uint64_t words = (plan.chunk + 31) / 32;
         const uint64_t bytes = plan.n_chunks * words * sizeof(uint32_t);
-        if (bytes <= free_b / 8 && cudaMalloc(&d_flags, bytes) == cudaSuccess) {
+        if (bytes <= free_b / 8 && edk::ws_alloc((void **)&d_flags, bytes, stream) == cudaSuccess) {
             plan.flags = d_flags;
             plan.flag_words = (uint32_t)words;
         }
@@ -759,20 +762,22 @@ ed_status basis_build_impl(int n_sites, int n_up, int spin_inversion, int n_elem
     if (count_only) {
         *count_only = dim;
         free_basis(b);
-        cudaFree(d_counts); cudaFree(d_offsets); cudaFree(d_tmp); cudaFree(d_binom);
+        edk::ws_free(d_counts, stream); edk::ws_free(d_offsets, stream); edk::ws_free(d_tmp, stream);
+        cudaFree(d_binom);
         return ED_OK;
     }
     if (dim >= (1ULL << 32)) {
         free_basis(b);
-        cudaFree(d_counts); cudaFree(d_flags); cudaFree(d_offsets); cudaFree(d_tmp); cudaFree(d_binom);
+        edk::ws_free(d_counts, stream); edk::ws_free(d_flags, stream); edk::ws_free(d_offsets, stream);
+        edk::ws_free(d_tmp, stream); cudaFree(d_binom);
         return ED_ERR_UNSUPPORTED;
     }
     b->dim = dim;
-    ED_B_TRY(cudaMalloc(&b->d_states, std::max<uint64_t>(dim, 1) * sizeof(uint64_t)));
-    ED_B_TRY(cudaMalloc(&b->d_norms, std::max<uint64_t>(dim, 1) * sizeof(uint16_t)));
+    ED_B_TRY(edk::ws_alloc((void **)&b->d_states, std::max<uint64_t>(dim, 1) * sizeof(uint64_t), stream));
+    ED_B_TRY(edk::ws_alloc((void **)&b->d_norms, std::max<uint64_t>(dim, 1) * sizeof(uint16_t), stream));
     ED_B_TRY(edk::launch_enum_write(plan, gv, d_offsets, b->d_states, b->d_norms, stream));
     if (n_sites <= 48) {
-        ED_B_TRY(cudaMalloc(&b->d_keys, std::max<uint64_t>(dim, 1) * sizeof(uint64_t)));
+        ED_B_TRY(edk::ws_alloc((void **)&b->d_keys, std::max<uint64_t>(dim, 1) * sizeof(uint64_t), stream));
         ED_B_TRY(edk::launch_pack_keys(b->d_states, b->d_norms, dim, b->d_keys, stream));
     }
 
@@ -792,7 +797,7 @@ ed_status basis_build_impl(int n_sites, int n_up, int spin_inversion, int n_elem
         ++mb;
     b->mbits = mb;
     b->tab_size = (uint64_t)n_exp << mb;
-    ED_B_TRY(cudaMalloc(&b->d_tab, (b->tab_size + 1) * sizeof(uint32_t)));
+    ED_B_TRY(edk::ws_alloc((void **)&b->d_tab, (b->tab_size + 1) * sizeof(uint32_t), stream));
     ED_B_TRY(edk::launch_prefix_table(b->index_view(), b->d_tab, stream));
     ED_B_TRY(cudaMalloc(&d_flag, 2 * sizeof(int)));
     ED_B_TRY(cudaMemsetAsync(d_flag, 0, 2 * sizeof(int), stream));
@@ -824,15 +829,15 @@ ed_status basis_build_impl(int n_sites, int n_up, int spin_inversion, int n_elem
         const uint64_t T = 1ULL << hb;
         uint32_t *d_hcount = nullptr;
         uint64_t *d_hoff = nullptr, *d_htmp = nullptr;
-        cudaError_t he = cudaMalloc(&d_hcount, T * sizeof(uint32_t));
+        cudaError_t he = edk::ws_alloc((void **)&d_hcount, T * sizeof(uint32_t), stream);
         if (he == cudaSuccess)
-            he = cudaMalloc(&d_hoff, (T + 1) * sizeof(uint64_t));
+            he = edk::ws_alloc((void **)&d_hoff, (T + 1) * sizeof(uint64_t), stream);
         if (he == cudaSuccess)
-            he = cudaMalloc(&d_htmp, edk::scan_tmp_words(T) * sizeof(uint64_t));
+            he = edk::ws_alloc((void **)&d_htmp, edk::scan_tmp_words(T) * sizeof(uint64_t), stream);
         if (he == cudaSuccess)
-            he = cudaMalloc(&b->d_htab, (T + 1) * sizeof(uint32_t));
+            he = edk::ws_alloc((void **)&b->d_htab, (T + 1) * sizeof(uint32_t), stream);
         if (he == cudaSuccess)
-            he = cudaMalloc(&b->d_hent, dim * (b->hwide ? 16 : 8));
+            he = edk::ws_alloc((void **)&b->d_hent, dim * (b->hwide ? 16 : 8), stream);
         if (he == cudaSuccess)
             he = cudaMemsetAsync(d_hcount, 0, T * sizeof(uint32_t), stream);
         if (he == cudaSuccess)
@@ -856,9 +861,9 @@ ed_status basis_build_impl(int n_sites, int n_up, int spin_inversion, int n_elem
             he = cudaMemcpyAsync(&hmax, d_hmax, sizeof(uint32_t), cudaMemcpyDeviceToHost, stream);
         if (he == cudaSuccess)
             he = cudaStreamSynchronize(stream);
-        cudaFree(d_hcount);
-        cudaFree(d_hoff);
-        cudaFree(d_htmp);
+        edk::ws_free(d_hcount, stream);
+        edk::ws_free(d_hoff, stream);
+        edk::ws_free(d_htmp, stream);
         ED_B_TRY(he);
         b->hash_max_bucket = hmax;
     }
@@ -868,10 +873,10 @@ ed_status basis_build_impl(int n_sites, int n_up, int spin_inversion, int n_elem
             ++k;
         b->probe_iters = k;
     }
-    cudaFree(d_counts);
-    cudaFree(d_flags);
-    cudaFree(d_offsets);
-    cudaFree(d_tmp);
+    edk::ws_free(d_counts, stream);
+    edk::ws_free(d_flags, stream);
+    edk::ws_free(d_offsets, stream);
+    edk::ws_free(d_tmp, stream);
     cudaFree(d_binom);
     cudaFree(d_flag);
 #undef ED_B_TRY

@@ -7,6 +7,11 @@
 
 namespace edk {
 
+// Library-owned, stream-ordered device memory (see ed_pool.cu): allocations
+// and frees are ordered on stream s; freed memory stays cached for later calls.
+cudaError_t ws_alloc(void **p, size_t bytes, cudaStream_t s);
+cudaError_t ws_free(void *p, cudaStream_t s);
+
 // Kernel launches issued by the library since it was loaded (diagnostics).
 void count_launch(unsigned n = 1);
 // Takes back n counted launches (kernels recorded into a graph by stream

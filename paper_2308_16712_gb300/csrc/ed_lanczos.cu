@@ -16,6 +16,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <type_traits>
 #include <vector>
 
 #include "ed_kernels.cuh"
@@ -88,13 +89,6 @@ __device__ double reduce_partials(const double2 *part, int nparts)
     return total;
 }
 
-// out = sum of the partials (root = 0) or its square root (root = 1); one block.
-__global__ void __launch_bounds__(kRedThreads) k_finalize(const double2 *part, int nparts, double *out, int root)
-{
-    const double t = reduce_partials(part, nparts);
-    if (threadIdx.x == 0)
-        *out = root ? sqrt(fmax(t, 0.0)) : t;
-}
 
 // ---- vector element access (real or complex, fp64 or fp32) -------------------
 template <bool kC> struct Vec;
@@ -131,34 +125,76 @@ template <> struct Vec<true> {
     }
 };
 
-// partial[b] = compensated sum over this block's slice of Re<a_i, b_i> (or |a_i|^2)
+// The block that finishes last: every block stores its partial (thread 0),
+// fences, and takes a ticket; the one that draws gridDim.x - 1 knows every
+// partial is visible.  Nothing waits, so no block can stall another.
+__device__ bool is_last_block(unsigned int *ticket)
+{
+    __shared__ bool last;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    return last;
+}
+
+// The sum of the block partials in block order (the same merge order as
+// reduce_partials), read through L2; valid in thread 0.
+__device__ double sum_partials_l2(const double2 *part, int nparts)
+{
+    KSum k{0.0, 0.0};
+    for (int i = threadIdx.x; i < nparts; i += blockDim.x) {
+        const double2 p = __ldcg(part + i);
+        k = ksum_merge(k, KSum{p.x, p.y});
+    }
+    k = block_ksum(k);
+    return k.s + k.c;
+}
+
+// partial[b] = compensated sum over this block's slice of Re<a_i, b_i>; with a
+// ticket, the last block also stores the total in *out and resets the ticket.
+// Four elements per iteration, loads first, for memory-level parallelism.
 template <bool kC, bool kF32>
 __global__ void __launch_bounds__(kRedThreads) k_dot_part(const typename Vec<kC>::D *a, const void *bv,
-                                                           uint64_t n, double2 *part)
+                                                           uint64_t n, double2 *part, unsigned int *ticket,
+                                                           double *out)
 {
     using VT = Vec<kC>;
+    using B = std::conditional_t<kF32, typename VT::F, typename VT::D>;
+    const B *bp = reinterpret_cast<const B *>(bv);
+    auto dotv = [](typename VT::D x, B y) {
+        if constexpr (kF32)
+            return VT::dotf(x, y);
+        else
+            return VT::dot(x, y);
+    };
     double s0 = 0.0, s1 = 0.0;
     const uint64_t per = (n + gridDim.x - 1) / gridDim.x;
     const uint64_t lo = min(n, blockIdx.x * per), hi = min(n, lo + per);
+    const uint64_t bs = blockDim.x;
     uint64_t i = lo + threadIdx.x;
-    for (; i + blockDim.x < hi; i += 2 * blockDim.x) {
-        if constexpr (kF32) {
-            s0 += VT::dotf(a[i], reinterpret_cast<const typename VT::F *>(bv)[i]);
-            s1 += VT::dotf(a[i + blockDim.x], reinterpret_cast<const typename VT::F *>(bv)[i + blockDim.x]);
-        } else {
-            s0 += VT::dot(a[i], reinterpret_cast<const typename VT::D *>(bv)[i]);
-            s1 += VT::dot(a[i + blockDim.x], reinterpret_cast<const typename VT::D *>(bv)[i + blockDim.x]);
-        }
+    for (; i + 3 * bs < hi; i += 4 * bs) {
+        const typename VT::D a0 = a[i], a1 = a[i + bs], a2 = a[i + 2 * bs], a3 = a[i + 3 * bs];
+        const B b0 = bp[i], b1 = bp[i + bs], b2 = bp[i + 2 * bs], b3 = bp[i + 3 * bs];
+        s0 += dotv(a0, b0);
+        s1 += dotv(a1, b1);
+        s0 += dotv(a2, b2);
+        s1 += dotv(a3, b3);
     }
-    if (i < hi) {
-        if constexpr (kF32)
-            s0 += VT::dotf(a[i], reinterpret_cast<const typename VT::F *>(bv)[i]);
-        else
-            s0 += VT::dot(a[i], reinterpret_cast<const typename VT::D *>(bv)[i]);
-    }
+    for (; i < hi; i += bs)
+        s0 += dotv(a[i], bp[i]);
     const KSum k = block_ksum(two_sum(s0, s1));
     if (threadIdx.x == 0)
         part[blockIdx.x] = make_double2(k.s, k.c);
+    if (ticket && is_last_block(ticket)) {
+        const double t = sum_partials_l2(part, gridDim.x);
+        if (threadIdx.x == 0) {
+            *out = t;
+            *ticket = 0;
+        }
+    }
 }
 
 template <bool kC>
@@ -180,41 +216,79 @@ __global__ void __launch_bounds__(kRedThreads) k_norm_part(const typename Vec<kC
         part[blockIdx.x] = make_double2(k.s, k.c);
 }
 
-// alpha_j from the dot partials; w = w_in - alpha v - beta_j vp; norm partials of w
+// w = w_in - alpha_j v - beta_j vp (alpha_j and beta_j already stored); norm
+// partials of w; with a ticket, the last block stores sqrt(|w|^2) in *beta_out.
 template <bool kC, bool kF32>
 __global__ void __launch_bounds__(kRedThreads) k_update(const void *w_in, typename Vec<kC>::D *w,
                                                          const typename Vec<kC>::D *v,
                                                          const typename Vec<kC>::D *vp, uint64_t n,
                                                          const double *alpha, const double *beta_j,
-                                                         double2 *norm_part)
+                                                         double2 *norm_part, unsigned int *ticket,
+                                                         double *beta_out)
 {
     using VT = Vec<kC>;
+    using D = typename VT::D;
+    using WI = std::conditional_t<kF32, typename VT::F, D>;
+    const WI *wp = reinterpret_cast<const WI *>(w_in);
+    auto upw = [](WI x) {
+        if constexpr (kF32)
+            return VT::up(x);
+        else
+            return x;
+    };
     const double a = *alpha;
     const double b = vp ? *beta_j : 0.0;
     double s0 = 0.0, s1 = 0.0;
     const uint64_t per = (n + gridDim.x - 1) / gridDim.x;
     const uint64_t lo = min(n, blockIdx.x * per), hi = min(n, lo + per);
-    int parity = 0;
-    for (uint64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
-        typename VT::D wi;
-        if constexpr (kF32)
-            wi = VT::up(reinterpret_cast<const typename VT::F *>(w_in)[i]);
-        else
-            wi = reinterpret_cast<const typename VT::D *>(w_in)[i];
-        const typename VT::D r = VT::axpby(wi, a, v[i], b, vp ? vp[i] : VT::zero());
+    const uint64_t bs = blockDim.x;
+    uint64_t i = lo + threadIdx.x;
+    for (; i + 3 * bs < hi; i += 4 * bs) {
+        D wv[4], vv[4], pv[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            wv[u] = upw(wp[i + u * bs]);
+            vv[u] = v[i + u * bs];
+            pv[u] = vp ? vp[i + u * bs] : VT::zero();
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const D r = VT::axpby(wv[u], a, vv[u], b, pv[u]);
+            w[i + u * bs] = r;
+            if (u & 1)
+                s1 += VT::norm2(r);
+            else
+                s0 += VT::norm2(r);
+        }
+    }
+    for (; i < hi; i += bs) {
+        const D r = VT::axpby(upw(wp[i]), a, v[i], b, vp ? vp[i] : VT::zero());
         w[i] = r;
-        if (parity)
-            s1 += VT::norm2(r);
-        else
-            s0 += VT::norm2(r);
-        parity ^= 1;
+        s0 += VT::norm2(r);
     }
     const KSum k = block_ksum(two_sum(s0, s1));
     if (threadIdx.x == 0)
         norm_part[blockIdx.x] = make_double2(k.s, k.c);
+    if (ticket && is_last_block(ticket)) {
+        const double t = sum_partials_l2(norm_part, gridDim.x);
+        if (threadIdx.x == 0) {
+            *beta_out = sqrt(fmax(t, 0.0));
+            *ticket = 0;
+        }
+    }
 }
 
-// beta = sqrt(sum of partials); v_out = w / beta (zero on breakdown); fp32 copy
+// beta_{j+1} = sqrt(sum of the norm partials) in one block (after the
+// reorthogonalisation has replaced w and its partials)
+__global__ void __launch_bounds__(kRedThreads) k_norm_final(const double2 *part, int nparts, double *beta)
+{
+    const double t = reduce_partials(part, nparts);
+    if (threadIdx.x == 0)
+        *beta = sqrt(fmax(t, 0.0));
+}
+
+// v_out = w / beta (zero on breakdown); fp32 copy; four elements per thread
+// per iteration
 template <bool kC>
 __global__ void __launch_bounds__(kRedThreads) k_normalize(const typename Vec<kC>::D *w,
                                                             typename Vec<kC>::D *v_out,
@@ -224,8 +298,21 @@ __global__ void __launch_bounds__(kRedThreads) k_normalize(const typename Vec<kC
     using VT = Vec<kC>;
     const double b = *beta;
     const double s = b > 0.0 ? 1.0 / b : 0.0;
-    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-         i += (uint64_t)gridDim.x * blockDim.x) {
+    const uint64_t G = (uint64_t)gridDim.x * blockDim.x;
+    uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    for (; i + 3 * G < n; i += 4 * G) {
+        typename VT::D r[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+            r[u] = VT::scale(w[i + u * G], s);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            v_out[i + u * G] = r[u];
+            if (x32)
+                x32[i + u * G] = VT::down(r[u]);
+        }
+    }
+    for (; i < n; i += G) {
         const typename VT::D r = VT::scale(w[i], s);
         v_out[i] = r;
         if (x32)
@@ -530,11 +617,6 @@ __global__ void k_tridiag_kth(const double *alpha, const double *beta, int m, co
         out[e] = 0.5 * (lo + hi);
 }
 
-template <typename T>
-cudaError_t dalloc(T **p, size_t count)
-{
-    return cudaMalloc((void **)p, std::max<size_t>(count, 1) * sizeof(T));
-}
 
 // CUDA event pairs around every matvec launch; summed after the final sync.
 struct MatvecTimer {
@@ -565,17 +647,20 @@ struct MatvecTimer {
     }
 };
 
+// Work arrays of one call, from the library's stream-ordered pool.
 struct Scratch {
+    cudaStream_t st;
     std::vector<void *> ptrs;
+    explicit Scratch(cudaStream_t s) : st(s) {}
     ~Scratch()
     {
         for (void *p : ptrs)
-            cudaFree(p);
+            ws_free(p, st);
     }
     template <typename T>
     cudaError_t get(T **p, size_t count)
     {
-        cudaError_t e = dalloc(p, count);
+        cudaError_t e = ws_alloc((void **)p, std::max<size_t>(count, 1) * sizeof(T), st);
         if (e == cudaSuccess)
             ptrs.push_back((void *)*p);
         return e;
@@ -609,7 +694,7 @@ ed_status run_lanczos(const ed_operator *op, const ed_basis *b, const void *x0, 
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const int nparts = std::max(1, std::min<int>(sms * 4, (int)((n + kRedThreads - 1) / kRedThreads)));
+    const int nparts = std::max(1, std::min<int>(sms * 8, (int)((n + kRedThreads - 1) / kRedThreads)));
     const int vgrid = std::max(1, std::min<int>(sms * 8, (int)((n + kRedThreads - 1) / kRedThreads)));
 
     // store the Krylov basis if it fits in half of the free memory
@@ -625,7 +710,7 @@ ed_status run_lanczos(const ed_operator *op, const ed_basis *b, const void *x0, 
     if (reorth && !store)
         return ED_ERR_UNSUPPORTED;
 
-    Scratch S;
+    Scratch S(st);
     D *V = nullptr, *w = nullptr, *ring[2] = {nullptr, nullptr}, *psi = nullptr;
     F *x32 = nullptr, *w32 = nullptr;
     double *alpha = nullptr, *beta = nullptr, *y = nullptr, *work = nullptr, *scal = nullptr;
@@ -654,6 +739,9 @@ ed_status run_lanczos(const ed_operator *op, const ed_basis *b, const void *x0, 
     ED_L_TRY(S.get(&part_a, nparts));
     ED_L_TRY(S.get(&part_b, nparts));
     ED_L_TRY(S.get(&part_c, nparts));
+    unsigned int *tickets = nullptr;  // last-block tickets of k_dot_part and k_update
+    ED_L_TRY(S.get(&tickets, 2));
+    ED_L_TRY(cudaMemsetAsync(tickets, 0, 2 * sizeof(unsigned int), st));
     Part4 *rpart = nullptr;
     double2 *rcoef = nullptr;
     double *d_eigs = nullptr;
@@ -696,17 +784,15 @@ ed_status run_lanczos(const ed_operator *op, const ed_basis *b, const void *x0, 
                 e = timed_matvec(x32, w32, dt32);
                 if (e != cudaSuccess)
                     return e;
-                k_dot_part<kC, true><<<nparts, kRedThreads, 0, st>>>(v, w32, n, part_a); count_launch();
-                k_finalize<<<1, kRedThreads, 0, st>>>(part_a, nparts, alpha + j, 0); count_launch();
-                k_update<kC, true><<<nparts, kRedThreads, 0, st>>>(w32, w, v, vp, n, alpha + j, beta + j,
-                                                                    part_b); count_launch();
+                k_dot_part<kC, true><<<nparts, kRedThreads, 0, st>>>(v, w32, n, part_a, tickets, alpha + j); count_launch();
+                k_update<kC, true><<<nparts, kRedThreads, 0, st>>>(w32, w, v, vp, n, alpha + j, beta + j, part_b,
+                                                                    tickets + 1, beta + j + 1); count_launch();
             } else {
                 if ((e = H64(v, w)) != cudaSuccess)
                     return e;
-                k_dot_part<kC, false><<<nparts, kRedThreads, 0, st>>>(v, w, n, part_a); count_launch();
-                k_finalize<<<1, kRedThreads, 0, st>>>(part_a, nparts, alpha + j, 0); count_launch();
-                k_update<kC, false><<<nparts, kRedThreads, 0, st>>>(w, w, v, vp, n, alpha + j, beta + j,
-                                                                     part_b); count_launch();
+                k_dot_part<kC, false><<<nparts, kRedThreads, 0, st>>>(v, w, n, part_a, tickets, alpha + j); count_launch();
+                k_update<kC, false><<<nparts, kRedThreads, 0, st>>>(w, w, v, vp, n, alpha + j, beta + j, part_b,
+                                                                     tickets + 1, beta + j + 1); count_launch();
             }
             if (reorth && Vs) {  // against v_0 .. v_j, twice
                 for (int pass = 0; pass < 2; ++pass) {
@@ -714,11 +800,10 @@ ed_status run_lanczos(const ed_operator *op, const ed_basis *b, const void *x0, 
                     k_reorth_coef<<<j + 1, kRedThreads, 0, st>>>(rpart, nparts, rcoef); count_launch();
                     k_reorth_update<kC><<<nparts, kRedThreads, 0, st>>>(Vs, w, n, j + 1, rcoef, part_b); count_launch();
                 }
+                k_norm_final<<<1, kRedThreads, 0, st>>>(part_b, nparts, beta + j + 1); count_launch();
             }
             D *vn = Vs ? Vs + (uint64_t)(j + 1) * n : (vp ? vp : ring[1]);
-            k_finalize<<<1, kRedThreads, 0, st>>>(part_b, nparts, beta + j + 1, 1); count_launch();
-            k_normalize<kC><<<vgrid, kRedThreads, 0, st>>>(w, vn, use_f32 ? x32 : nullptr, n,
-                                                           beta + j + 1); count_launch();
+            k_normalize<kC><<<vgrid, kRedThreads, 0, st>>>(w, vn, use_f32 ? x32 : nullptr, n, beta + j + 1); count_launch();
             vp = v;
             v = vn;
         }
@@ -757,7 +842,7 @@ ed_status run_lanczos(const ed_operator *op, const ed_basis *b, const void *x0, 
     }
     // fp64 Rayleigh quotient and residual of the final vector u
     ED_L_TRY(H64(u, w));
-    k_dot_part<kC, false><<<nparts, kRedThreads, 0, st>>>(u, w, n, part_a); count_launch();
+    k_dot_part<kC, false><<<nparts, kRedThreads, 0, st>>>(u, w, n, part_a, nullptr, nullptr); count_launch();
     k_norm_part<kC><<<nparts, kRedThreads, 0, st>>>(u, n, part_b); count_launch();
     k_residual<kC><<<nparts, kRedThreads, 0, st>>>(w, u, n, part_a, part_b, nparts, scal + 2, part_c); count_launch();
     k_finish_residual<<<1, kRedThreads, 0, st>>>(part_c, part_b, nparts, scal + 3); count_launch();

@@ -364,10 +364,12 @@ __global__ void k_seg_tridiag(const double *alpha, const double *beta, int strid
 
 // device buffers, graphs and the capture stream, released on every exit path
 struct Owned {
+    cudaStream_t st;  // the call's stream: work arrays are allocated and freed in its order
     std::vector<void *> ptrs;
     std::vector<cudaGraphExec_t> execs;
     std::vector<cudaGraph_t> graphs;
     cudaStream_t cap = nullptr;
+    explicit Owned(cudaStream_t s) : st(s) {}
     ~Owned()
     {
         for (auto g : execs)
@@ -375,14 +377,14 @@ struct Owned {
         for (auto g : graphs)
             cudaGraphDestroy(g);
         for (void *p : ptrs)
-            cudaFree(p);
+            ws_free(p, st);
         if (cap)
             cudaStreamDestroy(cap);
     }
     template <typename T>
     cudaError_t get(T **p, size_t n)
     {
-        const cudaError_t e = cudaMalloc((void **)p, std::max<size_t>(n, 1) * sizeof(T));
+        const cudaError_t e = ws_alloc((void **)p, std::max<size_t>(n, 1) * sizeof(T), st);
         if (e == cudaSuccess)
             ptrs.push_back((void *)*p);
         return e;
@@ -412,7 +414,7 @@ ed_status run_multi(const ed_operator *op, const ed_sector *sectors, int ns, int
 {
     using D = typename El<C>::D;
     using F = typename El<C>::F;
-    Owned O;
+    Owned O(st);
     std::vector<uint64_t> off(ns + 1, 0);
     for (int k = 0; k < ns; ++k)
         off[k + 1] = off[k] + sectors[k].basis->dim;
@@ -442,10 +444,10 @@ ed_status run_multi(const ed_operator *op, const ed_sector *sectors, int ns, int
         LM_TRY(O.get(&p_hi, nblk));
         LM_TRY(O.get(&p_bs, nblk));
         LM_TRY(O.get(&p_sb, ns + 1));
-        LM_TRY(cudaMemcpy(p_lo, blk_lo.data(), nblk * sizeof(uint64_t), cudaMemcpyHostToDevice));
-        LM_TRY(cudaMemcpy(p_hi, blk_hi.data(), nblk * sizeof(uint64_t), cudaMemcpyHostToDevice));
-        LM_TRY(cudaMemcpy(p_bs, blk_sec.data(), nblk * sizeof(int), cudaMemcpyHostToDevice));
-        LM_TRY(cudaMemcpy(p_sb, sec_blk.data(), (ns + 1) * sizeof(int), cudaMemcpyHostToDevice));
+        LM_TRY(cudaMemcpyAsync(p_lo, blk_lo.data(), nblk * sizeof(uint64_t), cudaMemcpyHostToDevice, st));
+        LM_TRY(cudaMemcpyAsync(p_hi, blk_hi.data(), nblk * sizeof(uint64_t), cudaMemcpyHostToDevice, st));
+        LM_TRY(cudaMemcpyAsync(p_bs, blk_sec.data(), nblk * sizeof(int), cudaMemcpyHostToDevice, st));
+        LM_TRY(cudaMemcpyAsync(p_sb, sec_blk.data(), (ns + 1) * sizeof(int), cudaMemcpyHostToDevice, st));
         sg.blk_lo = p_lo;
         sg.blk_hi = p_hi;
         sg.blk_sec = p_bs;

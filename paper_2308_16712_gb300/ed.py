@@ -49,6 +49,7 @@ class LanczosInfo(ctypes.Structure):
 
 _SIGS = {
     "ed_status_string": (ctypes.c_char_p, [_i32]),
+    "ed_release_cached_memory": (_i32, []),
     "ed_stream_status": (_i32, [_P]),
     "ed_basis_build": (_i32, [_i32, _i32, _i32, _i32, _P, _P, _P, ctypes.POINTER(_P)]),
     "ed_basis_size": (_i32, [_P, ctypes.POINTER(_u64)]),
@@ -147,6 +148,11 @@ class Operator:
         if getattr(self, "handle", None):
             _lib.ed_operator_destroy(self.handle)
             self.handle = None
+
+
+def release_cached_memory() -> None:
+    """Return the device memory the library keeps cached for later calls."""
+    _check(_lib.ed_release_cached_memory(), "ed_release_cached_memory")
 
 
 def status_string(status: int) -> str:

@@ -172,3 +172,18 @@ def test_eigs_low_spectrum_with_reorthogonalisation():
     with pytest.raises(ed.EDError):
         ed.lanczos_eigs(S["O"], S["B"], x0, 20, 2,
                         ed.ED_LANCZOS_F64 | ed.ED_LANCZOS_REORTH | ed.ED_LANCZOS_RECOMPUTE)
+
+
+def test_cached_workspace_memory_is_reused_and_released():
+    """Work arrays come from the library's pool: a second identical solve gives
+    the same bits, and the cached memory can be handed back."""
+    torch, ed = gpu()
+    w = ei.workload("ring16")
+    S = build_pair(16, 8, +1, w["perms"], w["chars"], w["op"], with_oracle=False)
+    x0 = to_torch(ei.x_by_index(0, S["dim"])[:, 0], np.float64)
+    r1 = ed.lanczos(S["O"], S["B"], x0, 40, ed.ED_LANCZOS_F32_MATVEC)
+    r2 = ed.lanczos(S["O"], S["B"], x0, 40, ed.ED_LANCZOS_F32_MATVEC)
+    assert r1.e0 == r2.e0 and r1.residual == r2.residual
+    ed.release_cached_memory()
+    r3 = ed.lanczos(S["O"], S["B"], x0, 40, ed.ED_LANCZOS_F32_MATVEC)
+    assert r3.e0 == r1.e0
