@@ -48,7 +48,7 @@ INT_LANES_PER_SM = 64
 # capture of it (--set full, which starts every replay with a cold L2); keyed by
 # workload.  Retake the capture and update the figure whenever the kernel
 # changes (the roofline reports null traffic for workloads not listed).
-KERNEL_DRAM_BYTES = {}
+KERNEL_DRAM_BYTES = {"ring32": 554_140_160 + 112_350_720}
 
 
 def peaks():
