@@ -114,7 +114,9 @@ ed_status ed_stream_status(void *stream);
  *   stream         cudaStream_t for the enumeration kernels
  *   out            receives the new handle
  *
- * The call synchronises `stream` once (to size the output).  Errors:
+ * The call synchronises `stream` (to size its arrays) and returns with the
+ * basis ready; its large arrays come from the library's memory pool (see
+ * ed_release_cached_memory).  Errors:
  * ED_ERR_INVALID_ARG, ED_ERR_NOT_A_GROUP, ED_ERR_BAD_CHARACTER, ED_ERR_OOM,
  * ED_ERR_CUDA, ED_ERR_INTERNAL.
  */
@@ -307,8 +309,9 @@ typedef struct {
  * from stored Krylov vectors when they fit in device memory, else by a second,
  * bit-identical pass of the recurrence.  It is then refined in fp64: a few
  * fp64 Lanczos steps started from it, whose lowest Ritz value is returned
- * together with its residual.  Allocates its work vectors; synchronises
- * `stream` before returning.
+ * together with its residual.  Takes its work vectors from the library's
+ * memory pool (see ed_release_cached_memory); synchronises `stream` before
+ * returning.
  * Errors: ED_ERR_INVALID_ARG, ED_ERR_SYMMETRY_MISMATCH, ED_ERR_UNSUPPORTED
  * (ED_LANCZOS_PUSH not applicable), ED_ERR_OOM, ED_ERR_CUDA.
  */
@@ -372,9 +375,10 @@ ed_status ed_lanczos_eigs(const ed_operator *op, const ed_basis *basis, const vo
  * memory (in the fp32-matvec mode as the fp32 copies the products consumed:
  * that Ritz vector only starts the fp64 refinement), else the Ritz vectors
  * come from a second, bit-identical pass.  Per sector the energy is the fp64
- * Rayleigh quotient of its final vector, as ed_lanczos returns.  Allocates
- * its work vectors (five fp64 vectors of the summed dimension, two fp32 ones
- * in the fp32-matvec mode, and the kept Lanczos vectors); synchronises
+ * Rayleigh quotient of its final vector, as ed_lanczos returns.  Takes its
+ * work vectors from the library's memory pool (five fp64 vectors of the
+ * summed dimension, two fp32 ones in the fp32-matvec mode, and the kept
+ * Lanczos vectors); synchronises
  * `stream` before returning.  Not to be called while `stream` is being
  * captured.  Errors: ED_ERR_INVALID_ARG, ED_ERR_SYMMETRY_MISMATCH,
  * ED_ERR_UNSUPPORTED (a basis without the hash index), ED_ERR_OOM, ED_ERR_CUDA.
