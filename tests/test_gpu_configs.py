@@ -145,6 +145,21 @@ def test_xxz28_all_sectors():
         assert torch.equal(y, y1)
     del items
     torch.cuda.empty_cache()
+    # one vector in single precision: per-sector term-parallel launches inside
+    # the batched call (every sector fills the GPU), the same bits as ed_matvec
+    items = []
+    for s in sectors[::5]:
+        B = ed.basis_build(28, s["n_up"], s["spin_inversion"], s["perms"], s["chars"])
+        st, _ = ed.basis_states(B)
+        x = ei.x_by_state_torch(6, st, 1, True, dtype=torch.complex64).reshape(-1).contiguous()
+        items.append((B, x, torch.empty_like(x)))
+    ed.matvec_multi(O, items, 1)
+    for B, x, y in items:
+        y1 = torch.empty_like(x)
+        ed.matvec(O, B, x, y1, 1)
+        assert torch.equal(y, y1)
+    del items
+    torch.cuda.empty_cache()
     for k in (0, 33, 77, 139):  # Sz=0 z=+1 k=0; a complex Sz=0 sector; Sz=1 and Sz=3 sectors
         s = sectors[k]
         B = ed.basis_build(28, s["n_up"], s["spin_inversion"], s["perms"], s["chars"])
