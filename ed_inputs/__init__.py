@@ -247,7 +247,7 @@ def j1j2_torus(lx: int, ly: int, j1: float = 1.0, j2: float = 0.5) -> dict:
 
 
 # ----------------------------------------------------------------------------
-# the named workloads (sizes as stated by the benchmark configurations)
+# the named workloads, at their full sizes
 # ----------------------------------------------------------------------------
 def workload(name: str) -> dict:
     """Problem definitions: n_sites, n_up, spin inversion, group, operator."""

@@ -1,4 +1,4 @@
-"""The benchmark configurations other than the timed one, at their full sizes,
+"""The workloads other than the timed one, at their full sizes,
 as parity cases: basis dimensions against the character formula (and, for the
 N=40 ring, against the paper's Table 2), sampled representatives checked one by
 one by the oracle, and sampled rows of y = Hx (x keyed by the state) against the
