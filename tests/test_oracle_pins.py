@@ -261,6 +261,30 @@ def test_oracle_lanczos_matches_dense():
     assert abs(e0 - np.linalg.eigvalsh(M)[0]) < 1e-10
 
 
+def test_oracle_reorthogonalised_lanczos_spans_the_spectrum():
+    """With full reorthogonalisation and as many steps as the Krylov space has
+    dimensions, the tridiagonal matrix carries every distinct eigenvalue the
+    start vector touches: for a 29-state sector with one degenerate pair, the
+    28 distinct eigenvalues of the dense matrix; the plain recurrence after
+    many more steps repeats converged values (ghosts) instead."""
+    from scipy.linalg import eigh_tridiagonal
+    G, H, st, nm = ring_sector(12, 6, 6, -1, +1)
+    M = oracle.dense_matrix(G, H, st, nm).real
+    ev = np.linalg.eigvalsh(M)
+    distinct = [ev[0]]
+    for e in ev[1:]:
+        if e - distinct[-1] > 1e-8:
+            distinct.append(e)
+    assert len(st) == 29 and len(distinct) == 28
+    x0 = ei.x_by_index(1, len(st))[:, 0]
+    a, b, e0 = oracle.lanczos(lambda v: M @ v, x0, 28, reorth=True)
+    ritz = eigh_tridiagonal(a, b, eigvals_only=True)
+    assert np.max(np.abs(ritz - np.array(distinct))) < 1e-10
+    a, b, _ = oracle.lanczos(lambda v: M @ v, x0, 80)
+    plain = eigh_tridiagonal(a, b, eigvals_only=True)
+    assert abs(plain[0] - ev[0]) < 1e-10 and len(plain) > 28  # extra copies of converged values
+
+
 # ----------------------------------------------------------------------------
 # rows evaluated from states alone (used at sizes where no basis is enumerated)
 # ----------------------------------------------------------------------------
