@@ -128,8 +128,9 @@ ed_status ed_basis_build(int n_sites, int n_up, int spin_inversion, int n_elems,
  * ed_basis_count -- the sector dimension only: the count pass of the
  * enumeration and its scan, without keeping the basis (Table 2 of the paper
  * lists such dimensions, up to 48 spins, which no single GPU could store).
- * Arguments as ed_basis_build; the dimension may exceed 2^32.  Allocates and
- * frees its work arrays; synchronises `stream`.
+ * Arguments as ed_basis_build; the dimension may exceed 2^32.  Takes its work
+ * arrays from the library's memory pool and returns them; synchronises
+ * `stream`.
  */
 ed_status ed_basis_count(int n_sites, int n_up, int spin_inversion, int n_elems,
                          const int32_t *perms, const double *chars, void *stream, uint64_t *dim);
