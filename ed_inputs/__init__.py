@@ -259,6 +259,10 @@ def workload(name: str) -> dict:
         p, c = ring_group(32, 0, parity=+1)
         return dict(name=name, n_sites=32, n_up=16, spin_inversion=+1, perms=p, chars=c,
                     op=heisenberg_ring(32), complex_=False, lanczos_steps=100)
+    if name == "ring36":
+        p, c = ring_group(36, 0, parity=+1)
+        return dict(name=name, n_sites=36, n_up=18, spin_inversion=+1, perms=p, chars=c,
+                    op=heisenberg_ring(36), complex_=False, lanczos_steps=150)
     if name == "ring40":
         p, c = ring_group(40, 0, parity=+1)
         return dict(name=name, n_sites=40, n_up=20, spin_inversion=+1, perms=p, chars=c,

@@ -238,6 +238,7 @@ bool factorize(int n, int ne, const int32_t *perms, Factorization &F)
 
 bool g_force_generic = false;
 bool g_force_prefix = false;
+bool g_force_all_rotations = false;  // test hook: factored search over every rotation
 
 void free_basis(ed_basis *b)
 {
@@ -530,6 +531,7 @@ edk::GroupView ed_basis::group_view() const
     g.rot_L = rot_L;
     g.rot_d = rot_d;
     g.n_cos = n_cos;
+    g.prune = g.fact && rot_d == 1 && !g_force_all_rotations;
     g.cos_kind = d_cos_kind;
     g.cos_masks32 = d_cos_masks32;
     g.cos_masks64 = d_cos_masks64;
@@ -1073,6 +1075,11 @@ int edx_count_nnz(const ed_operator *op, const ed_basis *b, unsigned long long *
 // for every group even when the factored form is available (both paths are
 // then exercised by the same parity tests).  Affects later launches.
 void edx_force_generic(int on) { g_force_generic = on != 0; }
+
+// Test hook: 1 = the factored search visits every rotation of every coset
+// image (no pruning to the tops of the longest runs), so that the pruned and
+// the exhaustive factored search run through the same parity tests.
+void edx_force_all_rotations(int on) { g_force_all_rotations = on != 0; }
 
 // Host-only test hook: the factored form the library finds for a permutation
 // group (returns the number of cosets, 0 if there is none); kinds_out gets one

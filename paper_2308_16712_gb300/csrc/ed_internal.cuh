@@ -99,6 +99,10 @@ struct GroupView {
     // Expanded factored index: c * rot_L + b (+ n_perm if flipped).
     int fact;                 // 1 if the factored form is available
     int rot_L, rot_d, n_cos;
+    int prune;                // 1: rot_d == 1; the kernels then use the pruned search
+                              // (rep_search_rot1) for 64-bit words and for tracked
+                              // minimisers; 32-bit words without tracking keep the
+                              // exhaustive funnel-shift loop, which measured faster
     const uint8_t *cos_kind;  // n_cos: 0 identity, 1 bit reversal, 2 Benes network
     const uint32_t *cos_masks32;  // n_cos x kMaskStride
     const uint64_t *cos_masks64;  // n_cos x kMaskStride
@@ -365,6 +369,134 @@ __device__ __forceinline__ void rep_search_fact(W s, const uint8_t *kinds, const
         }
         return false;
     });
+    best = bst;
+    gbest = gb;
+}
+
+// ---------------------------------------------------------------------------
+// Pruned search for a rotation step of one site (every translation of a ring).
+//
+// Compared as unsigned integers, a rotation of an n-bit word h is the smaller
+// the longer the run of zeros it starts with (at bit n-1).  The minimum over
+// all n rotations therefore brings the top of one of the LONGEST zero runs of
+// h to bit n-1, and only those rotations need to be formed and compared.  With
+// spin inversion the complement of a rotation starts with the complemented
+// bits, so a longest run of ones qualifies as well: the candidates are the tops
+// of the longest runs of equal bits (a zero run gives the plain rotation, a
+// one run the complemented one).  The tops are found bit-parallel: with
+// X_k = {p : bits p, p-1, ..., p-k+1 of h are equal} (zeros only, without
+// spin inversion), X_{k+1} = X_2 & rotl(X_k, 1); the last nonempty X_k holds
+// exactly the tops of the longest runs.  The bit reversal maps the runs of h to
+// mirrored runs of the same lengths, so the candidates of the reversal image
+// are the mirrored bottoms of those runs (the tops rotated down by length - 1),
+// with no second pass.  The minimum equals the brute-force minimum over the
+// rotations of every coset image; the minimiser may differ only by an element
+// of the stabiliser of the minimum.
+// ---------------------------------------------------------------------------
+// rotation of the n-bit word x up by b (0 <= b < n): bit p goes to p + b mod n
+template <typename W>
+__device__ __forceinline__ W rotl_n(W x, int b, int n, W full)
+{
+    if constexpr (sizeof(W) == 4) {
+        if (n == 32)
+            return __funnelshift_l(x, x, b);
+        return ((x << b) | (x >> (n - b))) & full;
+    } else {
+        if (n == 64)
+            return (x << b) | (x >> ((64 - b) & 63));
+        return ((x << b) | (x >> (n - b))) & full;
+    }
+}
+
+// Tops of the longest runs of equal bits of h (of zeros only when !flip), and
+// the length of those runs.  A word without such a run structure (all bits
+// equal, or no zero at all without spin inversion: every rotation is the same
+// word) gives the single candidate top n - 1 (rotation 0) and length n.
+template <typename W>
+__device__ __forceinline__ W run_tops(W h, int n, int flip, W full, int &len)
+{
+    const W r1 = rotl_n(h, 1, n, full);  // bit p of r1 = bit p-1 of h
+    const W x2 = flip ? (W)(~(h ^ r1) & full) : (W)(~(h | r1) & full);
+    W cur = flip ? full : (W)(~h & full);
+    if (x2 == full || cur == 0) {
+        len = n;
+        return W(1) << (n - 1);
+    }
+    // x2 != full: X_k is empty once k - 1 >= n, so the loop ends within n steps
+    len = 1;
+    while (true) {
+        const W nxt = x2 & rotl_n(cur, 1, n, full);
+        if (nxt == 0)
+            break;
+        cur = nxt;
+        ++len;
+    }
+    return cur;
+}
+
+template <typename W>
+__device__ __forceinline__ int lowest_set(W v)
+{
+    if constexpr (sizeof(W) == 4)
+        return __ffs((int)v) - 1;
+    else
+        return __ffsll((long long)v) - 1;
+}
+
+// Candidates of one coset image h (coset c): the rotations that bring a top in
+// `tops` to bit n - 1, complemented where the run there is a run of ones.
+template <typename W, bool kTrack>
+__device__ __forceinline__ void rot1_candidates(W h, W tops, int c, int n, int n_perm, int flip, W full,
+                                                W &best, int &gbest)
+{
+    while (tops) {
+        const int p = lowest_set(tops);
+        tops &= tops - 1;
+        const int b = n - 1 - p;
+        W q = rotl_n(h, b, n, full);
+        int gi = c * n + b;
+        if (flip && ((h >> p) & 1)) {
+            q ^= full;
+            gi += n_perm;
+        }
+        if (kTrack) {
+            if (q < best) {
+                best = q;
+                gbest = gi;
+            }
+        } else {
+            best = min(best, q);
+        }
+    }
+}
+
+// Minimum over the factored group when its rotations step by one site (rot_L
+// = n); gbest is a factored index of a minimiser.  `flip` may differ per lane.
+template <typename W, bool kTrack>
+__device__ __forceinline__ void rep_search_rot1(W s, const uint8_t *kinds, const W *masks, int n_cos, int n,
+                                                int n_perm, int flip, W full, W &best, int &gbest)
+{
+    W bst = ~W(0);
+    int gb = 0;
+    int len0;
+    const W t0 = run_tops(s, n, flip, full, len0);
+    for (int c = 0; c < n_cos; ++c) {
+        const int kind = kinds[c];
+        W h, tops;
+        if (kind == 0) {
+            h = s;
+            tops = t0;
+        } else if (kind == 1) {
+            h = reverse_bits(s, n);
+            const int dn = len0 - 1;  // bottoms = tops rotated down by len - 1
+            tops = reverse_bits(rotl_n(t0, dn ? n - dn : 0, n, full), n);
+        } else {
+            h = benes_apply(s, masks + c * kMaskStride);
+            int l;
+            tops = run_tops(h, n, flip, full, l);
+        }
+        rot1_candidates<W, kTrack>(h, tops, c, n, n_perm, flip, full, bst, gb);
+    }
     best = bst;
     gbest = gb;
 }

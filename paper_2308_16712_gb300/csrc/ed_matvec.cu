@@ -133,7 +133,10 @@ __global__ void __launch_bounds__(256) k_count_nnz(const OpView op, const GroupV
                         const W s = r ^ (W((fl >> 1) & 1) << i) ^ (W(fl & 1) << j);
                         W best;
                         int gb;
-                        if (kFact)
+                        if (kFact && g.prune && sizeof(W) == 8)
+                            rep_search_rot1<W, false>(s, sm_kind, sm_masks, g.n_cos, n, g.n_perm, g.flip, full,
+                                                      best, gb);
+                        else if (kFact)
                             rep_search_fact<W, false>(s, sm_kind, sm_masks, g.n_cos, g.rot_L, g.rot_d, n, g.n_perm,
                                                       g.flip, full, best, gb);
                         else

@@ -70,6 +70,10 @@ template <typename W, bool kTrack, bool kFact>
 __device__ __forceinline__ void search_lane(W s, const uint8_t *kinds, const W *masks, const GroupView &g,
                                             int lane_flip, W full, W &best, int &gbest)
 {
+    if (kFact && g.prune && (sizeof(W) == 8 || kTrack)) {
+        rep_search_rot1<W, kTrack>(s, kinds, masks, g.n_cos, g.n_sites, g.n_perm, lane_flip, full, best, gbest);
+        return;
+    }
     if (kFact && !kTrack) {
         best = rep_min_fact<W>(s, kinds, masks, g.n_cos, g.rot_L, g.rot_d, g.n_sites, lane_flip, full);
         gbest = 0;

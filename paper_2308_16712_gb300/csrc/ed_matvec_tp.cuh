@@ -356,7 +356,10 @@ __global__ void __launch_bounds__(kTpThreads, 8) k_matvec_tp(const __grid_consta
             // representative search (every lane; idle lanes search s = 0)
             W best;
             int gbest = 0;
-            if (kFact) {
+            if (kFact && a.g.prune && (sizeof(W) == 8 || kTrack)) {
+                rep_search_rot1<W, kTrack>(s, sm_kind, sm_masks, a.g.n_cos, n, a.g.n_perm, flip, full, best,
+                                           gbest);
+            } else if (kFact) {
                 if (kTrack)
                     rep_search_fact<W, true>(s, sm_kind, sm_masks, a.g.n_cos, a.g.rot_L, a.g.rot_d, n,
                                              a.g.n_perm, flip, full, best, gbest);

@@ -71,6 +71,7 @@ _SIGS = {
     "ed_basis_count_noalloc": (_i32, [_i32, _i32, _i32, _i32, _P, _P, _P, ctypes.POINTER(_u64)]),
     "edx_launch_count": (ctypes.c_ulonglong, []),
     "edx_force_generic": (None, [_i32]),
+    "edx_force_all_rotations": (None, [_i32]),
     "edx_count_nnz": (_i32, [_P, _P, ctypes.POINTER(ctypes.c_ulonglong)]),
     "edx_force_prefix_search": (None, [_i32]),
     "edx_kernel_policy": (None, [_i32]),
@@ -273,6 +274,12 @@ def force_generic(on: bool) -> None:
     """Testing aid: use the generic Benes group search even where the factored
     (rotation x coset) search applies.  Affects later launches and builds."""
     _lib.edx_force_generic(1 if on else 0)
+
+
+def force_all_rotations(on: bool) -> None:
+    """Test hook: the factored group search visits every rotation (no pruning
+    to the tops of the longest runs of equal bits)."""
+    _lib.edx_force_all_rotations(1 if on else 0)
 
 
 def count_nnz(op: Operator, basis: Basis) -> int:

@@ -35,6 +35,25 @@ def dm_ring(n, d):
     return op
 
 
+def affine_group(n, a, sign=1.0):
+    """Site maps i -> u*i + b mod n, u in {1, a} (a*a = 1 mod n): translations
+    times one non-reflection automorphism of the ring, so that the factored
+    search has a coset applied by a Benes network; chi = sign on the second
+    coset (momentum 0)."""
+    perms, chars = [], []
+    for u in (1, a):
+        for b in range(n):
+            perms.append([(u * i + b) % n for i in range(n)])
+            chars.append([1.0 if u == 1 else sign, 0.0])
+    return np.asarray(perms, np.int32), np.asarray(chars)
+
+
+def affine_heisenberg(n, a):
+    """Heisenberg bonds at distances 1 and a (the affine map exchanges them)."""
+    bonds = [(i, (i + 1) % n) for i in range(n)] + [(i, (i + a) % n) for i in range(n)]
+    return ei.make_operator(bonds, [1.0] * len(bonds), ei.heisenberg_local())
+
+
 SECTORS = [
     # name, n, n_up, z, group builder, operator
     ("ring16_k0_p+_z+", 16, 8, +1, lambda: ei.ring_group(16, 0, +1), lambda: ei.heisenberg_ring(16)),
@@ -55,6 +74,10 @@ SECTORS = [
     ("ring8_empty", 8, 4, -1, lambda: ei.ring_group(8, 4, -1), lambda: ei.heisenberg_ring(8)),
     ("ring10_noU1_xx_z-", 10, -1, -1, lambda: ei.ring_group(10, 0, +1), lambda: xx_ring(10)),
     ("ring11_dm_k2", 11, 5, 0, lambda: ei.ring_group(11, 2), lambda: dm_ring(11, 0.3)),
+    ("ring32_nup4_k3", 32, 4, 0, lambda: ei.ring_group(32, 3), lambda: ei.heisenberg_ring(32)),
+    ("ring33_nup3_k0_p-", 33, 3, 0, lambda: ei.ring_group(33, 0, -1), lambda: ei.xxz_ring(33, 1.0, 1.5)),
+    ("ring64_nup2_k0_p+", 64, 2, 0, lambda: ei.ring_group(64, 0, +1), lambda: ei.heisenberg_ring(64)),
+    ("affine16_a7_z+", 16, 8, +1, lambda: affine_group(16, 7, -1.0), lambda: affine_heisenberg(16, 7)),
 ]
 
 
@@ -64,21 +87,26 @@ def make(case, with_oracle=True):
     return build_pair(n, n_up, z, p, c, opf(), with_oracle)
 
 
-@pytest.fixture(params=["factored", "generic", "prefix", "rowwise", "term_parallel"], autouse=True)
+@pytest.fixture(params=["factored", "all_rotations", "generic", "prefix", "rowwise", "term_parallel"],
+                autouse=True)
 def search_mode(request):
-    """Run every parity test five times: factored (rotation x coset) group
-    search with the hash index; generic Benes search over every element with
-    the hash index; factored search with the prefix-table binary search (the
-    row-per-lane kernel); factored search and hash index with the row-per-lane
-    kernel forced; and with the term-parallel kernel forced in both precisions
-    (it otherwise serves single vectors of exchange-only operators in single
-    precision only)."""
+    """Run every parity test six times: factored (rotation x coset) group
+    search with the hash index, pruned to the tops of the longest runs where
+    the rotations step by one site; the same search visiting every rotation;
+    generic Benes search over every element with the hash index; factored
+    search with the prefix-table binary search (the row-per-lane kernel);
+    factored search and hash index with the row-per-lane kernel forced; and
+    with the term-parallel kernel forced in both precisions (it otherwise
+    serves single vectors of exchange-only operators in single precision
+    only)."""
     torch, ed = gpu()
     ed.force_generic(request.param == "generic")
+    ed.force_all_rotations(request.param == "all_rotations")
     ed.force_prefix_search(request.param == "prefix")
     ed.kernel_policy(request.param if request.param in ("rowwise", "term_parallel") else "auto")
     yield request.param
     ed.force_generic(False)
+    ed.force_all_rotations(False)
     ed.force_prefix_search(False)
     ed.kernel_policy("auto")
 
