@@ -239,6 +239,79 @@ bool factorize(int n, int ne, const int32_t *perms, Factorization &F)
 bool g_force_generic = false;
 bool g_force_prefix = false;
 bool g_force_all_rotations = false;  // test hook: factored search over every rotation
+// Index built by ed_basis_build: 0 = the bucketed index for sectors of at
+// least kBucketAutoDim states (where the hash index no longer fits in L2 and
+// every lookup is DRAM traffic), else the hash index; 1 = always the hash
+// index; 2 = the bucketed index wherever its entry fits in 64 bits.
+int g_index_policy = 0;
+constexpr uint64_t kBucketAutoDim = 1ULL << 23;
+
+// Bucketed index over the basis (see find_bucketed): 2^bbits >= dim / 1.8
+// buckets of four slots (at 1.8 keys per bucket about 3 % of the keys go to
+// their alternative bucket and 0.2 % to the stash).  Returns false (and leaves nothing allocated) when
+// the entry does not fit in 64 bits, allocation fails or the stash would
+// overflow; the caller then builds the hash index.
+bool build_bucket_index(ed_basis *b, int norm_bits, cudaStream_t stream)
+{
+    const uint64_t dim = b->dim;
+    int bb = 1;
+    while (bb < 31 && (double)dim > 1.8 * (double)(1ULL << bb))
+        ++bb;
+    const int brem = b->n_sites - bb;
+    if (brem < 0 || brem + 1 + norm_bits > 32 || dim >= 0xFFFFFFFFULL)
+        return false;
+    const uint64_t nbk = 1ULL << bb;
+    const uint32_t cap = (uint32_t)std::min<uint64_t>(dim, std::max<uint64_t>(4096, dim >> 6));
+    uint64_t *d_bkt = nullptr;
+    uint32_t *d_cnt = nullptr;
+    ulonglong2 *d_st = nullptr;
+    cudaError_t e = edk::ws_alloc((void **)&d_bkt, nbk * edk::kBucketSlots * sizeof(uint64_t), stream);
+    if (e == cudaSuccess)
+        e = edk::ws_alloc((void **)&d_cnt, (nbk + 1) * sizeof(uint32_t), stream);  // + the stash counter
+    if (e == cudaSuccess)
+        e = edk::ws_alloc((void **)&d_st, (size_t)cap * sizeof(ulonglong2), stream);
+    if (e == cudaSuccess)
+        e = cudaMemsetAsync(d_bkt, 0xFF, nbk * edk::kBucketSlots * sizeof(uint64_t), stream);
+    if (e == cudaSuccess)
+        e = cudaMemsetAsync(d_cnt, 0, (nbk + 1) * sizeof(uint32_t), stream);
+    if (e == cudaSuccess)
+        e = edk::launch_bucket_fill(b->d_states, b->d_norms, dim, b->n_sites, bb, brem, d_cnt, d_bkt, d_st,
+                                    d_cnt + nbk, cap, stream);
+    uint32_t n_st = 0;
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(&n_st, d_cnt + nbk, sizeof(uint32_t), cudaMemcpyDeviceToHost, stream);
+    if (e == cudaSuccess)
+        e = cudaStreamSynchronize(stream);
+    std::vector<ulonglong2> st;
+    if (e == cudaSuccess && n_st > 0 && n_st <= cap) {
+        // the stash is searched by binary search: sort it by state on the host
+        st.resize(n_st);
+        e = cudaMemcpy(st.data(), d_st, n_st * sizeof(ulonglong2), cudaMemcpyDeviceToHost);
+        std::sort(st.begin(), st.end(), [](const ulonglong2 &a, const ulonglong2 &c) { return a.x < c.x; });
+    }
+    edk::ws_free(d_cnt, stream);
+    edk::ws_free(d_st, stream);
+    ulonglong2 *d_stash = nullptr;
+    if (e == cudaSuccess && n_st > 0 && n_st <= cap) {
+        e = edk::ws_alloc((void **)&d_stash, n_st * sizeof(ulonglong2), stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(d_stash, st.data(), n_st * sizeof(ulonglong2), cudaMemcpyHostToDevice, stream);
+        if (e == cudaSuccess)
+            e = cudaStreamSynchronize(stream);
+    }
+    if (e != cudaSuccess || n_st > cap) {
+        (void)cudaGetLastError();
+        edk::ws_free(d_bkt, stream);
+        edk::ws_free(d_stash, stream);
+        return false;
+    }
+    b->d_bkt = d_bkt;
+    b->d_stash = d_stash;
+    b->n_stash = n_st;
+    b->bbits = bb;
+    b->brem = brem;
+    return true;
+}
 
 void free_basis(ed_basis *b)
 {
@@ -258,6 +331,8 @@ void free_basis(ed_basis *b)
     edk::ws_free(b->d_keys, 0);
     edk::ws_free(b->d_htab, 0);
     edk::ws_free(b->d_hent, 0);
+    edk::ws_free(b->d_bkt, 0);
+    edk::ws_free(b->d_stash, 0);
     edk::ws_free(b->d_tab, 0);
     cudaFree(b->d_masks32);
     cudaFree(b->d_masks64);
@@ -544,12 +619,17 @@ edk::GroupView ed_basis::group_view() const
 edk::IndexView ed_basis::index_view() const
 {
     edk::IndexView v{d_states, d_norms, d_keys, dim, d_tab, tab_size, e_lo, e_hi, mbits, probe_iters};
-    const bool use_hash = d_htab && !g_force_prefix;
+    const bool use_hash = (d_htab || d_bkt) && !g_force_prefix;
     v.htab = use_hash ? d_htab : nullptr;
     v.hent = use_hash ? d_hent : nullptr;
     v.hbits = hbits;
     v.hwide = hwide;
     v.norm_bits = norm_bits;
+    v.bkt = use_hash ? d_bkt : nullptr;
+    v.stash = d_stash;
+    v.n_stash = n_stash;
+    v.bbits = bbits;
+    v.brem = brem;
     return v;
 }
 
@@ -814,7 +894,14 @@ ed_status basis_build_impl(int n_sites, int n_up, int spin_inversion, int n_elem
         ED_B_TRY(edk::basis_status_take(&dev_status));
         flag[0] |= (int)dev_status;
     }
-    if (dim) {
+    bool bucketed = false;
+    if (dim && g_index_policy != 1 && (g_index_policy == 2 || dim >= kBucketAutoDim)) {
+        int nb = 1;
+        while ((1 << nb) <= b->order)
+            ++nb;
+        bucketed = build_bucket_index(b, nb, stream);
+    }
+    if (dim && !bucketed) {
         // hash index: 2^hbits >= dim / 2 buckets (one to two states per bucket)
         int hb = 1;
         while ((2ULL << hb) < dim)
@@ -1101,6 +1188,21 @@ int edx_factorize(int n, int ne, const int32_t *perms, int *rot_L, int *rot_d, u
 // Test hook: 1 = the matvec finds indices through the prefix table and binary
 // search even where the hash index exists.  Affects later launches.
 void edx_force_prefix_search(int on) { g_force_prefix = on != 0; }
+
+// Test hook: the index later basis builds make (0 automatic, 1 hash index,
+// 2 bucketed index wherever its entry fits).
+void edx_index_policy(int policy) { g_index_policy = policy; }
+
+// Diagnostics hook: whether a basis has the bucketed index, its log2 bucket
+// count and the number of stashed keys.
+int edx_basis_bucket(const ed_basis *b, int *bbits, uint32_t *n_stash)
+{
+    if (!b)
+        return -1;
+    if (bbits) *bbits = b->bbits;
+    if (n_stash) *n_stash = b->n_stash;
+    return b->d_bkt ? 1 : 0;
+}
 
 // Diagnostics hook: largest bucket of the hash index and its entry width.
 int edx_basis_hash(const ed_basis *b, int *hbits, uint32_t *max_bucket, int *wide)

@@ -354,6 +354,38 @@ __global__ void k_hash_fill(const uint64_t *states, const uint16_t *norms, uint6
     }
 }
 
+// Slot order inside a bucket depends on atomic timing; a lookup compares the
+// tag, so its result does not.
+__global__ void k_bucket_fill(const uint64_t *states, const uint16_t *norms, uint64_t dim, int n, int bbits,
+                              int brem, uint32_t *cnt, uint64_t *bkt, ulonglong2 *stash, uint32_t *n_stash,
+                              uint32_t stash_cap)
+{
+    const uint32_t bmask = (uint32_t)((1ULL << bbits) - 1);
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < dim;
+         i += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t s = states[i];
+        const uint64_t m = bucket_mix(s, n);
+        const uint32_t rem = (uint32_t)m & ((1u << brem) - 1u);
+        uint32_t b = (uint32_t)(m >> brem);
+        const uint64_t hi = ((uint64_t)norms[i] << (brem + 1)) | ((uint64_t)rem << 1);
+        const uint64_t e = i | (hi << 32);
+        uint32_t slot = atomicAdd(cnt + b, 1u);
+        if (slot < kBucketSlots) {
+            bkt[((uint64_t)b << 2) + slot] = e;
+            continue;
+        }
+        b ^= bucket_alt(rem, bmask);
+        slot = atomicAdd(cnt + b, 1u);
+        if (slot < kBucketSlots) {
+            bkt[((uint64_t)b << 2) + slot] = e | (1ULL << 32);
+            continue;
+        }
+        const uint32_t k = atomicAdd(n_stash, 1u);
+        if (k < stash_cap)
+            stash[k] = make_ulonglong2(s, i | ((uint64_t)norms[i] << 32));
+    }
+}
+
 __global__ void k_max_bucket(const uint32_t *tab, uint64_t tab_size, uint32_t *out)
 {
     uint32_t m = 0;
@@ -463,6 +495,17 @@ cudaError_t launch_hash_fill(const uint64_t *states, const uint16_t *norms, uint
         return cudaSuccess;
     k_hash_fill<<<grid_for(dim), 256, 0, stream>>>(states, norms, dim, hbits, cursor, entries, wide,
                                                     norm_bits); count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_bucket_fill(const uint64_t *states, const uint16_t *norms, uint64_t dim, int n_sites,
+                               int bbits, int brem, uint32_t *cnt, uint64_t *bkt, ulonglong2 *stash,
+                               uint32_t *n_stash, uint32_t stash_cap, cudaStream_t stream)
+{
+    if (!dim)
+        return cudaSuccess;
+    k_bucket_fill<<<grid_for(dim), 256, 0, stream>>>(states, norms, dim, n_sites, bbits, brem, cnt, bkt, stash,
+                                                      n_stash, stash_cap); count_launch();
     return cudaGetLastError();
 }
 

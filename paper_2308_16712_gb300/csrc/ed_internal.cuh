@@ -127,7 +127,97 @@ struct IndexView {
     int hbits;               // log2 of the bucket count
     int hwide;               // 1: 16-byte entries {state, index | norm << 32}
     int norm_bits;           // 8-byte entries: low norm_bits of the packed word hold the norm
+    // bucketed index (replaces the hash index above when present): one 32-byte
+    // bucket of four 8-byte entries per lookup, see find_bucketed
+    const uint64_t *bkt;     // 2^bbits buckets x 4 entries, or null
+    const ulonglong2 *stash; // ascending {state, index | norm << 32} of keys whose two buckets were full
+    uint32_t n_stash;
+    int bbits;               // log2 of the bucket count
+    int brem;                // remainder bits kept per entry: n_sites - bbits
 };
+
+// ---------------------------------------------------------------------------
+// Bucketed index ("stateToIndex" with one memory access).  A product over a
+// sector far larger than L2 is bound by the rate of random DRAM accesses: on
+// GB300 random 32-byte reads saturate near 4e10/s and 64-byte reads near
+// 2.3e10/s, whatever their footprint beyond a few GiB, so each lookup reads
+// exactly one aligned 32-byte bucket (one sector) holding up to four entries,
+// instead of a bucket offset and then an entry.  The state s is mapped by
+// an invertible mix m of its n bits; the top bbits of m choose the bucket and
+// the low brem bits (the remainder) are stored, so that (bucket, remainder)
+// identifies m and hence s with a 64-bit entry:
+//   bits  0..31  index in the basis (dim < 2^32 - 1, so 0xFFFFFFFF marks empty)
+//   bits 32..    tag = remainder << 1 | alt, then the orbit norm above the tag
+// A key goes to the first free slot of its primary bucket, else of its
+// alternative bucket (primary XOR a nonzero function of the remainder; alt = 1
+// in the tag), else to a small sorted stash.  Slots fill in order, so a key is
+// in its alternative bucket only if its primary bucket's last slot is used,
+// and in the stash only if both are full.
+// ---------------------------------------------------------------------------
+constexpr int kBucketSlots = 4;
+
+__host__ __device__ __forceinline__ uint64_t bucket_mix(uint64_t s, int n)
+{
+    const uint64_t full = n >= 64 ? ~0ULL : ((1ULL << n) - 1);
+    uint64_t m = (s * 0x9E3779B97F4A7C15ULL) & full;  // odd multiplier: a bijection mod 2^n
+    m ^= m >> ((n + 1) >> 1);                         // xorshift: a bijection on n bits
+    return (m * 0xD6E8FEB86659FD93ULL) & full;
+}
+
+__host__ __device__ __forceinline__ uint32_t bucket_alt(uint32_t rem, uint32_t bmask)
+{
+    return (uint32_t)((((uint64_t)rem * 0x9E3779B97F4A7C15ULL) >> 40) | 1u) & bmask;  // odd: nonzero
+}
+
+__device__ __forceinline__ bool find_bucketed(uint64_t s, const uint64_t *bkt, const ulonglong2 *stash,
+                                              uint32_t n_stash, int n, int bbits, int brem, uint32_t &idx,
+                                              uint32_t &norm)
+{
+    const uint64_t m = bucket_mix(s, n);
+    const uint32_t rem = (uint32_t)m & ((1u << brem) - 1u);
+    const uint32_t tmask = (2u << brem) - 1u;
+    uint32_t b = (uint32_t)(m >> brem);
+    uint32_t tag = rem << 1;
+#pragma unroll 1
+    for (int pass = 0; pass < 2; ++pass) {
+        const ulonglong2 *p = reinterpret_cast<const ulonglong2 *>(bkt + ((uint64_t)b << 2));
+        ulonglong2 v[kBucketSlots / 2];
+#pragma unroll
+        for (int k = 0; k < kBucketSlots / 2; ++k)
+            v[k] = __ldg(p + k);
+#pragma unroll
+        for (int k = 0; k < kBucketSlots; ++k) {
+            const uint64_t e = (k & 1) ? v[k >> 1].y : v[k >> 1].x;
+            const uint32_t lo = (uint32_t)e, hi = (uint32_t)(e >> 32);
+            if (((hi ^ tag) & tmask) == 0 && lo != 0xFFFFFFFFu) {
+                idx = lo;
+                norm = hi >> (brem + 1);
+                return true;
+            }
+        }
+        if ((uint32_t)v[kBucketSlots / 2 - 1].y == 0xFFFFFFFFu)
+            return false;  // primary (or alternative) bucket not full
+        b ^= bucket_alt(rem, (1u << bbits) - 1u);
+        tag |= 1u;
+    }
+    uint32_t lo = 0, hi = n_stash;
+    while (lo < hi) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (__ldg(&stash[mid].x) < s)
+            lo = mid + 1;
+        else
+            hi = mid;
+    }
+    if (lo < n_stash) {
+        const ulonglong2 e = __ldg(stash + lo);
+        if (e.x == s) {
+            idx = (uint32_t)e.y;
+            norm = (uint32_t)(e.y >> 32);
+            return true;
+        }
+    }
+    return false;
+}
 
 __host__ __device__ __forceinline__ uint32_t hash_bucket(uint64_t s, int hbits)
 {
@@ -565,6 +655,11 @@ struct ed_basis {
     void *d_hent = nullptr;
     int hbits = 0, hwide = 0, norm_bits = 0;
     uint32_t hash_max_bucket = 0;
+    // bucketed index (IndexView; built instead of the hash index for large sectors)
+    uint64_t *d_bkt = nullptr;
+    ulonglong2 *d_stash = nullptr;
+    uint32_t n_stash = 0;
+    int bbits = 0, brem = 0;
 
     edk::GroupView group_view() const;
     edk::IndexView index_view() const;

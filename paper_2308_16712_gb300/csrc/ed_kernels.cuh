@@ -57,6 +57,14 @@ cudaError_t launch_offsets_to_u32(const uint64_t *offsets, uint64_t n, uint32_t 
 cudaError_t launch_hash_fill(const uint64_t *states, const uint16_t *norms, uint64_t dim, int hbits,
                              uint32_t *cursor, void *entries, int wide, int norm_bits,
                              cudaStream_t stream);
+// Bucketed index build: every basis state into the first free slot of its
+// primary bucket, else of its alternative bucket, else appended to the stash
+// (at most stash_cap entries; *n_stash counts every stash insertion, so a value
+// above stash_cap means entries were dropped).  bkt must be all ones (empty),
+// cnt (2^bbits counters) zero.
+cudaError_t launch_bucket_fill(const uint64_t *states, const uint16_t *norms, uint64_t dim, int n_sites,
+                               int bbits, int brem, uint32_t *cnt, uint64_t *bkt, ulonglong2 *stash,
+                               uint32_t *n_stash, uint32_t stash_cap, cudaStream_t stream);
 // *out = max over buckets of tab[t+1] - tab[t] (*out must start at 0)
 cudaError_t launch_max_bucket(const uint32_t *tab, uint64_t tab_size, uint32_t *out, cudaStream_t stream);
 // keys[i] = states[i] << 16 | norms[i]

@@ -704,7 +704,7 @@ ed_status run_lanczos(const ed_operator *op, const ed_basis *b, const void *x0, 
     const bool store = !recompute && (double)(steps + 1) * vec_bytes < 0.5 * (double)free_b;
     // push products are not bit-reproducible, so a recomputed pass would not
     // retrace the first one
-    if (push && (!store || !ov.exchange_only || !iv.htab))
+    if (push && (!store || !ov.exchange_only || !(iv.htab || iv.bkt)))
         return ED_ERR_UNSUPPORTED;
     // reorthogonalisation needs every earlier Lanczos vector
     if (reorth && !store)

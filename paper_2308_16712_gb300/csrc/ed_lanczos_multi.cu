@@ -551,17 +551,13 @@ ed_status run_multi(const ed_operator *op, const ed_sector *sectors, int ns, int
             d.keys = iv.keys;
             d.states = iv.states;
             d.norms = iv.norms;
-            d.htab = b->d_htab;
-            d.hent = b->d_hent;
+            sector_index_from(d, b);
             d.chi = gv.fact ? gv.fchi : gv.chi;
             d.chif = gv.fact ? gv.fchif : gv.chif;
             d.x = (const char *)xin + off[k] * esize;
             d.y = (char *)yout + off[k] * esize;
             d.dim = b->dim;
             d.tile_begin = tiles;
-            d.hbits = b->hbits;
-            d.hwide = b->hwide;
-            d.norm_bits = b->norm_bits;
             d.flip = b->spin_inversion != 0;
             tiles += (b->dim + 31) / 32;
         }
@@ -739,7 +735,7 @@ extern "C" ed_status ed_lanczos_multi(const ed_operator *op, const ed_sector *se
         const void *y = sectors[s].d_y;
         if (b->dim == 0 || !x || (((uintptr_t)x | (uintptr_t)y) & 15))
             return ED_ERR_INVALID_ARG;
-        if (!b->d_htab)
+        if (!b->d_htab && !b->d_bkt)
             return ED_ERR_UNSUPPORTED;
     }
     static std::mutex mtx;  // the launch-argument staging is shared by all calls

@@ -36,6 +36,11 @@ static TpArgs<1> single_tp_args(const OpView &op, const GroupView &g, const Inde
     d.hbits = ix.hbits;
     d.hwide = ix.hwide;
     d.norm_bits = ix.norm_bits;
+    d.bkt = ix.bkt;
+    d.stash = ix.stash;
+    d.n_stash = ix.n_stash;
+    d.bbits = ix.bbits;
+    d.brem = ix.brem;
     d.flip = g.flip;
     return t;
 }
@@ -48,19 +53,21 @@ cudaError_t launch_matvec_push(const OpView &op, const GroupView &g, const Index
     cudaError_t e = cudaMemsetAsync(y, 0, ix.dim * vb, stream);
     if (e != cudaSuccess)
         return e;
-    return tp_push(single_tp_args(op, g, ix, x, y), track, ix.hwide != 0, dtype, stream);
+    const TpArgs<1> t = single_tp_args(op, g, ix, x, y);
+    return tp_push(t, track, tp_index_kind(t.sec[0]), dtype, stream);
 }
 
 cudaError_t launch_matvec(const OpView &op, const GroupView &g, const IndexView &ix, bool track,
                           const void *x, void *y, int nvec, ed_dtype dtype, cudaStream_t stream)
 {
-    if (ix.htab && use_term_parallel(nvec, op, dtype)) {
+    if ((ix.htab || ix.bkt) && use_term_parallel(nvec, op, dtype)) {
         const TpArgs<1> t = single_tp_args(op, g, ix, x, y);
+        const int k = tp_index_kind(t.sec[0]);
         switch (dtype) {
-        case ED_F64: return tp_single_f64(t, track, ix.hwide != 0, stream);
-        case ED_F32: return tp_single_f32(t, track, ix.hwide != 0, stream);
-        case ED_C128: return tp_single_c128(t, track, ix.hwide != 0, stream);
-        case ED_C64: return tp_single_c64(t, track, ix.hwide != 0, stream);
+        case ED_F64: return tp_single_f64(t, track, k, stream);
+        case ED_F32: return tp_single_f32(t, track, k, stream);
+        case ED_C128: return tp_single_c128(t, track, k, stream);
+        case ED_C64: return tp_single_c64(t, track, k, stream);
         }
         return cudaErrorInvalidValue;
     }

@@ -393,7 +393,10 @@ __global__ void __launch_bounds__(kMvThreads) k_matvec(const MatvecArgs a)
         if (has) {
             uint32_t jj = 0, nj = 0;
             bool found;
-            if (a.ix.htab) {
+            if (a.ix.bkt) {
+                found = find_bucketed((uint64_t)best, a.ix.bkt, a.ix.stash, a.ix.n_stash, n, a.ix.bbits,
+                                      a.ix.brem, jj, nj);
+            } else if (a.ix.htab) {
                 found = find_hashed((uint64_t)best, a.ix, jj, nj);
             } else if (packed) {
                 found = find_key((uint64_t)best, a.ix, jj, nj);

@@ -17,11 +17,11 @@ cudaError_t multi_c64(const MultiArgs &a, bool track, cudaStream_t s) { return m
 // multi-sector kernel.
 cudaError_t multi_launch_any(const MultiArgs &a, bool track, ed_dtype dtype, cudaStream_t s)
 {
-    bool same_width = true;
+    bool same_kind = true;
     for (int k = 1; k < a.n_sectors; ++k)
-        same_width = same_width && (a.sec[k].hwide != 0) == (a.sec[0].hwide != 0);
-    if (same_width && use_term_parallel(a.nvec, a.op, dtype)) {
-        const bool wide = a.n_sectors > 0 && a.sec[0].hwide != 0;
+        same_kind = same_kind && tp_index_kind(a.sec[k]) == tp_index_kind(a.sec[0]);
+    if (same_kind && use_term_parallel(a.nvec, a.op, dtype)) {
+        const int kind = a.n_sectors > 0 ? tp_index_kind(a.sec[0]) : 0;
         static thread_local TpArgs<kMaxSectors> t;  // host staging (17 KB); copied at launch
         t.op = a.op;
         t.g = a.g;
@@ -31,10 +31,10 @@ cudaError_t multi_launch_any(const MultiArgs &a, bool track, ed_dtype dtype, cud
         for (int k = 0; k < a.n_sectors; ++k)
             t.sec[k] = a.sec[k];
         switch (dtype) {
-        case ED_F64: return tp_multi_f64(t, track, wide, s);
-        case ED_F32: return tp_multi_f32(t, track, wide, s);
-        case ED_C128: return tp_multi_c128(t, track, wide, s);
-        case ED_C64: return tp_multi_c64(t, track, wide, s);
+        case ED_F64: return tp_multi_f64(t, track, kind, s);
+        case ED_F32: return tp_multi_f32(t, track, kind, s);
+        case ED_C128: return tp_multi_c128(t, track, kind, s);
+        case ED_C64: return tp_multi_c64(t, track, kind, s);
         }
         return cudaErrorInvalidValue;
     }
@@ -85,7 +85,7 @@ extern "C" ed_status ed_matvec_multi(const ed_operator *op, const ed_sector *sec
         void *y = sectors[s].d_y;
         if (!x || !y || x == y || (((uintptr_t)x | (uintptr_t)y) & 15))
             return ED_ERR_INVALID_ARG;
-        if (!b->d_htab)
+        if (!b->d_htab && !b->d_bkt)
             return ED_ERR_UNSUPPORTED;
         const GroupView gv = b->group_view();
         const IndexView iv = b->index_view();
@@ -93,17 +93,13 @@ extern "C" ed_status ed_matvec_multi(const ed_operator *op, const ed_sector *sec
         d.keys = iv.keys;
         d.states = iv.states;
         d.norms = iv.norms;
-        d.htab = b->d_htab;
-        d.hent = b->d_hent;
+        sector_index_from(d, b);
         d.chi = gv.fact ? gv.fchi : gv.chi;
         d.chif = gv.fact ? gv.fchif : gv.chif;
         d.x = x;
         d.y = y;
         d.dim = b->dim;
         d.tile_begin = tiles;
-        d.hbits = b->hbits;
-        d.hwide = b->hwide;
-        d.norm_bits = b->norm_bits;
         d.flip = b->spin_inversion != 0;
         tiles += (b->dim + 31) / 32;
         track = track || !b->trivial_chars;

@@ -20,8 +20,12 @@ struct SectorDesc {
     const uint64_t *keys;     // state << 16 | norm (or null: states + norms)
     const uint64_t *states;
     const uint16_t *norms;
-    const uint32_t *htab;     // hash index (required)
+    const uint32_t *htab;     // hash index (this or the bucketed index is required)
     const void *hent;
+    const uint64_t *bkt;      // bucketed index (IndexView), or null
+    const ulonglong2 *stash;
+    uint32_t n_stash;
+    int bbits, brem;
     const double2 *chi;       // characters in the order of the search used
     const float2 *chif;
     const void *x;
@@ -30,6 +34,22 @@ struct SectorDesc {
     uint64_t tile_begin;      // first tile of this sector in the batch
     int hbits, hwide, norm_bits, flip;
 };
+
+// the index of a basis as a sector descriptor sees it (the hash index, or the
+// bucketed index where the basis has one)
+inline void sector_index_from(SectorDesc &d, const ed_basis *b)
+{
+    d.htab = b->d_htab;
+    d.hent = b->d_hent;
+    d.hbits = b->hbits;
+    d.hwide = b->hwide;
+    d.norm_bits = b->norm_bits;
+    d.bkt = b->d_bkt;
+    d.stash = b->d_stash;
+    d.n_stash = b->n_stash;
+    d.bbits = b->bbits;
+    d.brem = b->brem;
+}
 
 struct MultiArgs {
     OpView op;
@@ -316,7 +336,10 @@ __global__ void __launch_bounds__(kMvThreads) k_matvec_multi(const __grid_consta
             ix.hwide = sd.hwide;
             ix.norm_bits = sd.norm_bits;
             uint32_t jj = 0, nj = 0;
-            if (find_hashed((uint64_t)best, ix, jj, nj)) {
+            const bool found = sd.bkt ? find_bucketed((uint64_t)best, sd.bkt, sd.stash, sd.n_stash, n, sd.bbits,
+                                                      sd.brem, jj, nj)
+                                      : find_hashed((uint64_t)best, ix, jj, nj);
+            if (found) {
                 const uint64_t j = jj;
                 const T ratio = sm_sq[nj] * rinv;
                 const Cplx<T> h = sm_mats[amp];

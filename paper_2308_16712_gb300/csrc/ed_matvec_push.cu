@@ -9,13 +9,13 @@
 
 namespace edk {
 
-cudaError_t tp_push(const TpArgs<1> &a, bool track, bool wide, ed_dtype dtype, cudaStream_t s)
+cudaError_t tp_push(const TpArgs<1> &a, bool track, int idx, ed_dtype dtype, cudaStream_t s)
 {
     switch (dtype) {
-    case ED_F64: return tp_dispatch<double, false, 1, true>(a, track, wide, s);
-    case ED_F32: return tp_dispatch<float, false, 1, true>(a, track, wide, s);
-    case ED_C128: return tp_dispatch<double, true, 1, true>(a, track, wide, s);
-    case ED_C64: return tp_dispatch<float, true, 1, true>(a, track, wide, s);
+    case ED_F64: return tp_dispatch<double, false, 1, true>(a, track, idx, s);
+    case ED_F32: return tp_dispatch<float, false, 1, true>(a, track, idx, s);
+    case ED_C128: return tp_dispatch<double, true, 1, true>(a, track, idx, s);
+    case ED_C64: return tp_dispatch<float, true, 1, true>(a, track, idx, s);
     }
     return cudaErrorInvalidValue;
 }

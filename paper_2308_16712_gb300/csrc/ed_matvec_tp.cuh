@@ -137,11 +137,13 @@ __device__ __forceinline__ uint32_t ent_norm(uint2 v, int nb) { return v.y & ((1
 __device__ __forceinline__ uint32_t ent_index(ulonglong2 v, int) { return (uint32_t)v.y; }
 __device__ __forceinline__ uint32_t ent_norm(ulonglong2 v, int) { return (uint32_t)(v.y >> 32); }
 
-template <typename W, typename T, bool kC, bool kTrack, bool kFact, bool kWide, int kSec, bool kPush = false>
+// kIdx: index of the sectors -- 0 hash index with 8-byte entries, 1 with
+// 16-byte entries, 2 bucketed index (find_bucketed)
+template <typename W, typename T, bool kC, bool kTrack, bool kFact, int kIdx, int kSec, bool kPush = false>
 __global__ void __launch_bounds__(kTpThreads, 8) k_matvec_tp(const __grid_constant__ TpArgs<kSec> a)
 {
     using V = typename ValT<T, kC>::type;
-    using E = std::conditional_t<kWide, ulonglong2, uint2>;
+    using E = std::conditional_t<kIdx == 1, ulonglong2, uint2>;
     extern __shared__ __align__(16) unsigned char smem[];
     size_t off[8];
     tp_smem_layout<W, T, V, kFact>(a.g, a.op, a.n_sectors, a.max_order, off);
@@ -373,12 +375,27 @@ __global__ void __launch_bounds__(kTpThreads, 8) k_matvec_tp(const __grid_consta
             // stateToIndex through the bucket of the hash index, gather, scale
             V val = vzero<V>();
             if (act) {
-                const uint32_t bk = hash_bucket((uint64_t)best, hbits);
-                const uint32_t e1 = __ldg(htab + bk + 1);
-                for (uint32_t e = __ldg(htab + bk); e < e1; ++e) {
-                    const E v = __ldg(hent + e);
-                    if (ent_state<W>(v) == best) {
-                        const T ratio = sm_sq[ent_norm(v, norm_bits)] * ws.rinv[rho];
+                uint32_t jidx = 0, jnorm = 0;
+                bool found = false;
+                if constexpr (kIdx == 2) {
+                    found = find_bucketed((uint64_t)best, sd.bkt, sd.stash, sd.n_stash, n, sd.bbits, sd.brem, jidx,
+                                          jnorm);
+                } else {
+                    const uint32_t bk = hash_bucket((uint64_t)best, hbits);
+                    const uint32_t e1 = __ldg(htab + bk + 1);
+                    for (uint32_t e = __ldg(htab + bk); e < e1; ++e) {
+                        const E v = __ldg(hent + e);
+                        if (ent_state<W>(v) == best) {
+                            jidx = ent_index(v, norm_bits);
+                            jnorm = ent_norm(v, norm_bits);
+                            found = true;
+                            break;
+                        }
+                    }
+                }
+                if (found) {
+                    {
+                        const T ratio = sm_sq[jnorm] * ws.rinv[rho];
                         const Cplx<T> h = sm_mats[amp];
                         Cplx<T> coef = {h.re * ratio, -h.im * ratio};  // conj(h) sqrt(n'/n)
                         if (kTrack) {
@@ -398,15 +415,14 @@ __global__ void __launch_bounds__(kTpThreads, 8) k_matvec_tp(const __grid_consta
                                 pv = cmul(conjc(coef), xr);
                             else
                                 pv = coef.re * xr;
-                            atomic_add(reinterpret_cast<V *>(sd.y) + ent_index(v, norm_bits), pv);
+                            atomic_add(reinterpret_cast<V *>(sd.y) + jidx, pv);
                         } else {
-                            const V xv = x[ent_index(v, norm_bits)];
+                            const V xv = x[jidx];
                             if constexpr (kC)
                                 val = cmul(coef, xv);
                             else
                                 val = coef.re * xv;
                         }
-                        break;
                     }
                 }
             }
@@ -430,11 +446,11 @@ __global__ void __launch_bounds__(kTpThreads, 8) k_matvec_tp(const __grid_consta
     }
 }
 
-template <typename W, typename T, bool kC, bool kTrack, bool kFact, bool kWide, int kSec, bool kPush = false>
+template <typename W, typename T, bool kC, bool kTrack, bool kFact, int kIdx, int kSec, bool kPush = false>
 cudaError_t tp_launch(const TpArgs<kSec> &a, cudaStream_t stream)
 {
     using V = typename ValT<T, kC>::type;
-    auto kern = k_matvec_tp<W, T, kC, kTrack, kFact, kWide, kSec, kPush>;
+    auto kern = k_matvec_tp<W, T, kC, kTrack, kFact, kIdx, kSec, kPush>;
     const size_t smem = tp_smem_bytes<W, T, V, kFact>(a.g, a.op, a.n_sectors, a.max_order);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess)
@@ -451,28 +467,34 @@ cudaError_t tp_launch(const TpArgs<kSec> &a, cudaStream_t stream)
     return cudaGetLastError();
 }
 
-// wide: 16-byte hash entries (every sector of the batch must agree); kPush:
+// idx: index kind of every sector of the batch (they must agree): 0 hash
+// index with 8-byte entries, 1 with 16-byte entries, 2 bucketed index; kPush:
 // the transposed (push) form with atomic scatter into y, which must be zero
 template <typename T, bool kC, int kSec, bool kPush = false>
-cudaError_t tp_dispatch(const TpArgs<kSec> &a, bool track, bool wide, cudaStream_t stream)
+cudaError_t tp_dispatch(const TpArgs<kSec> &a, bool track, int idx, cudaStream_t stream)
 {
     const bool w32 = a.g.n_sites <= 32;
     const bool fact = a.g.fact != 0;
-#define ED_TP_FA(W, TR, WD)                                                             \
+#define ED_TP_FA(W, TR, IX)                                                             \
     do {                                                                                \
-        if (fact) return tp_launch<W, T, kC, TR, true, WD, kSec, kPush>(a, stream);     \
-        return tp_launch<W, T, kC, TR, false, WD, kSec, kPush>(a, stream);              \
+        if (fact) return tp_launch<W, T, kC, TR, true, IX, kSec, kPush>(a, stream);     \
+        return tp_launch<W, T, kC, TR, false, IX, kSec, kPush>(a, stream);              \
     } while (0)
-    if (w32) {
-        if (wide) {
-            if (track) ED_TP_FA(uint32_t, true, true);
-            ED_TP_FA(uint32_t, false, true);
-        }
-        if (track) ED_TP_FA(uint32_t, true, false);
-        ED_TP_FA(uint32_t, false, false);
+#define ED_TP_TR(W, IX)                  \
+    do {                                 \
+        if (track) ED_TP_FA(W, true, IX); \
+        ED_TP_FA(W, false, IX);          \
+    } while (0)
+    if (idx == 2) {
+        if (w32) ED_TP_TR(uint32_t, 2);
+        ED_TP_TR(uint64_t, 2);
     }
-    if (track) ED_TP_FA(uint64_t, true, true);
-    ED_TP_FA(uint64_t, false, true);
+    if (w32) {
+        if (idx == 1) ED_TP_TR(uint32_t, 1);
+        ED_TP_TR(uint32_t, 0);
+    }
+    ED_TP_TR(uint64_t, 1);
+#undef ED_TP_TR
 #undef ED_TP_FA
 }
 
@@ -480,16 +502,19 @@ cudaError_t tp_dispatch(const TpArgs<kSec> &a, bool track, bool wide, cudaStream
 // family's matrix couples configurations 1 and 2 (|01> <-> |10>).
 bool tp_operator_ok(const ed_operator *op);
 
-// one sector (tp_single_*) or a batch (tp_multi_*), nvec = 1
-cudaError_t tp_single_f64(const TpArgs<1> &a, bool track, bool wide, cudaStream_t s);
-cudaError_t tp_single_f32(const TpArgs<1> &a, bool track, bool wide, cudaStream_t s);
-cudaError_t tp_single_c128(const TpArgs<1> &a, bool track, bool wide, cudaStream_t s);
-cudaError_t tp_single_c64(const TpArgs<1> &a, bool track, bool wide, cudaStream_t s);
-cudaError_t tp_multi_f64(const TpArgs<kMaxSectors> &a, bool track, bool wide, cudaStream_t s);
-cudaError_t tp_multi_f32(const TpArgs<kMaxSectors> &a, bool track, bool wide, cudaStream_t s);
-cudaError_t tp_multi_c128(const TpArgs<kMaxSectors> &a, bool track, bool wide, cudaStream_t s);
-cudaError_t tp_multi_c64(const TpArgs<kMaxSectors> &a, bool track, bool wide, cudaStream_t s);
+// index kind of a sector for tp_dispatch
+inline int tp_index_kind(const SectorDesc &d) { return d.bkt ? 2 : (d.hwide ? 1 : 0); }
+
+// one sector (tp_single_*) or a batch (tp_multi_*), nvec = 1; idx as tp_dispatch
+cudaError_t tp_single_f64(const TpArgs<1> &a, bool track, int idx, cudaStream_t s);
+cudaError_t tp_single_f32(const TpArgs<1> &a, bool track, int idx, cudaStream_t s);
+cudaError_t tp_single_c128(const TpArgs<1> &a, bool track, int idx, cudaStream_t s);
+cudaError_t tp_single_c64(const TpArgs<1> &a, bool track, int idx, cudaStream_t s);
+cudaError_t tp_multi_f64(const TpArgs<kMaxSectors> &a, bool track, int idx, cudaStream_t s);
+cudaError_t tp_multi_f32(const TpArgs<kMaxSectors> &a, bool track, int idx, cudaStream_t s);
+cudaError_t tp_multi_c128(const TpArgs<kMaxSectors> &a, bool track, int idx, cudaStream_t s);
+cudaError_t tp_multi_c64(const TpArgs<kMaxSectors> &a, bool track, int idx, cudaStream_t s);
 // push form (ablation), one sector, y zeroed by the caller
-cudaError_t tp_push(const TpArgs<1> &a, bool track, bool wide, ed_dtype dtype, cudaStream_t s);
+cudaError_t tp_push(const TpArgs<1> &a, bool track, int idx, ed_dtype dtype, cudaStream_t s);
 
 }  // namespace edk

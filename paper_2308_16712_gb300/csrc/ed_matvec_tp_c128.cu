@@ -3,12 +3,12 @@
 #include "ed_matvec_tp.cuh"
 
 namespace edk {
-cudaError_t tp_single_c128(const TpArgs<1> &a, bool track, bool wide, cudaStream_t s)
+cudaError_t tp_single_c128(const TpArgs<1> &a, bool track, int idx, cudaStream_t s)
 {
-    return tp_dispatch<double, true, 1>(a, track, wide, s);
+    return tp_dispatch<double, true, 1>(a, track, idx, s);
 }
-cudaError_t tp_multi_c128(const TpArgs<kMaxSectors> &a, bool track, bool wide, cudaStream_t s)
+cudaError_t tp_multi_c128(const TpArgs<kMaxSectors> &a, bool track, int idx, cudaStream_t s)
 {
-    return tp_dispatch<double, true, kMaxSectors>(a, track, wide, s);
+    return tp_dispatch<double, true, kMaxSectors>(a, track, idx, s);
 }
 }  // namespace edk

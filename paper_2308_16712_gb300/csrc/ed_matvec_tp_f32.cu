@@ -3,12 +3,12 @@
 #include "ed_matvec_tp.cuh"
 
 namespace edk {
-cudaError_t tp_single_f32(const TpArgs<1> &a, bool track, bool wide, cudaStream_t s)
+cudaError_t tp_single_f32(const TpArgs<1> &a, bool track, int idx, cudaStream_t s)
 {
-    return tp_dispatch<float, false, 1>(a, track, wide, s);
+    return tp_dispatch<float, false, 1>(a, track, idx, s);
 }
-cudaError_t tp_multi_f32(const TpArgs<kMaxSectors> &a, bool track, bool wide, cudaStream_t s)
+cudaError_t tp_multi_f32(const TpArgs<kMaxSectors> &a, bool track, int idx, cudaStream_t s)
 {
-    return tp_dispatch<float, false, kMaxSectors>(a, track, wide, s);
+    return tp_dispatch<float, false, kMaxSectors>(a, track, idx, s);
 }
 }  // namespace edk

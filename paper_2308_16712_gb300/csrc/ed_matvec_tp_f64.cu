@@ -3,12 +3,12 @@
 #include "ed_matvec_tp.cuh"
 
 namespace edk {
-cudaError_t tp_single_f64(const TpArgs<1> &a, bool track, bool wide, cudaStream_t s)
+cudaError_t tp_single_f64(const TpArgs<1> &a, bool track, int idx, cudaStream_t s)
 {
-    return tp_dispatch<double, false, 1>(a, track, wide, s);
+    return tp_dispatch<double, false, 1>(a, track, idx, s);
 }
-cudaError_t tp_multi_f64(const TpArgs<kMaxSectors> &a, bool track, bool wide, cudaStream_t s)
+cudaError_t tp_multi_f64(const TpArgs<kMaxSectors> &a, bool track, int idx, cudaStream_t s)
 {
-    return tp_dispatch<double, false, kMaxSectors>(a, track, wide, s);
+    return tp_dispatch<double, false, kMaxSectors>(a, track, idx, s);
 }
 }  // namespace edk

@@ -72,6 +72,8 @@ _SIGS = {
     "edx_launch_count": (ctypes.c_ulonglong, []),
     "edx_force_generic": (None, [_i32]),
     "edx_force_all_rotations": (None, [_i32]),
+    "edx_index_policy": (None, [_i32]),
+    "edx_basis_bucket": (_i32, [_P, ctypes.POINTER(_i32), ctypes.POINTER(ctypes.c_uint32)]),
     "edx_count_nnz": (_i32, [_P, _P, ctypes.POINTER(ctypes.c_ulonglong)]),
     "edx_force_prefix_search": (None, [_i32]),
     "edx_kernel_policy": (None, [_i32]),
@@ -280,6 +282,23 @@ def force_all_rotations(on: bool) -> None:
     """Test hook: the factored group search visits every rotation (no pruning
     to the tops of the longest runs of equal bits)."""
     _lib.edx_force_all_rotations(1 if on else 0)
+
+
+INDEX_POLICIES = {"auto": 0, "hash": 1, "bucket": 2}
+
+
+def index_policy(policy: str) -> None:
+    """Test hook: the index later basis builds make -- "auto" (the bucketed
+    index for large sectors), "hash" (always the hash index) or "bucket" (the
+    bucketed index wherever its 64-bit entry can hold the key)."""
+    _lib.edx_index_policy(INDEX_POLICIES[policy])
+
+
+def basis_bucket(basis: Basis):
+    """(present, log2 bucket count, stashed keys) of a basis's bucketed index."""
+    bb, ns = _i32(0), ctypes.c_uint32(0)
+    r = _lib.edx_basis_bucket(basis.handle, ctypes.byref(bb), ctypes.byref(ns))
+    return bool(r == 1), bb.value, ns.value
 
 
 def count_nnz(op: Operator, basis: Basis) -> int:

@@ -56,6 +56,7 @@ def test_ring40_config():
     B = ed.basis_build(40, 20, +1, w["perms"], w["chars"])
     assert ed.basis_size(B) == 861725794
     assert ed.basis_factored(B)[0]
+    assert ed.basis_bucket(B)[0]  # the bucketed index (chosen for large sectors)
     O = ed.operator_create(40, w["op"]["sites"], w["op"]["coeff"], w["op"]["local"])
     G = oracle.Group(40, w["perms"], w["chars"], +1)
     st_t, _ = ed.basis_states(B)
@@ -65,8 +66,8 @@ def test_ring40_config():
 
 def test_ring42_config():
     """Heisenberg ring N=42, Sz=0, k=0, p=+1, z=+1: 3 204 236 779 representatives
-    (the paper's Table 2), built in full on one GPU (64-bit words, 16-byte hash
-    entries, indices beyond 2^31); sampled rows of y = Hx in fp64 (row-per-lane
+    (the paper's Table 2), built in full on one GPU (64-bit words, bucketed
+    index, indices beyond 2^31); sampled rows of y = Hx in fp64 (row-per-lane
     kernel) and fp32 (term-parallel kernel) against the oracle."""
     torch, ed = gpu()
     torch.cuda.empty_cache()  # the basis and its index take ~125 GB outside torch's cache
@@ -74,7 +75,7 @@ def test_ring42_config():
     B = ed.basis_build(42, 21, +1, w["perms"], w["chars"])
     assert ed.basis_size(B) == 3204236779
     assert ed.basis_factored(B)[0]
-    assert ed.basis_hash(B)[0] and ed.basis_hash(B)[3]  # hash index with wide entries
+    assert ed.basis_bucket(B)[0] and not ed.basis_hash(B)[0]
     O = ed.operator_create(42, w["op"]["sites"], w["op"]["coeff"], w["op"]["local"])
     G = oracle.Group(42, w["perms"], w["chars"], +1)
     st_t, _ = ed.basis_states(B)
@@ -86,6 +87,37 @@ def test_ring42_config():
     q = st_t[[0, (1 << 31) + 12345, 3204236778]].contiguous()
     assert ed.basis_index(B, q).cpu().tolist() == [0, (1 << 31) + 12345, 3204236778]
     sampled_rows_check(B, O, G, oracle.Operator(w["op"]), 43, 1, False, n_rows=40)
+
+
+def test_ring36_bucketed_equals_hash_index():
+    """Heisenberg ring N=36 (63 068 876 representatives): the products through
+    the bucketed index equal those through the hash index bit for bit (both
+    lookups are exact and the summation order is the same), for the
+    term-parallel kernel (fp32), the row-per-lane kernel (fp64) and block
+    vectors (fp32, nvec = 8)."""
+    torch, ed = gpu()
+    w = ei.workload("ring36")
+    O = ed.operator_create(36, w["op"]["sites"], w["op"]["coeff"], w["op"]["local"])
+    bases = {}
+    try:
+        for pol in ("hash", "bucket"):
+            ed.index_policy(pol)
+            bases[pol] = ed.basis_build(36, 18, +1, w["perms"], w["chars"])
+    finally:
+        ed.index_policy("auto")
+    assert ed.basis_hash(bases["hash"])[0] and ed.basis_bucket(bases["bucket"])[0]
+    assert ed.basis_size(bases["hash"]) == ed.basis_size(bases["bucket"]) == 63068876
+    st, _ = ed.basis_states(bases["hash"])
+    for dt, nvec in ((torch.float32, 1), (torch.float64, 1), (torch.float32, 8)):
+        x = ei.x_by_state_torch_chunked(7, st, nvec, False, dtype=dt)
+        ys = []
+        for pol in ("hash", "bucket"):
+            y = torch.empty_like(x)
+            ed.matvec(O, bases[pol], x, y, nvec)
+            ys.append(y)
+        assert torch.equal(ys[0], ys[1])
+        del x, ys
+        torch.cuda.empty_cache()
 
 
 def test_table2_n44_count_on_gpu():

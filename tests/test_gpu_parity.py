@@ -87,8 +87,8 @@ def make(case, with_oracle=True):
     return build_pair(n, n_up, z, p, c, opf(), with_oracle)
 
 
-@pytest.fixture(params=["factored", "all_rotations", "generic", "prefix", "rowwise", "term_parallel"],
-                autouse=True)
+@pytest.fixture(params=["factored", "all_rotations", "generic", "prefix", "rowwise", "term_parallel",
+                        "bucket"], autouse=True)
 def search_mode(request):
     """Run every parity test six times: factored (rotation x coset) group
     search with the hash index, pruned to the tops of the longest runs where
@@ -98,13 +98,16 @@ def search_mode(request):
     factored search and hash index with the row-per-lane kernel forced; and
     with the term-parallel kernel forced in both precisions (it otherwise
     serves single vectors of exchange-only operators in single precision
-    only)."""
+    only); and with the bucketed index (one 64-byte bucket per lookup) built
+    for every sector whose key fits its entry."""
     torch, ed = gpu()
+    ed.index_policy("bucket" if request.param == "bucket" else "hash")
     ed.force_generic(request.param == "generic")
     ed.force_all_rotations(request.param == "all_rotations")
     ed.force_prefix_search(request.param == "prefix")
     ed.kernel_policy(request.param if request.param in ("rowwise", "term_parallel") else "auto")
     yield request.param
+    ed.index_policy("auto")
     ed.force_generic(False)
     ed.force_all_rotations(False)
     ed.force_prefix_search(False)
@@ -119,9 +122,12 @@ def test_basis_bit_exact(case, search_mode):
     if case[0].startswith(("ring", "torus")) and search_mode == "factored":
         assert fact and nc * L == len(case[4]()[0])
     has_hash, hbits, hmax, wide = ed.basis_hash(S["B"])
-    assert has_hash == (S["dim"] > 0)
-    if S["dim"]:
+    has_bkt, bbits, n_stash = ed.basis_bucket(S["B"])
+    assert (has_hash or has_bkt) == (S["dim"] > 0) and not (has_hash and has_bkt)
+    if has_hash:
         assert (2 << hbits) >= S["dim"] and hmax <= 16
+    if has_bkt:
+        assert search_mode == "bucket" and 1.8 * (1 << bbits) >= S["dim"] and n_stash <= S["dim"]
     st, nm = gpu_basis_numpy(S["B"])
     assert S["dim"] == len(S["st"]) == oracle.sector_dim(S["G"], case[2])
     assert np.array_equal(st, S["st"])
