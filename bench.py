@@ -353,6 +353,37 @@ def search_ops_per_term(n, n_perm, flip, fact, rot_L, n_cos, kinds):
     return head + n_cos * rot_L * per_rot + (1 if flip else 0)
 
 
+def measure_peaks(dev=None):
+    """This GPU's measured ceilings (the library's peak kernels, CUDA events):
+    integer op mix of the group search, fp64 and fp32 FMA, and random 32-byte
+    reads over an 8 GiB buffer (far above L2)."""
+    import torch
+    from paper_2308_16712_gb300 import ed
+    out = {}
+    for kind in ("int32_mix", "fp64_fma", "fp32_fma"):
+        rate, ms = ed.peak(kind)
+        out[kind] = {"rate": rate, "ms": ms}
+    buf = torch.empty(8 << 30, dtype=torch.uint8, device=dev or "cuda")
+    buf.fill_(1)
+    rate, ms = ed.peak("gather32", buf)
+    out["gather32"] = {"rate": rate, "ms": ms, "span_bytes": buf.numel()}
+    del buf
+    torch.cuda.empty_cache()
+    return out
+
+
+def run_peaks(args, w):
+    import torch
+    sampler = ClockSampler(0)
+    pk = measure_peaks()
+    clocks = sampler.stop()
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    mhz = (clocks or {}).get("sm_mhz", 2070.0)
+    for k in ("int32_mix", "fp64_fma", "fp32_fma"):
+        pk[k]["per_sm_per_clk"] = pk[k]["rate"] / sms / (mhz * 1e6)
+    print(json.dumps({"mode": "peaks", "sms": sms, "clocks": clocks, **pk}), flush=True)
+
+
 def run_one_step(args, w):
     import torch
     from paper_2308_16712_gb300 import ed
@@ -538,7 +569,8 @@ def main():
     ap.add_argument("--lanczos-steps", type=int, default=100,
                     help="Lanczos steps of the batched solve in --mode multi (0: skip)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--mode", default="job", choices=["job", "matvec", "step", "solve", "multi", "push"],
+    ap.add_argument("--mode", default="job", choices=["job", "matvec", "step", "solve", "multi", "push",
+                                                      "peaks"],
                     help="job: the benchmark; matvec: only the basis build and --steps matvec "
                          "launches per dtype; step: one untimed and one more whole step "
                          "(short programs for profiler captures)")
@@ -551,6 +583,8 @@ def main():
         return run_matvec_only(args, w)
     if args.mode == "step":
         return run_one_step(args, w)
+    if args.mode == "peaks":
+        return run_peaks(args, w)
     if args.mode == "solve":
         return run_solve(args, w)
     if args.mode == "push":

@@ -346,6 +346,55 @@ ed_status ed_lanczos_eigs(const ed_operator *op, const ed_basis *basis, const vo
                           ed_lanczos_info *info, void *stream);
 
 /*
+ * ed_lanczos_block -- lowest eigenvalues of H in a real sector by the block
+ * Lanczos recurrence on nvec vectors at once (Background: Krylov methods
+ * consume hundreds of matrix-vector products; here every product is one
+ * interleaved block product, in which one representative search and index
+ * lookup per matrix element serves all nvec columns, Sec. "Matrix-vector
+ * product").
+ *
+ *   d_x0      device start block, dim x nvec doubles laid out [dim][nvec]
+ *             (need not be orthonormal; must have rank nvec)
+ *   nvec      block size: 2, 4, 8 or 16
+ *   steps     1..10000 block steps (no restart); the recurrence stops early
+ *             when the block Krylov space stops growing
+ *   mode      ED_LANCZOS_F64 (fp64 block products) or ED_LANCZOS_F32_MATVEC
+ *             (products of the block's fp32 copy), optionally OR-ed with
+ *             ED_LANCZOS_REORTH: every block is kept and each new one is
+ *             orthogonalised against all earlier ones (block modified
+ *             Gram-Schmidt, twice), so that the higher Ritz values carry no
+ *             spurious copies of converged ones; needs the blocks to fit in
+ *             half of the free memory (ED_ERR_UNSUPPORTED otherwise)
+ *   n_eig     0..nvec*steps lowest Ritz values to return in eigs_out (host,
+ *             ascending; NaN past the dimension of the space built)
+ *   e0_out    host, the refined lowest energy (may be NULL)
+ *   d_vec_out device, dim doubles, the normalised ground-state approximation
+ *             (may be NULL)
+ *   info      host (may be NULL); steps = block steps taken, matvecs = block
+ *             products plus the refinement's single products, ritz = lowest
+ *             Ritz value of the block recurrence
+ *
+ * The blocks and their coefficient matrices are fp64: for every step
+ * C = V_j^T W and Cp = V_{j-1}^T W of the product W = H V_j (compensated
+ * fp64 sums over a fixed partition), W -= V_j C + V_{j-1} Cp, and a Cholesky
+ * QR applied twice gives the next block and the coupling B_{j+1}.  The lowest
+ * eigenpair of the block tridiagonal matrix (bandwidth nvec) is found on the
+ * GPU by bisection with Sturm counts of its banded LDL^T factorisation and by
+ * inverse iteration; the Ritz vector by a second, bit-identical pass (no
+ * block is stored); the energy is then refined exactly as ed_lanczos's
+ * fp32-matvec mode does (a short fp64 single-vector Lanczos run from the
+ * Ritz vector; fp64 Rayleigh quotient and residual).  Memory: three blocks
+ * of fp64 (two in the fp32 mode, plus two fp32 blocks) from the library's
+ * pool.  Synchronises `stream` before returning.
+ * Errors: ED_ERR_INVALID_ARG (also nvec not in {2, 4, 8, 16}, a sector
+ * smaller than nvec or a start block of lower rank), ED_ERR_SYMMETRY_MISMATCH,
+ * ED_ERR_UNSUPPORTED (complex sectors or operators), ED_ERR_OOM, ED_ERR_CUDA.
+ */
+ed_status ed_lanczos_block(const ed_operator *op, const ed_basis *basis, const void *d_x0, int nvec, int steps,
+                           int mode, int n_eig, double *eigs_out, double *e0_out, void *d_vec_out,
+                           ed_lanczos_info *info, void *stream);
+
+/*
  * ed_lanczos_multi -- lowest eigenvalue of H in each of up to 160 symmetry
  * sectors, by the recurrence of ed_lanczos run on all sectors together
  * (Sec. "Introduction": symmetries make H block diagonal, one independent

@@ -66,6 +66,8 @@ _SIGS = {
                           ctypes.POINTER(LanczosInfo), _P]),
     "ed_lanczos_eigs": (_i32, [_P, _P, _P, _i32, _i32, _i32, ctypes.POINTER(_d), _d, _P,
                                ctypes.POINTER(LanczosInfo), _P]),
+    "ed_lanczos_block": (_i32, [_P, _P, _P, _i32, _i32, _i32, _i32, ctypes.POINTER(_d), ctypes.POINTER(_d), _P,
+                                ctypes.POINTER(LanczosInfo), _P]),
     "ed_lanczos_multi": (_i32, [_P, _P, _i32, _i32, _i32, _i32, ctypes.POINTER(_d),
                                 ctypes.POINTER(LanczosInfo), _P]),
     "ed_basis_count_noalloc": (_i32, [_i32, _i32, _i32, _i32, _P, _P, _P, ctypes.POINTER(_u64)]),
@@ -73,6 +75,7 @@ _SIGS = {
     "edx_force_generic": (None, [_i32]),
     "edx_force_all_rotations": (None, [_i32]),
     "edx_index_policy": (None, [_i32]),
+    "edx_peak": (_d, [_i32, _P, _u64, ctypes.POINTER(_d), _P]),
     "edx_basis_bucket": (_i32, [_P, ctypes.POINTER(_i32), ctypes.POINTER(ctypes.c_uint32)]),
     "edx_count_nnz": (_i32, [_P, _P, ctypes.POINTER(ctypes.c_ulonglong)]),
     "edx_force_prefix_search": (None, [_i32]),
@@ -301,6 +304,23 @@ def basis_bucket(basis: Basis):
     return bool(r == 1), bb.value, ns.value
 
 
+PEAK_KINDS = {"int32_mix": 0, "fp64_fma": 1, "fp32_fma": 2, "gather32": 3}
+
+
+def peak(kind: str, buf=None, stream=None):
+    """Measured ceiling of this GPU (diagnostics): "int32_mix" integer ops/s of
+    the group search's op mix (funnel shift, three-input logic, min, add),
+    "fp64_fma" / "fp32_fma" fused multiply-adds per second, "gather32" random
+    32-byte reads per second from the device tensor buf.  Returns (rate, ms)."""
+    ms = _d(0.0)
+    ptr = _ptr(buf) if buf is not None else ctypes.c_void_p(0)
+    nbytes = buf.numel() * buf.element_size() if buf is not None else 0
+    r = _lib.edx_peak(PEAK_KINDS[kind], ptr, nbytes, ctypes.byref(ms), _stream(stream))
+    if r < 0:
+        raise RuntimeError(f"edx_peak({kind}) failed")
+    return r, ms.value
+
+
 def count_nnz(op: Operator, basis: Basis) -> int:
     """Exact number of stored nonzeros of H in the sector (diagnostics)."""
     v = ctypes.c_ulonglong()
@@ -406,6 +426,20 @@ def lanczos_eigs(op: Operator, basis: Basis, x0, steps: int, n_eig: int, mode: i
     _check(_lib.ed_lanczos_eigs(op.handle, basis.handle, _ptr(x0), steps, mode, n_eig, eigs, float(tol),
                                 _ptr(vec_out) if vec_out is not None else None, ctypes.byref(info),
                                 _stream(stream)), "ed_lanczos_eigs")
+    return list(eigs[:n_eig]), LanczosResult(info.e0, info.steps, info.matvecs, info.ritz, info.residual,
+                                             info.matvec_ms)
+
+
+def lanczos_block(op: Operator, basis: Basis, x0, nvec: int, steps: int, mode: int = ED_LANCZOS_F32_MATVEC,
+                  n_eig: int = 0, vec_out=None, stream=None):
+    """Block Lanczos (ed_lanczos_block) from the [dim][nvec] fp64 start block x0:
+    (lowest n_eig Ritz values as a list, LanczosResult with the refined energy)."""
+    eigs = (ctypes.c_double * max(n_eig, 1))()
+    e0 = _d(0.0)
+    info = LanczosInfo()
+    _check(_lib.ed_lanczos_block(op.handle, basis.handle, _ptr(x0), nvec, steps, mode, n_eig, eigs,
+                                 ctypes.byref(e0), _ptr(vec_out) if vec_out is not None else None,
+                                 ctypes.byref(info), _stream(stream)), "ed_lanczos_block")
     return list(eigs[:n_eig]), LanczosResult(info.e0, info.steps, info.matvecs, info.ritz, info.residual,
                                              info.matvec_ms)
 
