@@ -11,6 +11,9 @@ namespace edk {
 // and frees are ordered on stream s; freed memory stays cached for later calls.
 cudaError_t ws_alloc(void **p, size_t bytes, cudaStream_t s);
 cudaError_t ws_free(void *p, cudaStream_t s);
+// Bytes the pool holds freed and ready for reuse (counted as free memory when
+// a solver decides whether its vectors fit).
+size_t ws_cached_bytes();
 
 // Kernel launches issued by the library since it was loaded (diagnostics).
 void count_launch(unsigned n = 1);

@@ -700,6 +700,7 @@ ed_status run_lanczos(const ed_operator *op, const ed_basis *b, const void *x0, 
     // store the Krylov basis if it fits in half of the free memory
     size_t free_b = 0, total_b = 0;
     cudaMemGetInfo(&free_b, &total_b);
+    free_b += ws_cached_bytes();
     const size_t vec_bytes = n * sizeof(D);
     const bool store = !recompute && (double)(steps + 1) * vec_bytes < 0.5 * (double)free_b;
     // push products are not bit-reproducible, so a recomputed pass would not

@@ -3,8 +3,8 @@
 // consume hundreds of products; one representative search and index lookup per
 // matrix element serves all p columns of a block).
 //
-// Recurrence (real sectors; blocks are [dim][p] fp64, interleaved like the
-// product's vectors):  V_1 R_0 = X0 (QR),
+// Recurrence (real sectors; blocks are [dim][p], interleaved like the
+// product's vectors, held as double-float pairs of fp32 arrays):  V_1 R_0 = X0 (QR),
 //   W = H V_j,  C = V_j^T W,  Cp = V_{j-1}^T W,  A_j = (C + C^T) / 2,
 //   W -= V_j C + V_{j-1} Cp,            (classical Gram-Schmidt against the two
 //                                        last blocks: Cp replaces B_j^T)
@@ -18,7 +18,9 @@
 //
 // Every reduction over the rows is a per-block partial in a fixed tile order,
 // merged by the last block to finish in block order with compensated (TwoSum)
-// merges, so both passes reproduce every coefficient bit for bit.
+// merges, so both passes reproduce every coefficient bit for bit.  The
+// per-element arithmetic is double-float on the fp32 pipe (see dd_acc); the
+// coefficient matrices, the tile sums and all merges are fp64.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -78,244 +80,468 @@ __device__ void merge_partials(const double2 *part, int E, double *out, unsigned
         *ticket = 0;
 }
 
-template <typename T> __device__ __forceinline__ double ld_up(const T *p) { return (double)*p; }
-
-// Stage rows [r0, r0 + kTileRows) of a [n][P] block into shared memory
-// (zeros past n); coalesced: consecutive threads read consecutive elements.
-template <int P, typename T>
-__device__ __forceinline__ void stage(double *sm, const T *g, uint64_t r0, uint64_t n)
+// ---- double-float arithmetic on the fp32 pipe --------------------------------
+// GB300's fp64 FMA rate is 1/74 of its fp32 rate (measured: 5.3e11 against
+// 3.9e13 per second), so the per-element arithmetic of the block kernels uses
+// pairs of floats (h + l, about 48 significant bits): error-free products by
+// FMA and TwoSum accumulation.  Coefficient matrices, tile sums and every
+// merge across threads and blocks stay fp64.
+__device__ __forceinline__ void dd_acc(float xh, float xl, float yh, float yl, float &s, float &c)
 {
-    const uint64_t base = r0 * P;
+    const float p = xh * yh;
+    float e = fmaf(xh, yh, -p);
+    e = fmaf(xh, yl, e);
+    e = fmaf(xl, yh, e);
+    const float t = s + p;
+    const float z = t - s;
+    c += ((s - (t - z)) + (p - z)) + e;
+    s = t;
+}
+
+__device__ __forceinline__ void dd_split(double x, float &h, float &l)
+{
+    h = (float)x;
+    l = (float)(x - (double)h);
+}
+
+// (h, l) += (s, c) as double-float numbers, renormalised
+__device__ __forceinline__ void dd_add(float &h, float &l, float s, float c)
+{
+    const float t = h + s;
+    const float z = t - h;
+    float e = (h - (t - z)) + (s - z);
+    e += l + c;
+    h = t + e;
+    l = e - (h - t);
+}
+
+// normalise s + c into h + l (|c| small against |s| after an accumulation)
+__device__ __forceinline__ void dd_norm(float s, float c, float &h, float &l)
+{
+    h = s + c;
+    l = c - (h - s);
+}
+
+// Tile staging.  Kind 0: fp32 array (low word 0); 1: fp64 array (split);
+// 2: double-float block (separate high and low float arrays).
+template <int P, int K>
+__device__ __forceinline__ void stage_dd(float *sh, float *sl, const void *gh, const float *gl, uint64_t r0,
+                                         uint64_t n)
+{
     const uint64_t lim = n * P;
     for (int e = threadIdx.x; e < kTileRows * P; e += blockDim.x) {
-        const uint64_t gi = base + (uint64_t)e;
-        sm[e] = gi < lim ? ld_up(g + gi) : 0.0;
+        const uint64_t gi = r0 * P + (uint64_t)e;
+        float h = 0.f, l = 0.f;
+        if (gi < lim) {
+            if (K == 0) {
+                h = reinterpret_cast<const float *>(gh)[gi];
+            } else if (K == 1) {
+                dd_split(reinterpret_cast<const double *>(gh)[gi], h, l);
+            } else {
+                h = reinterpret_cast<const float *>(gh)[gi];
+                l = gl[gi];
+            }
+        }
+        sh[e] = h;
+        sl[e] = l;
     }
 }
 
-// Gram of NM fp64 blocks X_m against Y: out[m][a][b] = sum_i X_m[i][a] Y[i][b].
-// A thread owns entries e = tid, tid + 256, ...; per tile it sums the tile's
-// rows in a register and adds that into a compensated running sum.
-template <int P, int NM, typename YT>
-__global__ void __launch_bounds__(kBlThreads) k_bl_gram(const double *X0, const double *X1, const YT *Y,
+// A tile's elements held in registers between the load of tile t + grid and
+// the shared-memory store at the top of the next iteration, so that the
+// global loads overlap the current tile's arithmetic.
+template <int P, int K>
+struct Prefetch {
+    static constexpr int kN = (kTileRows * P + kBlThreads - 1) / kBlThreads;
+    float h[kN], l[kN];
+    __device__ __forceinline__ void load(const void *gh, const float *gl, uint64_t r0, uint64_t n)
+    {
+        const uint64_t lim = n * P;
+#pragma unroll
+        for (int k = 0; k < kN; ++k) {
+            const int e = threadIdx.x + k * kBlThreads;
+            const uint64_t gi = r0 * P + (uint64_t)e;
+            h[k] = 0.f;
+            l[k] = 0.f;
+            if (e < kTileRows * P && gi < lim) {
+                if (K == 0) {
+                    h[k] = reinterpret_cast<const float *>(gh)[gi];
+                } else if (K == 1) {
+                    dd_split(reinterpret_cast<const double *>(gh)[gi], h[k], l[k]);
+                } else {
+                    h[k] = reinterpret_cast<const float *>(gh)[gi];
+                    l[k] = gl[gi];
+                }
+            }
+        }
+    }
+    __device__ __forceinline__ void store(float *sh, float *sl) const
+    {
+#pragma unroll
+        for (int k = 0; k < kN; ++k) {
+            const int e = threadIdx.x + k * kBlThreads;
+            if (e < kTileRows * P) {
+                sh[e] = h[k];
+                sl[e] = l[k];
+            }
+        }
+    }
+};
+
+// Gram entries of a tile: entries are taken in 2 x 2 groups (a0, a0+1) x
+// (b0, b0+1) of matrix m; a thread owns one group and a slice of the tile's
+// rows (rows sl, sl + SL, ...), sums its four entries over them in double-
+// float, adds the tile sums into renormalised double-float accumulators and
+// moves those into fp64 every kFlushTiles tiles (fp64 work per row stays
+// negligible; each double-float run spans at most kFlushTiles tile sums).
+constexpr int kFlushTiles = 64;
+
+struct GramAcc {
+    float h[4], l[4];
+    double d[4];
+    int tiles;
+    __device__ void init()
+    {
+        for (int k = 0; k < 4; ++k) {
+            h[k] = l[k] = 0.f;
+            d[k] = 0.0;
+        }
+        tiles = 0;
+    }
+    __device__ void flush()
+    {
+        for (int k = 0; k < 4; ++k) {
+            d[k] += (double)h[k] + (double)l[k];
+            h[k] = l[k] = 0.f;
+        }
+        tiles = 0;
+    }
+};
+template <int P, int NM>
+struct GramLayout {
+    static constexpr int kHalf = P / 2;
+    static constexpr int kGroups = NM * kHalf * kHalf;
+    static constexpr int kSlices = kBlThreads / kGroups;
+    static constexpr int E = NM * P * P;
+};
+
+template <int P, int NM, bool kYlow>
+__device__ __forceinline__ void gram_tile(const float *sxh, const float *sxl, const float *syh, const float *syl,
+                                          GramAcc &acc)
+{
+    using L = GramLayout<P, NM>;
+    const int grp = threadIdx.x % L::kGroups, sl = threadIdx.x / L::kGroups;
+    if (sl >= L::kSlices)
+        return;
+    const int m = grp / (L::kHalf * L::kHalf), rem = grp % (L::kHalf * L::kHalf);
+    const int a0 = 2 * (rem / L::kHalf), b0 = 2 * (rem % L::kHalf);
+    const float *xh = sxh + m * kTileRows * P, *xl = sxl + m * kTileRows * P;
+    float s[4] = {0.f, 0.f, 0.f, 0.f}, c[4] = {0.f, 0.f, 0.f, 0.f};
+    for (int r = sl; r < kTileRows; r += L::kSlices) {
+        const float x0h = xh[r * P + a0], x1h = xh[r * P + a0 + 1];
+        const float x0l = xl[r * P + a0], x1l = xl[r * P + a0 + 1];
+        const float y0h = syh[r * P + b0], y1h = syh[r * P + b0 + 1];
+        const float y0l = kYlow ? syl[r * P + b0] : 0.f, y1l = kYlow ? syl[r * P + b0 + 1] : 0.f;
+        dd_acc(x0h, x0l, y0h, y0l, s[0], c[0]);
+        dd_acc(x0h, x0l, y1h, y1l, s[1], c[1]);
+        dd_acc(x1h, x1l, y0h, y0l, s[2], c[2]);
+        dd_acc(x1h, x1l, y1h, y1l, s[3], c[3]);
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+        dd_add(acc.h[k], acc.l[k], s[k], c[k]);
+    if (++acc.tiles == kFlushTiles)
+        acc.flush();
+}
+
+// Per-block partials of the Gram entries: the slices' fp64 accumulators merged
+// in slice order (compensated) through shared memory; the last block to
+// finish merges the blocks into out.
+template <int P, int NM>
+__device__ void gram_finish(GramAcc &acc, double *red, double2 *part, unsigned int *ticket, double *out)
+{
+    using L = GramLayout<P, NM>;
+    const int grp = threadIdx.x % L::kGroups, sl = threadIdx.x / L::kGroups;
+    acc.flush();
+    __syncthreads();
+    if (sl < L::kSlices)
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+            red[(sl * L::kGroups + grp) * 4 + k] = acc.d[k];
+    __syncthreads();
+    for (int e = threadIdx.x; e < L::E; e += blockDim.x) {
+        const int m = e / (P * P), a = (e / P) % P, b = e % P;
+        const int g = m * L::kHalf * L::kHalf + (a / 2) * L::kHalf + b / 2, k = (a & 1) * 2 + (b & 1);
+        KS t{0.0, 0.0};
+        for (int q = 0; q < L::kSlices; ++q)
+            t = ks_add(t, red[(q * L::kGroups + g) * 4 + k]);
+        part[(size_t)blockIdx.x * L::E + e] = make_double2(t.s, t.c);
+    }
+    if (last_block(ticket))
+        merge_partials(part, L::E, out, ticket);
+}
+
+// Gram of NM double-float blocks X_m against Y (kind YK, see stage_dd):
+// out[m][a][b] = sum_i X_m[i][a] Y[i][b].
+template <int P, int NM, int YK>
+__global__ void __launch_bounds__(kBlThreads) k_dd_gram(const float *X0h, const float *X0l, const float *X1h,
+                                                        const float *X1l, const void *Yh, const float *Yl,
                                                         uint64_t n, double2 *part, unsigned int *ticket,
                                                         double *out, const int *stop)
 {
     if (*stop)
         return;
-    __shared__ double sx[NM][kTileRows * P];
-    __shared__ double sy[kTileRows * P];
-    constexpr int E = NM * P * P;
-    constexpr int EPT = (E + kBlThreads - 1) / kBlThreads;
-    KS acc[EPT];
-#pragma unroll
-    for (int q = 0; q < EPT; ++q)
-        acc[q] = KS{0.0, 0.0};
+    __shared__ float sxh[NM * kTileRows * P], sxl[NM * kTileRows * P];
+    __shared__ float syh[kTileRows * P], syl[kTileRows * P];
+    __shared__ double red[kBlThreads * 4];
+    GramAcc acc;
+    acc.init();
     const uint64_t tiles = (n + kTileRows - 1) / kTileRows;
-    for (uint64_t t = blockIdx.x; t < tiles; t += gridDim.x) {
-        const uint64_t r0 = t * kTileRows;
-        stage<P>(sx[0], X0, r0, n);
+    Prefetch<P, 2> p0, p1;
+    Prefetch<P, YK> py;
+    auto fetch = [&](uint64_t t) {
+        p0.load(X0h, X0l, t * kTileRows, n);
         if (NM > 1)
-            stage<P>(sx[NM - 1], X1, r0, n);
-        stage<P>(sy, Y, r0, n);
+            p1.load(X1h, X1l, t * kTileRows, n);
+        py.load(Yh, Yl, t * kTileRows, n);
+    };
+    if (blockIdx.x < tiles)
+        fetch(blockIdx.x);
+    for (uint64_t t = blockIdx.x; t < tiles; t += gridDim.x) {
+        p0.store(sxh, sxl);
+        if (NM > 1)
+            p1.store(sxh + kTileRows * P, sxl + kTileRows * P);
+        py.store(syh, syl);
         __syncthreads();
-#pragma unroll
-        for (int q = 0; q < EPT; ++q) {
-            const int e = threadIdx.x + q * kBlThreads;
-            if (e < E) {
-                const int m = e / (P * P), a = (e / P) % P, b = e % P;
-                double s = 0.0;
-#pragma unroll 8
-                for (int r = 0; r < kTileRows; ++r)
-                    s = fma(sx[m][r * P + a], sy[r * P + b], s);
-                acc[q] = ks_add(acc[q], s);
-            }
-        }
+        if (t + gridDim.x < tiles)
+            fetch(t + gridDim.x);
+        gram_tile<P, NM, YK != 0>(sxh, sxl, syh, syl, acc);
         __syncthreads();
     }
-#pragma unroll
-    for (int q = 0; q < EPT; ++q) {
-        const int e = threadIdx.x + q * kBlThreads;
-        if (e < E)
-            part[(size_t)blockIdx.x * E + e] = make_double2(acc[q].s, acc[q].c);
-    }
-    if (last_block(ticket))
-        merge_partials(part, E, out, ticket);
+    gram_finish<P, NM>(acc, red, part, ticket, out);
 }
 
-// W = Y - X0 C0 - X1 C1 (C read from device memory, P x P row-major: W[i][b]
-// -= sum_a X[i][a] C[a][b]); W may alias X1 (a tile is read completely before
-// it is written).  With G: Gram partials of W^T W, merged into G by the last block.
-template <int P, int NM, typename YT>
-__global__ void __launch_bounds__(kBlThreads) k_bl_update(const double *X0, const double *X1, const YT *Y,
-                                                          const double *C, double *W, uint64_t n,
+// W = Y - X0 C0 - X1 C1 (C fp64, P x P row-major per matrix: W[i][b] -=
+// sum_a X[i][a] C[a][b]), written as a double-float block; W may alias X1 or
+// Y (a tile is staged completely before it is written).  With G: Gram of W.
+template <int P, int NM, int YK>
+__global__ void __launch_bounds__(kBlThreads) k_dd_update(const float *X0h, const float *X0l, const float *X1h,
+                                                          const float *X1l, const void *Yh, const float *Yl,
+                                                          const double *C, float *Wh, float *Wl, uint64_t n,
                                                           double2 *part, unsigned int *ticket, double *G,
                                                           const int *stop)
 {
     if (*stop)
         return;
-    __shared__ double sx[NM][kTileRows * P];
-    __shared__ double sw[kTileRows * P];
-    __shared__ double sc[NM * P * P];
+    __shared__ float sxh[NM * kTileRows * P], sxl[NM * kTileRows * P];
+    __shared__ float swh[kTileRows * P], swl[kTileRows * P];
+    __shared__ float sch[NM * P * P], scl[NM * P * P];
+    __shared__ double red[kBlThreads * 4];
     for (int e = threadIdx.x; e < NM * P * P; e += blockDim.x)
-        sc[e] = C[e];
-    constexpr int E = P * P;
-    constexpr int EPT = (E + kBlThreads - 1) / kBlThreads;
-    KS acc[EPT];
-#pragma unroll
-    for (int q = 0; q < EPT; ++q)
-        acc[q] = KS{0.0, 0.0};
+        dd_split(-C[e], sch[e], scl[e]);
+    GramAcc acc;
+    acc.init();
     const uint64_t tiles = (n + kTileRows - 1) / kTileRows;
+    const uint64_t lim = n * P;
+    Prefetch<P, 2> p0, p1;
+    Prefetch<P, YK> py;
+    auto fetch = [&](uint64_t t) {
+        p0.load(X0h, X0l, t * kTileRows, n);
+        if (NM > 1)
+            p1.load(X1h, X1l, t * kTileRows, n);
+        py.load(Yh, Yl, t * kTileRows, n);
+    };
+    if (blockIdx.x < tiles)
+        fetch(blockIdx.x);
     for (uint64_t t = blockIdx.x; t < tiles; t += gridDim.x) {
         const uint64_t r0 = t * kTileRows;
-        stage<P>(sx[0], X0, r0, n);
+        p0.store(sxh, sxl);
         if (NM > 1)
-            stage<P>(sx[NM - 1], X1, r0, n);
-        stage<P>(sw, Y, r0, n);
+            p1.store(sxh + kTileRows * P, sxl + kTileRows * P);
+        py.store(swh, swl);
         __syncthreads();
-        for (int e = threadIdx.x; e < kTileRows * P; e += blockDim.x) {
-            const int r = e / P, b = e % P;
-            double w = sw[e];
+        // the next tile's loads are issued now; W may alias X1 or Y, but a
+        // tile is only written by the block that staged it, after staging
+        if (t + gridDim.x < tiles)
+            fetch(t + gridDim.x);
+        {
+            constexpr int kE = (kTileRows * P + kBlThreads - 1) / kBlThreads;
+            float s[kE], c[kE];
+#pragma unroll
+            for (int k = 0; k < kE; ++k) {
+                const int e = threadIdx.x + k * kBlThreads;
+                s[k] = e < kTileRows * P ? swh[e] : 0.f;
+                c[k] = e < kTileRows * P ? swl[e] : 0.f;
+            }
 #pragma unroll
             for (int m = 0; m < NM; ++m)
 #pragma unroll
                 for (int a = 0; a < P; ++a)
-                    w = fma(-sx[m][r * P + a], sc[m * P * P + a * P + b], w);
-            sw[e] = w;
-        }
-        __syncthreads();
-        const uint64_t lim = n * P;
-        for (int e = threadIdx.x; e < kTileRows * P; e += blockDim.x) {
-            const uint64_t gi = r0 * P + (uint64_t)e;
-            if (gi < lim)
-                W[gi] = sw[e];
-        }
-        if (G) {
 #pragma unroll
-            for (int q = 0; q < EPT; ++q) {
-                const int e = threadIdx.x + q * kBlThreads;
-                if (e < E) {
-                    const int a = e / P, b = e % P;
-                    double s = 0.0;
-#pragma unroll 8
-                    for (int r = 0; r < kTileRows; ++r)
-                        s = fma(sw[r * P + a], sw[r * P + b], s);
-                    acc[q] = ks_add(acc[q], s);
-                }
+                    for (int k = 0; k < kE; ++k) {
+                        const int e = threadIdx.x + k * kBlThreads;
+                        if (e < kTileRows * P) {
+                            const int r = e / P, b = e % P;
+                            dd_acc(sxh[m * kTileRows * P + r * P + a], sxl[m * kTileRows * P + r * P + a],
+                                   sch[m * P * P + a * P + b], scl[m * P * P + a * P + b], s[k], c[k]);
+                        }
+                    }
+            __syncthreads();  // every element of the tile is read before any is overwritten
+#pragma unroll
+            for (int k = 0; k < kE; ++k) {
+                const int e = threadIdx.x + k * kBlThreads;
+                if (e < kTileRows * P)
+                    dd_norm(s[k], c[k], swh[e], swl[e]);
             }
         }
         __syncthreads();
+        for (int e = threadIdx.x; e < kTileRows * P; e += blockDim.x) {
+            const uint64_t gi = r0 * P + (uint64_t)e;
+            if (gi < lim) {
+                Wh[gi] = swh[e];
+                Wl[gi] = swl[e];
+            }
+        }
+        if (G)
+            gram_tile<P, 1, true>(swh, swl, swh, swl, acc);
+        __syncthreads();
     }
-    if (!G)
-        return;
-#pragma unroll
-    for (int q = 0; q < EPT; ++q) {
-        const int e = threadIdx.x + q * kBlThreads;
-        if (e < E)
-            part[(size_t)blockIdx.x * E + e] = make_double2(acc[q].s, acc[q].c);
-    }
-    if (last_block(ticket))
-        merge_partials(part, E, G, ticket);
+    if (G)
+        gram_finish<P, 1>(acc, red, part, ticket, G);
 }
 
-// Z = W R1i (R1i upper triangular, row-major); kApply = false: Gram partials
-// of Z^T Z merged into G2; kApply = true: V = Z R2i written over W, with its
-// fp32 copy V32 (may be null).  Z is formed identically in both.
+// Z = W R1i (R1i fp64 upper triangular, row-major); kApply = false: Gram of
+// Z merged into G2; kApply = true: V = Z R2i written over W.  Z is formed
+// identically in both.
 template <int P, bool kApply>
-__global__ void __launch_bounds__(kBlThreads) k_bl_qr(double *W, const double *R1i, const double *R2i,
-                                                      float *V32, uint64_t n, double2 *part,
-                                                      unsigned int *ticket, double *G2, const int *stop)
+__global__ void __launch_bounds__(kBlThreads) k_dd_qr(float *Wh, float *Wl, const double *R1i, const double *R2i,
+                                                      uint64_t n, double2 *part, unsigned int *ticket,
+                                                      double *G2, const int *stop)
 {
     if (*stop)
         return;
-    __shared__ double sw[kTileRows * P];
-    __shared__ double sz[kTileRows * P];
-    __shared__ double s1[P * P], s2[P * P];
+    __shared__ float swh[kTileRows * P], swl[kTileRows * P];
+    __shared__ float szh[kTileRows * P], szl[kTileRows * P];
+    __shared__ float s1h[P * P], s1l[P * P], s2h[P * P], s2l[P * P];
+    __shared__ double red[kBlThreads * 4];
     for (int e = threadIdx.x; e < P * P; e += blockDim.x) {
-        s1[e] = R1i[e];
+        dd_split(R1i[e], s1h[e], s1l[e]);
         if (kApply)
-            s2[e] = R2i[e];
+            dd_split(R2i[e], s2h[e], s2l[e]);
     }
-    constexpr int E = P * P;
-    constexpr int EPT = (E + kBlThreads - 1) / kBlThreads;
-    KS acc[EPT];
-#pragma unroll
-    for (int q = 0; q < EPT; ++q)
-        acc[q] = KS{0.0, 0.0};
+    GramAcc acc;
+    acc.init();
     const uint64_t tiles = (n + kTileRows - 1) / kTileRows;
     const uint64_t lim = n * P;
+    Prefetch<P, 2> pw;
+    if (blockIdx.x < tiles)
+        pw.load(Wh, Wl, (uint64_t)blockIdx.x * kTileRows, n);
     for (uint64_t t = blockIdx.x; t < tiles; t += gridDim.x) {
         const uint64_t r0 = t * kTileRows;
-        stage<P>(sw, W, r0, n);
+        pw.store(swh, swl);
         __syncthreads();
-        for (int e = threadIdx.x; e < kTileRows * P; e += blockDim.x) {
-            const int r = e / P, b = e % P;
-            double z = 0.0;
-            for (int a = 0; a <= b; ++a)
-                z = fma(sw[r * P + a], s1[a * P + b], z);
-            sz[e] = z;
+        if (t + gridDim.x < tiles)
+            pw.load(Wh, Wl, (t + gridDim.x) * kTileRows, n);
+        // the entries of R1i / R2i below the diagonal are exact zeros, for
+        // which dd_acc is an exact no-op: full unrolled loops, no divergence
+        // between the columns b of a warp, the thread's elements interleaved
+        constexpr int kE = (kTileRows * P + kBlThreads - 1) / kBlThreads;
+        {
+            float s[kE], c[kE];
+#pragma unroll
+            for (int k = 0; k < kE; ++k)
+                s[k] = c[k] = 0.f;
+#pragma unroll
+            for (int a = 0; a < P; ++a)
+#pragma unroll
+                for (int k = 0; k < kE; ++k) {
+                    const int e = threadIdx.x + k * kBlThreads;
+                    if (e < kTileRows * P) {
+                        const int r = e / P, b = e % P;
+                        dd_acc(swh[r * P + a], swl[r * P + a], s1h[a * P + b], s1l[a * P + b], s[k], c[k]);
+                    }
+                }
+#pragma unroll
+            for (int k = 0; k < kE; ++k) {
+                const int e = threadIdx.x + k * kBlThreads;
+                if (e < kTileRows * P)
+                    dd_norm(s[k], c[k], szh[e], szl[e]);
+            }
         }
         __syncthreads();
         if (kApply) {
-            for (int e = threadIdx.x; e < kTileRows * P; e += blockDim.x) {
-                const int r = e / P, b = e % P;
-                double v = 0.0;
-                for (int a = 0; a <= b; ++a)
-                    v = fma(sz[r * P + a], s2[a * P + b], v);
+            float s[kE], c[kE];
+#pragma unroll
+            for (int k = 0; k < kE; ++k)
+                s[k] = c[k] = 0.f;
+#pragma unroll
+            for (int a = 0; a < P; ++a)
+#pragma unroll
+                for (int k = 0; k < kE; ++k) {
+                    const int e = threadIdx.x + k * kBlThreads;
+                    if (e < kTileRows * P) {
+                        const int r = e / P, b = e % P;
+                        dd_acc(szh[r * P + a], szl[r * P + a], s2h[a * P + b], s2l[a * P + b], s[k], c[k]);
+                    }
+                }
+#pragma unroll
+            for (int k = 0; k < kE; ++k) {
+                const int e = threadIdx.x + k * kBlThreads;
                 const uint64_t gi = r0 * P + (uint64_t)e;
-                if (gi < lim) {
-                    W[gi] = v;
-                    if (V32)
-                        V32[gi] = (float)v;
+                if (e < kTileRows * P && gi < lim) {
+                    float h, l;
+                    dd_norm(s[k], c[k], h, l);
+                    Wh[gi] = h;
+                    Wl[gi] = l;
                 }
             }
         } else {
-#pragma unroll
-            for (int q = 0; q < EPT; ++q) {
-                const int e = threadIdx.x + q * kBlThreads;
-                if (e < E) {
-                    const int a = e / P, b = e % P;
-                    double s = 0.0;
-#pragma unroll 8
-                    for (int r = 0; r < kTileRows; ++r)
-                        s = fma(sz[r * P + a], sz[r * P + b], s);
-                    acc[q] = ks_add(acc[q], s);
-                }
-            }
+            gram_tile<P, 1, true>(szh, szl, szh, szl, acc);
         }
         __syncthreads();
     }
-    if (kApply)
-        return;
-#pragma unroll
-    for (int q = 0; q < EPT; ++q) {
-        const int e = threadIdx.x + q * kBlThreads;
-        if (e < E)
-            part[(size_t)blockIdx.x * E + e] = make_double2(acc[q].s, acc[q].c);
-    }
-    if (last_block(ticket))
-        merge_partials(part, E, G2, ticket);
+    if (!kApply)
+        gram_finish<P, 1>(acc, red, part, ticket, G2);
 }
 
-// psi (dim) += V_j s_j  (s_j = y[j P .. j P + P)), psi zeroed when first
+// psi (double-float, dim) += V_j s_j  (s_j = y[j P .. j P + P) in fp64); psi
+// starts from zero when first
 template <int P>
-__global__ void k_bl_ritz_acc(double *psi, const double *V, const double *y, int j, uint64_t n, int first,
-                              const int *m_eff)
+__global__ void k_dd_ritz_acc(float *ph, float *pl, const float *Vh, const float *Vl, const double *y, int j,
+                              uint64_t n, int first, const int *m_eff)
 {
     if (j >= *m_eff)
         return;
-    double c[P];
+    float ch[P], cl[P];
 #pragma unroll
     for (int a = 0; a < P; ++a)
-        c[a] = y[j * P + a];
+        dd_split(y[j * P + a], ch[a], cl[a]);
     for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (uint64_t)gridDim.x * blockDim.x) {
-        double acc = first ? 0.0 : psi[i];
+        float s = first ? 0.f : ph[i], c = first ? 0.f : pl[i];
 #pragma unroll
         for (int a = 0; a < P; ++a)
-            acc = fma(V[i * P + a], c[a], acc);
-        psi[i] = acc;
+            dd_acc(Vh[i * P + a], Vl[i * P + a], ch[a], cl[a], s, c);
+        float h, l;
+        dd_norm(s, c, h, l);
+        ph[i] = h;
+        pl[i] = l;
     }
+}
+
+// fp64 <-> double-float conversions of whole arrays
+__global__ void k_f64_to_dd(const double *x, float *h, float *l, uint64_t count)
+{
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count;
+         i += (uint64_t)gridDim.x * blockDim.x)
+        dd_split(x[i], h[i], l[i]);
+}
+
+__global__ void k_dd_to_f64(const float *h, const float *l, double *x, uint64_t count)
+{
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count;
+         i += (uint64_t)gridDim.x * blockDim.x)
+        x[i] = (double)h[i] + (double)l[i];
 }
 
 // Cholesky of the P x P symmetric matrix G (row-major): G = R^T R, R upper
@@ -564,6 +790,41 @@ struct Pool {
         }                                                                   \
     } while (0)
 
+// Launch helpers for the product output kind (0: fp32, 1: fp64) and the
+// number of earlier blocks (1 or 2) the new one is orthogonalised against.
+template <int P>
+void launch_gram(int nm, int yk, const float *X0h, const float *X0l, const float *X1h, const float *X1l,
+                 const void *Yh, const float *Yl, uint64_t n, int grid, double2 *part, unsigned int *ticket,
+                 double *out, const int *stop, cudaStream_t st)
+{
+#define ED_DD_GRAM(NM, YK) \
+    k_dd_gram<P, NM, YK><<<grid, kBlThreads, 0, st>>>(X0h, X0l, X1h, X1l, Yh, Yl, n, part, ticket, out, stop)
+    if (nm == 1) {
+        if (yk == 0) ED_DD_GRAM(1, 0); else if (yk == 1) ED_DD_GRAM(1, 1); else ED_DD_GRAM(1, 2);
+    } else {
+        if (yk == 0) ED_DD_GRAM(2, 0); else if (yk == 1) ED_DD_GRAM(2, 1); else ED_DD_GRAM(2, 2);
+    }
+#undef ED_DD_GRAM
+    count_launch();
+}
+
+template <int P>
+void launch_update(int nm, int yk, const float *X0h, const float *X0l, const float *X1h, const float *X1l,
+                   const void *Yh, const float *Yl, const double *C, float *Wh, float *Wl, uint64_t n, int grid,
+                   double2 *part, unsigned int *ticket, double *G, const int *stop, cudaStream_t st)
+{
+#define ED_DD_UPD(NM, YK)                                                                                  \
+    k_dd_update<P, NM, YK><<<grid, kBlThreads, 0, st>>>(X0h, X0l, X1h, X1l, Yh, Yl, C, Wh, Wl, n, part, ticket, \
+                                                        G, stop)
+    if (nm == 1) {
+        if (yk == 0) ED_DD_UPD(1, 0); else if (yk == 1) ED_DD_UPD(1, 1); else ED_DD_UPD(1, 2);
+    } else {
+        if (yk == 0) ED_DD_UPD(2, 0); else if (yk == 1) ED_DD_UPD(2, 1); else ED_DD_UPD(2, 2);
+    }
+#undef ED_DD_UPD
+    count_launch();
+}
+
 template <int P>
 ed_status run_block(const ed_operator *op, const ed_basis *b, const double *x0, int steps, bool f32, bool reorth,
                     int n_eig, double *eigs_out, double *psi_out, int *steps_out, int *matvecs_out,
@@ -579,28 +840,30 @@ ed_status run_block(const ed_operator *op, const ed_basis *b, const double *x0, 
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const uint64_t tiles = (n + kTileRows - 1) / kTileRows;
     const int grid = (int)std::max<uint64_t>(1, std::min<uint64_t>((uint64_t)sms * 4, tiles));
+    const int vgrid = (int)std::max<uint64_t>(1, std::min<uint64_t>((uint64_t)sms * 8, (n + 255) / 256));
     const size_t blk = (size_t)n * P;
 
     Pool S(st);
-    double *Vb[2] = {nullptr, nullptr}, *W64 = nullptr, *A = nullptr, *B = nullptr, *sm = nullptr;
+    // blocks as double-float (high and low float arrays); the high array is
+    // the fp32 copy the products read
+    float *Vh = nullptr, *Vl = nullptr;  // 2 blocks (ring), or steps + 1 (kept)
+    const int nblocks = reorth ? steps + 1 : 2;
+    float *W32 = nullptr, *ph = nullptr, *pl = nullptr;
+    double *V64 = nullptr, *W64 = nullptr, *A = nullptr, *B = nullptr, *sm = nullptr;
     double *y = nullptr, *eig = nullptr, *scr = nullptr;
-    float *V32 = nullptr, *W32 = nullptr;
     double2 *part = nullptr;
     unsigned int *tickets = nullptr;
     int *flags = nullptr;  // [0] stop, [1] m_eff (running), [2] m_eff of the main pass
-    double *Vall = nullptr;  // every block (reorthogonalisation), steps + 1 of them
-    if (reorth) {
-        ED_BL_TRY(S.get(&Vall, (size_t)(steps + 1) * blk));
-    } else {
-        ED_BL_TRY(S.get(&Vb[0], blk));
-        ED_BL_TRY(S.get(&Vb[1], blk));
-    }
+    ED_BL_TRY(S.get(&Vh, (size_t)nblocks * blk));
+    ED_BL_TRY(S.get(&Vl, (size_t)nblocks * blk));
     if (f32) {
-        ED_BL_TRY(S.get(&V32, blk));
         ED_BL_TRY(S.get(&W32, blk));
     } else {
+        ED_BL_TRY(S.get(&V64, blk));
         ED_BL_TRY(S.get(&W64, blk));
     }
+    ED_BL_TRY(S.get(&ph, n));
+    ED_BL_TRY(S.get(&pl, n));
     ED_BL_TRY(S.get(&A, (size_t)(steps + 1) * P * P));
     ED_BL_TRY(S.get(&B, (size_t)(steps + 2) * P * P));
     ED_BL_TRY(S.get(&sm, 8 * P * P));
@@ -624,171 +887,76 @@ ed_status run_block(const ed_operator *op, const ed_basis *b, const double *x0, 
         ev.push_back(e);
         return cudaEventRecord(e, st);
     };
-    const ed_dtype dt = f32 ? ED_F32 : ED_F64;
     double *C = sm, *G = sm + 2 * P * P, *R1i = sm + 4 * P * P, *G2 = sm + 5 * P * P, *R2i = sm + 7 * P * P;
     int *stop = flags;
+    const int yk = f32 ? 0 : 1;
+    const void *Yh = f32 ? (const void *)W32 : (const void *)W64;
+    auto bh = [&](int k) { return Vh + (size_t)(reorth ? k : (k & 1)) * blk; };
+    auto bl = [&](int k) { return Vl + (size_t)(reorth ? k : (k & 1)) * blk; };
 
-    // QR of the block in Vb[k] in place (Cholesky QR, twice); V32 refreshed
-    auto qr_inplace = [&](double *Wb, int j) {
-        k_bl_qr<P, false><<<grid, kBlThreads, 0, st>>>(Wb, R1i, nullptr, nullptr, n, part, tickets + 2, G2,
-                                                       stop); count_launch();
+    // Cholesky QR (twice) of the block (wh, wl) in place; R1 already in sm
+    auto qr = [&](float *wh, float *wl, int j) {
+        k_dd_qr<P, false><<<grid, kBlThreads, 0, st>>>(wh, wl, R1i, nullptr, n, part, tickets + 2, G2, stop);
+        count_launch();
         k_bl_small<P><<<1, 32, 0, st>>>(sm, A, B, j, 2, stop, flags + 1); count_launch();
-        k_bl_qr<P, true><<<grid, kBlThreads, 0, st>>>(Wb, R1i, R2i, V32, n, part, tickets + 2, nullptr,
-                                                      stop); count_launch();
+        k_dd_qr<P, true><<<grid, kBlThreads, 0, st>>>(wh, wl, R1i, R2i, n, part, tickets + 2, nullptr, stop);
+        count_launch();
     };
 
-    // One pass of `steps` block steps from x0.  With acc, psi += V_j s_j.
+    // One pass of `steps` block steps from x0; with acc, psi += V_j s_j.
     auto pass = [&](bool acc) -> cudaError_t {
         cudaError_t e = cudaMemsetAsync(flags, 0, 2 * sizeof(int), st);
         if (e != cudaSuccess)
             return e;
-        // start block: V_1 = QR(X0)
-        if ((e = cudaMemcpyAsync(Vb[0], x0, blk * sizeof(double), cudaMemcpyDeviceToDevice, st)) != cudaSuccess)
-            return e;
-        k_bl_gram<P, 1, double><<<grid, kBlThreads, 0, st>>>(Vb[0], nullptr, Vb[0], n, part, tickets, G,
-                                                             stop); count_launch();
+        k_f64_to_dd<<<vgrid, 256, 0, st>>>(x0, bh(0), bl(0), blk); count_launch();
+        launch_gram<P>(1, 2, bh(0), bl(0), nullptr, nullptr, bh(0), bl(0), n, grid, part, tickets, G, stop, st);
         k_bl_small<P><<<1, 32, 0, st>>>(sm, A, B, -1, 1, stop, flags + 1); count_launch();
-        k_bl_qr<P, false><<<grid, kBlThreads, 0, st>>>(Vb[0], R1i, nullptr, nullptr, n, part, tickets + 2, G2,
-                                                       stop); count_launch();
-        k_bl_small<P><<<1, 32, 0, st>>>(sm, A, B, -1, 2, stop, flags + 1); count_launch();
-        k_bl_qr<P, true><<<grid, kBlThreads, 0, st>>>(Vb[0], R1i, R2i, V32, n, part, tickets + 2, nullptr,
-                                                      stop); count_launch();
-        int cur = 0;
+        qr(bh(0), bl(0), -1);
         for (int j = 0; j < steps; ++j) {
-            double *V = Vb[cur], *Vp = Vb[cur ^ 1];
-            if (acc) {
-                k_bl_ritz_acc<P><<<grid, kBlThreads, 0, st>>>(psi_out, V, y, j, n, j == 0, flags + 2);
+            float *Vjh = bh(j), *Vjl = bl(j);
+            const float *Vph = j ? bh(j - 1) : nullptr, *Vpl = j ? bl(j - 1) : nullptr;
+            float *Wh = bh(j + 1), *Wl = bl(j + 1);  // the ring's V_{j-1} buffer, or kept block j + 1
+            if (acc && !reorth) {
+                k_dd_ritz_acc<P><<<vgrid, 256, 0, st>>>(ph, pl, Vjh, Vjl, y, j, n, j == 0, flags + 2);
                 count_launch();
             }
-            // W = H V_j (stopped recurrences still run the product: it is
-            // only skipped work for a sector smaller than the block space)
+            // W = H V_j (a stopped recurrence still runs the product: wasted
+            // work only when the sector is smaller than the block space)
             ++matvecs;
             if ((e = mark()) != cudaSuccess)
                 return e;
-            e = launch_matvec(ov, gv, iv, track, f32 ? (const void *)V32 : (const void *)V,
-                              f32 ? (void *)W32 : (void *)W64, P, dt, st);
+            if (!f32) {
+                k_dd_to_f64<<<vgrid, 256, 0, st>>>(Vjh, Vjl, V64, blk); count_launch();
+            }
+            e = launch_matvec(ov, gv, iv, track, f32 ? (const void *)Vjh : (const void *)V64,
+                              f32 ? (void *)W32 : (void *)W64, P, f32 ? ED_F32 : ED_F64, st);
             if (e != cudaSuccess)
                 return e;
             if ((e = mark()) != cudaSuccess)
                 return e;
-            if (f32) {
-                if (j == 0)
-                    k_bl_gram<P, 1, float><<<grid, kBlThreads, 0, st>>>(V, nullptr, W32, n, part, tickets, C,
-                                                                        stop);
-                else
-                    k_bl_gram<P, 2, float><<<grid, kBlThreads, 0, st>>>(V, Vp, W32, n, part, tickets, C, stop);
-                count_launch();
-                k_bl_small<P><<<1, 32, 0, st>>>(sm, A, B, j, 0, stop, flags + 1); count_launch();
-                if (j == 0)
-                    k_bl_update<P, 1, float><<<grid, kBlThreads, 0, st>>>(V, nullptr, W32, C, Vp, n, part,
-                                                                          tickets + 1, G, stop);
-                else
-                    k_bl_update<P, 2, float><<<grid, kBlThreads, 0, st>>>(V, Vp, W32, C, Vp, n, part,
-                                                                          tickets + 1, G, stop);
-                count_launch();
-            } else {
-                if (j == 0)
-                    k_bl_gram<P, 1, double><<<grid, kBlThreads, 0, st>>>(V, nullptr, W64, n, part, tickets, C,
-                                                                         stop);
-                else
-                    k_bl_gram<P, 2, double><<<grid, kBlThreads, 0, st>>>(V, Vp, W64, n, part, tickets, C,
-                                                                         stop);
-                count_launch();
-                k_bl_small<P><<<1, 32, 0, st>>>(sm, A, B, j, 0, stop, flags + 1); count_launch();
-                if (j == 0)
-                    k_bl_update<P, 1, double><<<grid, kBlThreads, 0, st>>>(V, nullptr, W64, C, Vp, n, part,
-                                                                           tickets + 1, G, stop);
-                else
-                    k_bl_update<P, 2, double><<<grid, kBlThreads, 0, st>>>(V, Vp, W64, C, Vp, n, part,
-                                                                           tickets + 1, G, stop);
-                count_launch();
+            const int nm = j ? 2 : 1;
+            launch_gram<P>(nm, yk, Vjh, Vjl, Vph, Vpl, Yh, nullptr, n, grid, part, tickets, C, stop, st);
+            k_bl_small<P><<<1, 32, 0, st>>>(sm, A, B, j, 0, stop, flags + 1); count_launch();
+            launch_update<P>(nm, yk, Vjh, Vjl, Vph, Vpl, Yh, nullptr, C, Wh, Wl, n, grid, part, tickets + 1,
+                             reorth ? nullptr : G, stop, st);
+            if (reorth) {  // against every kept block, block modified Gram-Schmidt, twice
+                for (int rep = 0; rep < 2; ++rep)
+                    for (int i = 0; i <= j; ++i) {
+                        launch_gram<P>(1, 2, bh(i), bl(i), nullptr, nullptr, Wh, Wl, n, grid, part, tickets, C,
+                                       stop, st);
+                        launch_update<P>(1, 2, bh(i), bl(i), nullptr, nullptr, Wh, Wl, C, Wh, Wl, n, grid, part,
+                                         tickets + 1, nullptr, stop, st);
+                    }
+                launch_gram<P>(1, 2, Wh, Wl, nullptr, nullptr, Wh, Wl, n, grid, part, tickets, G, stop, st);
             }
             k_bl_small<P><<<1, 32, 0, st>>>(sm, A, B, j, 1, stop, flags + 1); count_launch();
-            qr_inplace(Vp, j);  // V_{j+1} in the buffer of V_{j-1}
-            cur ^= 1;
+            qr(Wh, Wl, j);
         }
         return cudaGetLastError();
     };
 
-    // With every block kept: W is orthogonalised against all earlier blocks
-    // (block modified Gram-Schmidt, twice) and the Ritz vector is combined
-    // from the kept blocks.
-    auto pass_store = [&]() -> cudaError_t {
-        cudaError_t e = cudaMemsetAsync(flags, 0, 2 * sizeof(int), st);
-        if (e != cudaSuccess)
-            return e;
-        if ((e = cudaMemcpyAsync(Vall, x0, blk * sizeof(double), cudaMemcpyDeviceToDevice, st)) != cudaSuccess)
-            return e;
-        k_bl_gram<P, 1, double><<<grid, kBlThreads, 0, st>>>(Vall, nullptr, Vall, n, part, tickets, G,
-                                                             stop); count_launch();
-        k_bl_small<P><<<1, 32, 0, st>>>(sm, A, B, -1, 1, stop, flags + 1); count_launch();
-        k_bl_qr<P, false><<<grid, kBlThreads, 0, st>>>(Vall, R1i, nullptr, nullptr, n, part, tickets + 2, G2,
-                                                       stop); count_launch();
-        k_bl_small<P><<<1, 32, 0, st>>>(sm, A, B, -1, 2, stop, flags + 1); count_launch();
-        k_bl_qr<P, true><<<grid, kBlThreads, 0, st>>>(Vall, R1i, R2i, V32, n, part, tickets + 2, nullptr,
-                                                      stop); count_launch();
-        for (int j = 0; j < steps; ++j) {
-            double *V = Vall + (size_t)j * blk, *Vp = j ? V - blk : nullptr, *Wn = V + blk;
-            ++matvecs;
-            if ((e = mark()) != cudaSuccess)
-                return e;
-            e = launch_matvec(ov, gv, iv, track, f32 ? (const void *)V32 : (const void *)V,
-                              f32 ? (void *)W32 : (void *)W64, P, dt, st);
-            if (e != cudaSuccess)
-                return e;
-            if ((e = mark()) != cudaSuccess)
-                return e;
-            if (f32) {
-                if (j == 0)
-                    k_bl_gram<P, 1, float><<<grid, kBlThreads, 0, st>>>(V, nullptr, W32, n, part, tickets, C,
-                                                                        stop);
-                else
-                    k_bl_gram<P, 2, float><<<grid, kBlThreads, 0, st>>>(V, Vp, W32, n, part, tickets, C, stop);
-                count_launch();
-                k_bl_small<P><<<1, 32, 0, st>>>(sm, A, B, j, 0, stop, flags + 1); count_launch();
-                if (j == 0)
-                    k_bl_update<P, 1, float><<<grid, kBlThreads, 0, st>>>(V, nullptr, W32, C, Wn, n, part,
-                                                                          tickets + 1, nullptr, stop);
-                else
-                    k_bl_update<P, 2, float><<<grid, kBlThreads, 0, st>>>(V, Vp, W32, C, Wn, n, part,
-                                                                          tickets + 1, nullptr, stop);
-            } else {
-                if (j == 0)
-                    k_bl_gram<P, 1, double><<<grid, kBlThreads, 0, st>>>(V, nullptr, W64, n, part, tickets, C,
-                                                                         stop);
-                else
-                    k_bl_gram<P, 2, double><<<grid, kBlThreads, 0, st>>>(V, Vp, W64, n, part, tickets, C,
-                                                                         stop);
-                count_launch();
-                k_bl_small<P><<<1, 32, 0, st>>>(sm, A, B, j, 0, stop, flags + 1); count_launch();
-                if (j == 0)
-                    k_bl_update<P, 1, double><<<grid, kBlThreads, 0, st>>>(V, nullptr, W64, C, Wn, n, part,
-                                                                           tickets + 1, nullptr, stop);
-                else
-                    k_bl_update<P, 2, double><<<grid, kBlThreads, 0, st>>>(V, Vp, W64, C, Wn, n, part,
-                                                                           tickets + 1, nullptr, stop);
-            }
-            count_launch();
-            for (int rep = 0; rep < 2; ++rep)
-                for (int i = 0; i <= j; ++i) {
-                    const double *Vi = Vall + (size_t)i * blk;
-                    k_bl_gram<P, 1, double><<<grid, kBlThreads, 0, st>>>(Vi, nullptr, Wn, n, part, tickets, C,
-                                                                         stop); count_launch();
-                    k_bl_update<P, 1, double><<<grid, kBlThreads, 0, st>>>(Vi, nullptr, Wn, C, Wn, n, part,
-                                                                           tickets + 1, nullptr, stop);
-                    count_launch();
-                }
-            k_bl_gram<P, 1, double><<<grid, kBlThreads, 0, st>>>(Wn, nullptr, Wn, n, part, tickets, G, stop);
-            count_launch();
-            k_bl_small<P><<<1, 32, 0, st>>>(sm, A, B, j, 1, stop, flags + 1); count_launch();
-            qr_inplace(Wn, j);
-        }
-        return cudaGetLastError();
-    };
-
-    // main pass, then the projected problem
     {
-        cudaError_t e = reorth ? pass_store() : pass(false);
+        cudaError_t e = pass(false);
         if (e != cudaSuccess) {
             (void)cudaGetLastError();
             return e == cudaErrorMemoryAllocation ? ED_ERR_OOM : ED_ERR_CUDA;
@@ -802,8 +970,7 @@ ed_status run_block(const ed_operator *op, const ed_basis *b, const double *x0, 
         return ED_ERR_INVALID_ARG;  // the start block has lower rank than nvec
     ED_BL_TRY(cudaMemcpyAsync(flags + 2, flags + 1, sizeof(int), cudaMemcpyDeviceToDevice, st));
     const int ne = std::max(n_eig, 1);
-    int *d_me = flags + 1;
-    k_band_eigs<P><<<ne, 32, 0, st>>>(A, B, d_me, eig, y, scr); count_launch();
+    k_band_eigs<P><<<ne, 32, 0, st>>>(A, B, flags + 1, eig, y, scr); count_launch();
     ED_BL_TRY(cudaGetLastError());
     std::vector<double> eh(ne);
     ED_BL_TRY(cudaMemcpyAsync(eh.data(), eig, ne * sizeof(double), cudaMemcpyDeviceToHost, st));
@@ -811,8 +978,7 @@ ed_status run_block(const ed_operator *op, const ed_basis *b, const double *x0, 
     // bit-identical pass
     if (reorth) {
         for (int j = 0; j < me; ++j) {
-            k_bl_ritz_acc<P><<<grid, kBlThreads, 0, st>>>(psi_out, Vall + (size_t)j * blk, y, j, n, j == 0,
-                                                          flags + 2);
+            k_dd_ritz_acc<P><<<vgrid, 256, 0, st>>>(ph, pl, bh(j), bl(j), y, j, n, j == 0, flags + 2);
             count_launch();
         }
     } else {
@@ -822,6 +988,7 @@ ed_status run_block(const ed_operator *op, const ed_basis *b, const double *x0, 
             return e == cudaErrorMemoryAllocation ? ED_ERR_OOM : ED_ERR_CUDA;
         }
     }
+    k_dd_to_f64<<<vgrid, 256, 0, st>>>(ph, pl, psi_out, n); count_launch();
     ED_BL_TRY(cudaStreamSynchronize(st));
     double ms = 0.0;
     for (size_t i = 0; i + 1 < ev.size(); i += 2) {
@@ -871,6 +1038,7 @@ extern "C" ed_status ed_lanczos_block(const ed_operator *op, const ed_basis *b, 
     if (reorth) {  // every block is kept: it must fit in half of the free memory
         size_t free_b = 0, total_b = 0;
         cudaMemGetInfo(&free_b, &total_b);
+        free_b += ws_cached_bytes();
         if ((double)(steps + 1) * (double)b->dim * nvec * sizeof(double) > 0.5 * (double)free_b)
             return ED_ERR_UNSUPPORTED;
     }

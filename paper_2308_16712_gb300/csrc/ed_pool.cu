@@ -65,6 +65,18 @@ cudaError_t ws_free(void *p, cudaStream_t s)
     return p ? cudaFreeAsync(p, s) : cudaSuccess;
 }
 
+size_t ws_cached_bytes()
+{
+    cudaMemPool_t pool;
+    if (device_pool(&pool) != cudaSuccess)
+        return 0;
+    uint64_t reserved = 0, used = 0;
+    if (cudaMemPoolGetAttribute(pool, cudaMemPoolAttrReservedMemCurrent, &reserved) != cudaSuccess ||
+        cudaMemPoolGetAttribute(pool, cudaMemPoolAttrUsedMemCurrent, &used) != cudaSuccess)
+        return 0;
+    return reserved > used ? (size_t)(reserved - used) : 0;
+}
+
 }  // namespace edk
 
 extern "C" ed_status ed_release_cached_memory(void)
