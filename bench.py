@@ -1,15 +1,23 @@
 """Benchmark of the symmetry-adapted ED hot path on one GB300 (or N replicas).
 
-Workload (default): Heisenberg ring N=32, J=1, sector Sz=0, momentum 0,
-reflection +1, spin inversion +1 (group order 128, 4 707 969 representatives),
-x0 uniform in [-1, 1] from seed 0.
+Workload (default): Heisenberg ring N=40, J=1, sector Sz=0, momentum 0,
+reflection +1, spin inversion +1 (group order 160, 861 725 794
+representatives -- the paper's Table 2 dimension for 40 spins).
 
-One timed step = the whole hot path once: ed_basis_build (enumerate, filter,
-compact, prefix table) followed by ed_lanczos with 100 steps in the fp32-matvec
-mode (fp64 recurrence, fp64 refinement, fp64 Rayleigh quotient and residual).
-value = matrix rows processed by H.x per second over the step
-(dim x matvecs / step time).  The fp64-plain path (ed_lanczos fp64 mode) is
-timed the same way and reported beside it with |dE0| between the two.
+The metric compares two forms of the product H.x on this sector:
+  - FP32 batched: block Lanczos on nvec = 8 vectors, every product one
+    interleaved fp32 block product (one representative search and index
+    lookup per matrix element serves all 8 columns), block recurrence and
+    refinement in fp64-class arithmetic (ed_lanczos_block);
+  - FP64 plain: single-vector Lanczos with fp64 products (ed_lanczos).
+One timed step = one block-Lanczos step (the block product plus the block
+recurrence kernels; the basis is built once, before, and timed separately).
+value = H.x rows per second = dim x nvec x steps / time (every basis row of a
+block product counts once per vector).  fp64_plain.value is the same for the
+single-vector fp64 recurrence.  dE0 is taken between two full ground-state
+solves run in the same process outside the timed loops: the FP32 batched
+block solve (Ritz vector by a second pass, fp64 refinement, fp64 Rayleigh
+quotient) and the 150-step FP64 plain solve.
 
 Multi-GPU: the path has one sector, which this build does not split across
 GPUs; with --gpus N every rank runs an independent replica (weak scaling,
@@ -48,7 +56,7 @@ INT_LANES_PER_SM = 64
 # capture of it (--set full, which starts every replay with a cold L2); keyed by
 # workload.  Retake the capture and update the figure whenever the kernel
 # changes (the roofline reports null traffic for workloads not listed).
-KERNEL_DRAM_BYTES = {"ring32": 554_140_160 + 112_350_720}
+KERNEL_DRAM_BYTES = {}
 
 
 def peaks():
@@ -558,14 +566,264 @@ def run_multi(args):
     print(json.dumps(out), flush=True)
 
 
+def pruned_search_ops(states, n):
+    """INT32 operations of the pruned representative search (rotation step one
+    site, identity and reversal cosets, spin inversion, 64-bit words) averaged
+    over the terms that the given row states generate -- an instruction-level
+    count of the algorithm the kernel runs, with its data-dependent trip counts
+    (longest run of equal bits, number of candidate tops) taken from the terms:
+      fixed part 39 ops (first rotation, equal-bit mask, special cases, the
+      reversal's mirrored tops and image), 16 ops per run-length iteration (64-bit
+      rotation by one, mask, zero test, select), 35 ops per candidate (lowest
+      set bit, clear, rotation by a variable amount, complement test, 64-bit
+      compare and select), candidates counted for both cosets."""
+    full = np.uint64((1 << n) - 1)
+    one = np.uint64(1)
+
+    def rotl1(x):
+        return ((x << one) | (x >> np.uint64(n - 1))) & full
+
+    terms = []
+    for r in states:
+        r = np.uint64(r)
+        rr = rotl1(r)  # bit p = bit p-1 of r: bonds (p-1, p) antiparallel where r ^ rr
+        anti = int((r ^ rr) & full)
+        p = 0
+        while anti:
+            if anti & 1:
+                q = (p - 1) % n
+                terms.append(int(r) ^ (1 << p) ^ (1 << q))
+            anti >>= 1
+            p += 1
+    h = np.array(terms, dtype=np.uint64)
+    x2 = ~(h ^ rotl1(h)) & full
+    cur = np.full_like(h, full)
+    it = np.zeros(len(h), np.int64)
+    live = x2 != full
+    while live.any():
+        nxt = x2 & rotl1(cur)
+        go = live & (nxt != 0)
+        cur = np.where(go, nxt, cur)
+        it += live.astype(np.int64)  # the iteration that finds nxt == 0 counts too
+        live = go
+    cand = np.array([bin(int(c)).count("1") for c in cur], np.int64)
+    ops = 39 + 16 * it + 2 * 35 * cand
+    return float(ops.mean()), float(it.mean()), float(cand.mean()), len(h)
+
+
+def run_job(args, w):
+    import torch
+    from paper_2308_16712_gb300 import ed
+
+    rank, world, local = dist_setup(args.gpus)
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    n, n_up, z = w["n_sites"], w["n_up"], w["spin_inversion"]
+    nvec = args.nvec
+    op = w["op"]
+    O = ed.operator_create(n, op["sites"], op["coeff"], op["local"])
+    VO = ed.ED_LANCZOS_VALUES_ONLY
+
+    def ev():
+        return torch.cuda.Event(enable_timing=True)
+
+    b0, b1 = ev(), ev()
+    b0.record(stream)
+    B = ed.basis_build(n, n_up, z, w["perms"], w["chars"])
+    b1.record(stream)
+    torch.cuda.synchronize()
+    build_ms = b0.elapsed_time(b1)
+    dim = ed.basis_size(B)
+    states, _ = ed.basis_states(B)
+    # start blocks keyed by the state (seed 0): the [dim][nvec] fp64 block of
+    # the FP32 batched path and the single fp64 vector of the plain path
+    X0 = ei.x_by_state_torch_chunked(0, states, nvec, False, dtype=torch.float64)
+    x1 = ei.x_by_state_torch_chunked(0, states, 1, False, dtype=torch.float64).reshape(-1)
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
+
+    def timed(fn):
+        flush.fill_(1.0)
+        torch.cuda.synchronize()
+        barrier(world)
+        e0, e1 = ev(), ev()
+        e0.record(stream)
+        res = fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1), res
+
+    # ---- FP32 batched: block-Lanczos steps (the timed headline) --------------
+    ed.lanczos_block(O, B, X0, nvec, args.warmup, ed.ED_LANCZOS_F32_MATVEC | VO)
+    launches0 = ed.launch_count()
+    sampler = ClockSampler(local) if rank == 0 else None
+    ms_blk, (_, rb) = timed(lambda: ed.lanczos_block(O, B, X0, nvec, args.steps, ed.ED_LANCZOS_F32_MATVEC | VO))
+    clocks = sampler.stop() if sampler else None
+    launches = ed.launch_count() - launches0
+    ms_blk = max_over_ranks(ms_blk, world)
+    per_step = ms_blk / args.steps
+    rows_blk = dim * nvec * args.steps / (ms_blk * 1e-3)
+    value = sum_over_ranks(rows_blk, world) if world > 1 else rows_blk
+    prod_ms = rb.matvec_ms / max(rb.matvecs, 1)  # the block product, CUDA events in the step
+
+    # ---- FP64 plain: single-vector fp64 Lanczos steps --------------------------
+    ed.lanczos(O, B, x1, args.warmup, ed.ED_LANCZOS_F64 | VO)
+    ms_plain, rp_t = timed(lambda: ed.lanczos(O, B, x1, args.steps, ed.ED_LANCZOS_F64 | VO))
+    ms_plain = max_over_ranks(ms_plain, world)
+    rows_plain = dim * args.steps / (ms_plain * 1e-3)
+    prod64_ms = rp_t.matvec_ms / max(rp_t.matvecs, 1)
+
+    # ---- dE0: full solves outside the timed loops -------------------------------
+    t0 = time.perf_counter()
+    _, rfull = ed.lanczos_block(O, B, X0, nvec, args.block_steps, ed.ED_LANCZOS_F32_MATVEC)
+    t_blk_solve = time.perf_counter() - t0
+    plain_steps = w["lanczos_steps"]
+    t0 = time.perf_counter()
+    rplain = ed.lanczos(O, B, x1, plain_steps, ed.ED_LANCZOS_F64 | VO)
+    t_plain_solve = time.perf_counter() - t0
+    dE0 = abs(rfull.e0 - rplain.e0)
+    del x1
+    torch.cuda.empty_cache()
+
+    # ---- nonzeros and the roofline of the dominant kernel (the block product) --
+    nnz_total = ed.count_nnz(O, B)
+    nnz_row = nnz_total / dim
+    rng = np.random.default_rng(7)
+    idx = torch.from_numpy(rng.integers(0, dim, 3000)).to(dev)
+    sample = states[idx].cpu().numpy().view(np.uint64)
+    ops_term, run_iters, cands, n_terms = pruned_search_ops(sample, n)
+    t_gen = n_terms / len(sample)
+    terms = dim * t_gen
+    int_ops = terms * ops_term
+    int_peak, _ = ed.peak("int32_mix")
+    gather_peak = None
+    pk, pk_kind = peaks()
+    hbm_peak = pk.get("hbm_gbs", 6800.0)
+    alg_bytes = dim * (8 + 2 + 2 * 4 * nvec) + terms * (4 * nvec + 2)  # keys, norms, x_r, y_r; x_j, n(r')
+    sector_bytes = dim * (8 + 2 * 4 * nvec) + terms * (32 + max(32, 4 * nvec))  # bucket + x row per term
+    t_s = prod_ms * 1e-3
+    achieved_int = int_ops / t_s / 1e12
+    roofline = {
+        "bound": "alu", "achieved": achieved_int, "peak": int_peak / 1e12, "unit": "TOP/s",
+        "frac": achieved_int / (int_peak / 1e12),
+        "traffic": KERNEL_DRAM_BYTES.get((w["name"], nvec)),
+        "kernel": f"k_matvec (row-per-lane, fp32, nvec={nvec}, pruned rotation search, 64-bit words, "
+                  "bucketed index)",
+        "peak_kind": "measured live: int32 op mix of the search (funnel shift, lop3, min, add) on every SM",
+        "int_ops_per_launch": int_ops, "int_ops_per_term": ops_term,
+        "run_length_iterations_per_term": run_iters, "candidate_tops_per_term_and_coset": cands,
+        "generated_terms_per_row": t_gen,
+        "hbm": {"algorithmic_bytes": alg_bytes, "achieved_gbs": alg_bytes / t_s / 1e9, "peak_gbs": hbm_peak,
+                "frac": alg_bytes / t_s / 1e9 / hbm_peak, "peak_kind": pk_kind,
+                "sector_bytes": sector_bytes, "sector_gbs": sector_bytes / t_s / 1e9},
+    }
+    buf = torch.empty(8 << 30, dtype=torch.uint8, device=dev)
+    buf.fill_(1)
+    gather_peak, _ = ed.peak("gather32", buf)
+    del buf
+    accesses = terms * 2 + dim  # one bucket and one x row per term, one key/x/y row per basis row
+    roofline["random_access"] = {"accesses_per_launch": accesses, "achieved_per_s": accesses / t_s,
+                                 "peak_per_s": gather_peak, "frac": accesses / t_s / gather_peak,
+                                 "peak_kind": "measured live: random 32-byte reads over 8 GiB"}
+    roofline_time = max(alg_bytes / (hbm_peak * 1e9), int_ops / int_peak)
+    roofline["north_star_roofline_frac"] = roofline_time / t_s
+
+    # ---- CPU oracle on sampled rows of the same sector ---------------------------
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline and world == 1:
+        cpu = cpu_baseline(w)
+
+    # ---- end to end through the C ABI: pinned host start block in, Ritz values
+    # out, the same K block steps ----------------------------------------------
+    X0_host = torch.empty(X0.shape, dtype=X0.dtype, pin_memory=True)
+    X0_host.copy_(X0)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    X0.copy_(X0_host, non_blocking=True)
+    eigs, _ = ed.lanczos_block(O, B, X0, nvec, args.steps, ed.ED_LANCZOS_F32_MATVEC | VO, n_eig=nvec)
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    e2e_s = max_over_ranks(e2e_s, world)
+    e2e_value = dim * nvec * args.steps / e2e_s
+    if world > 1:
+        e2e_value = sum_over_ranks(e2e_value, world)
+    h2d = X0_host.numel() * X0_host.element_size()
+    del X0_host
+
+    # ---- secondary: ring N=32 (config 2) products, L2 flushed ----------------------
+    secondary = None
+    if args.workload == "ring40":
+        w2 = ei.workload("ring32")
+        B2 = ed.basis_build(32, 16, +1, w2["perms"], w2["chars"])
+        d2 = ed.basis_size(B2)
+        st2, _ = ed.basis_states(B2)
+        O2 = ed.operator_create(32, w2["op"]["sites"], w2["op"]["coeff"], w2["op"]["local"])
+        secondary = {"workload": "ring32: Heisenberg ring N=32, Sz=0, k=0, p=+1, z=+1", "dim": d2}
+        for name, dt, nv in (("f64", torch.float64, 1), ("f32", torch.float32, 1), ("f32_nvec8", torch.float32, 8)):
+            xx = ei.x_by_state_torch_chunked(5, st2, nv, False, dtype=dt)
+            yy = torch.empty_like(xx)
+            ed.matvec(O2, B2, xx, yy, nv)
+            ms = min(timed(lambda: ed.matvec(O2, B2, xx, yy, nv))[0] for _ in range(5))
+            secondary[name] = {"ms": ms, "rows_per_s": nv * d2 / (ms * 1e-3)}
+        del B2
+
+    if rank != 0:
+        return
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": per_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"{w['name']}: Heisenberg ring N={n}, J=1, Sz=0, k=0, p=+1, z=+1 "
+                               "(the paper's Table 2 sector for 40 spins)" if w["name"] == "ring40"
+                               else w["name"],
+                   "dim": dim, "group_order": len(w["perms"]) * (2 if z else 1), "nvec": nvec,
+                   "step": f"one block-Lanczos step: fp32 block product of {nvec} interleaved vectors + "
+                           "block recurrence (double-float arithmetic, fp64 coefficients and merges)",
+                   "value_counts": "H.x rows: basis rows x vectors per second",
+                   "l2": "flushed before each timed region (inputs far larger than L2)",
+                   "parallelism": f"replicas x{world}", "basis_build_ms": build_ms},
+        "batched_product": {"ms": prod_ms, "rows_per_s": dim / t_s, "vector_rows_per_s": nvec * dim / t_s,
+                            "nonzeros_per_s": nvec * nnz_total / t_s},
+        "fp64_plain": {"value": rows_plain, "unit": UNIT, "ms_per_step": ms_plain / args.steps,
+                       "product_ms": prod64_ms, "rows_per_s_product": dim / (prod64_ms * 1e-3),
+                       "nonzeros_per_s_product": nnz_total / (prod64_ms * 1e-3)},
+        "speedup_fp32_batched_vs_fp64_plain": value / sum_over_ranks(rows_plain, world) if world > 1
+        else rows_blk / rows_plain,
+        "nonzeros_per_s": value * nnz_row,
+        "nnz_per_row": nnz_row, "nnz_per_product": nnz_total,
+        "solves": {"fp32_batched": {"e0": rfull.e0, "residual": rfull.residual, "block_steps": rfull.steps,
+                                    "products": rfull.matvecs, "wall_s": t_blk_solve,
+                                    "form": f"block Lanczos nvec={nvec}, {args.block_steps} steps, Ritz vector "
+                                            "by a second pass, 6 fp64 refinement steps, fp64 Rayleigh "
+                                            "quotient"},
+                   "fp64_plain": {"e0": rplain.e0, "residual_estimate": rplain.residual,
+                                  "steps": rplain.steps, "wall_s": t_plain_solve,
+                                  "form": f"single-vector fp64 Lanczos, {plain_steps} steps, lowest Ritz value"}},
+        "dE0": dE0,
+        "roofline": roofline,
+        "cpu_baseline": cpu,
+        "e2e": {"value": e2e_value, "unit": UNIT, "s": e2e_s, "h2d_bytes_per_step": h2d / args.steps,
+                "d2h_bytes_per_step": 8 * nvec / args.steps,
+                "path": "pinned host start block -> device, ed_lanczos_block over the same steps, Ritz "
+                        "values -> host"},
+        "gpu_launches": launches,
+        "clocks": clocks,
+        "secondary": secondary,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="ring32")
-    ap.add_argument("--nvec", type=int, default=1, help="vectors per matvec in --mode matvec")
+    ap.add_argument("--workload", default="ring40")
+    ap.add_argument("--nvec", type=int, default=8,
+                    help="block size of the FP32 batched path (and vectors per product in --mode matvec)")
+    ap.add_argument("--block-steps", type=int, default=60,
+                    help="block steps of the full FP32 batched solve behind dE0")
     ap.add_argument("--lanczos-steps", type=int, default=100,
                     help="Lanczos steps of the batched solve in --mode multi (0: skip)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -592,190 +850,7 @@ def main():
     if args.mode == "multi":
         return run_multi(args)
 
-    import torch
-    from paper_2308_16712_gb300 import ed
-
-    rank, world, local = dist_setup(args.gpus)
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
-    stream = torch.cuda.current_stream(dev)
-    n, n_up, z = w["n_sites"], w["n_up"], w["spin_inversion"]
-    op = w["op"]
-    steps = w["lanczos_steps"]
-    O = ed.operator_create(n, op["sites"], op["coeff"], op["local"])
-    B = ed.basis_build(n, n_up, z, w["perms"], w["chars"])
-    dim = ed.basis_size(B)
-    states, _ = ed.basis_states(B)
-    t_gen = generated_terms_per_row(states, n)
-    x0_host = torch.from_numpy(ei.x_by_index(0, dim)[:, 0]).pin_memory()
-    x0 = x0_host.to(dev)
-    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
-
-    def flush_l2():
-        flush.fill_(1.0)
-
-    def one_step(mode):
-        b = ed.basis_build(n, n_up, z, w["perms"], w["chars"])
-        r = ed.lanczos(O, b, x0, steps, mode)
-        del b
-        return r
-
-    def timed_steps(mode, k, warm):
-        for _ in range(warm):
-            one_step(mode)
-        torch.cuda.synchronize()
-        barrier(world)
-        total_ms, res, mv_ms, mv_n = 0.0, None, 0.0, 0
-        launches0 = ed.launch_count()
-        for _ in range(k):
-            flush_l2()
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            torch.cuda.synchronize()
-            e0.record(stream)
-            res = one_step(mode)
-            e1.record(stream)
-            torch.cuda.synchronize()
-            total_ms += e0.elapsed_time(e1)
-            mv_ms += res.matvec_ms
-            mv_n += res.matvecs
-        launches = ed.launch_count() - launches0
-        barrier(world)
-        return total_ms, res, mv_ms, mv_n, launches
-
-    sampler = ClockSampler(local) if rank == 0 else None
-    ms32, r32, mv32_ms, mv32_n, launches = timed_steps(ed.ED_LANCZOS_F32_MATVEC, args.steps, args.warmup)
-    clocks = sampler.stop() if sampler else None
-    ms64, r64, mv64_ms, mv64_n, _ = timed_steps(ed.ED_LANCZOS_F64, max(1, args.steps), 1)
-    # the same job with push-form products (opt-in, not bit-reproducible)
-    msp, rp, _, _, _ = timed_steps(ed.ED_LANCZOS_F32_MATVEC | ed.ED_LANCZOS_PUSH, max(1, args.steps), 1)
-    msp = max_over_ranks(msp, world)
-    ms32 = max_over_ranks(ms32, world)
-    ms64 = max_over_ranks(ms64, world)
-    per32 = ms32 / args.steps
-    per64 = ms64 / max(1, args.steps)
-    rows32 = dim * r32.matvecs / (per32 * 1e-3)
-    rows64 = dim * r64.matvecs / (per64 * 1e-3)
-    value = sum_over_ranks(rows32, world) if world > 1 else rows32
-
-    # where a step's time goes: basis build alone (events, L2 flushed first),
-    # products (CUDA events around every product inside ed_lanczos), the rest
-    build_ts = []
-    for _ in range(3):
-        flush_l2()
-        b0, b1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        torch.cuda.synchronize()
-        b0.record(stream)
-        bb = ed.basis_build(n, n_up, z, w["perms"], w["chars"])
-        b1.record(stream)
-        torch.cuda.synchronize()
-        build_ts.append(b0.elapsed_time(b1))
-        del bb
-    build_ms = statistics.median(build_ts)
-    mv_step_ms = mv32_ms / args.steps
-    breakdown = {"basis_build_ms": build_ms, "products_ms": mv_step_ms,
-                 "products": mv32_n // max(args.steps, 1),
-                 "lanczos_vectors_and_rest_ms": per32 - build_ms - mv_step_ms}
-
-    # single matvec launches (kernel level), L2 flushed between launches
-    def matvec_rate(dtype, nvec, reps=5):
-        xx = torch.from_numpy(ei.x_by_index(5, dim, nvec)).to(dev).to(dtype)
-        yy = torch.empty_like(xx)
-        ed.matvec(O, B, xx, yy, nvec)
-        tot = 0.0
-        for _ in range(reps):
-            flush_l2()
-            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            a.record(stream)
-            ed.matvec(O, B, xx, yy, nvec)
-            b.record(stream)
-            torch.cuda.synchronize()
-            tot += a.elapsed_time(b)
-        return tot / reps
-
-    mv = {}
-    for name, dt, nv in [("f64", torch.float64, 1), ("f32", torch.float32, 1), ("f32_nvec8", torch.float32, 8)]:
-        ms = matvec_rate(dt, nv)
-        mv[name] = {"ms": ms, "rows_per_s": dim / (ms * 1e-3), "vector_rows_per_s": nv * dim / (ms * 1e-3)}
-
-    # roofline of the dominant kernel (the matvec): integer ALU bound
-    pk, pk_kind = peaks()
-    n_perm = len(w["perms"])
-    fact, rot_L, rot_d, n_cos = ed.basis_factored(B)
-    kinds = [0, 1] if (fact and n_cos == 2) else [0] + [2] * (n_cos - 1)
-    ops_term = search_ops_per_term(n, n_perm, z != 0, fact, rot_L, n_cos, kinds)
-    int_ops = dim * t_gen * ops_term
-    avg_ms = (mv32_ms / max(mv32_n, 1)) if mv32_n else mv["f32"]["ms"]
-    achieved = int_ops / (avg_ms * 1e-3) / 1e12
-    peak_int = SMS * INT_LANES_PER_SM * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
-    cpu = None
-    if rank == 0 and not args.no_cpu_baseline and world == 1:
-        cpu = cpu_baseline(w)
-    nnz_total = ed.count_nnz(O, B)  # exact, on the GPU
-    nnz_row = nnz_total / dim
-
-    # end to end through the C ABI: pinned host x0 in, ground state and E0 out
-    host_out = torch.empty(dim, dtype=torch.float64).pin_memory()
-    vec = torch.empty(dim, dtype=torch.float64, device=dev)
-    e2e_ms = 0.0
-    for i in range(1 + args.steps):
-        flush_l2()
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        xd = x0_host.to(dev, non_blocking=True)
-        b = ed.basis_build(n, n_up, z, w["perms"], w["chars"])
-        r = ed.lanczos(O, b, xd, steps, ed.ED_LANCZOS_F32_MATVEC, vec_out=vec)
-        host_out.copy_(vec, non_blocking=True)
-        torch.cuda.synchronize()
-        del b
-        if i:
-            e2e_ms += 1e3 * (time.perf_counter() - t0)
-    e2e_ms = max_over_ranks(e2e_ms / args.steps, world)
-    e2e_value = dim * r.matvecs / (e2e_ms * 1e-3)
-    if world > 1:
-        e2e_value = sum_over_ranks(e2e_value, world)
-
-    if rank != 0:
-        return
-    line = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": per32, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": f"{w['name']}: Heisenberg ring N={n}, J=1, Sz=0, k=0, p=+1, z=+1",
-                   "dim": dim, "group_order": n_perm * 2, "lanczos_steps": steps,
-                   "step": "basis build + Lanczos (fp32 matvec, fp64 recurrence, fp64 refinement)",
-                   "l2": "flushed between timed steps", "parallelism": f"replicas x{world}"},
-        "e0": r32.e0, "residual": r32.residual, "matvecs_per_step": r32.matvecs,
-        "fp64_plain": {"value": rows64, "ms_per_step": per64, "e0": r64.e0, "residual": r64.residual,
-                       "matvecs_per_step": r64.matvecs},
-        "dE0": abs(r32.e0 - r64.e0),
-        "step_breakdown": breakdown,
-        "push_mode": {"value": dim * rp.matvecs / (msp / max(1, args.steps) * 1e-3),
-                      "ms_per_step": msp / max(1, args.steps), "e0": rp.e0, "dE0": abs(rp.e0 - r64.e0),
-                      "note": "ED_LANCZOS_PUSH: atomic scatter products, E0 varies in the last bits"},
-        "speedup_fp32_vs_fp64": rows32 / rows64,
-        "nonzeros_per_s": value * nnz_row,
-        "nnz_per_row": nnz_row,
-        "nnz_per_matvec": nnz_total,
-        "generated_terms_per_row": t_gen,
-        "prefix_table": dict(zip(("entries", "largest_bucket", "probe_steps"), ed.basis_table(B))),
-        "hash_index": dict(zip(("present", "log2_buckets", "largest_bucket", "wide_entries"),
-                               ed.basis_hash(B))),
-        "matvec_kernel": mv,
-        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_int, "unit": "TOP/s",
-                     "frac": achieved / peak_int, "traffic": KERNEL_DRAM_BYTES.get(w["name"]),
-                     "kernel": "k_matvec_tp (term-parallel, fp32, " + ("rotation x coset" if fact else "Benes")
-                               + f" group search, {'32' if n <= 32 else '64'}-bit words)",
-                     "int_ops_per_launch": int_ops, "int_ops_per_term": ops_term,
-                     "peak_basis": f"{SMS} SMs x {INT_LANES_PER_SM} INT32 lanes x "
-                                   f"{pk.get('sm_max_mhz', 2070.0):.0f} MHz ({pk_kind} clock)"},
-        "cpu_baseline": cpu,
-        "e2e": {"value": e2e_value, "unit": UNIT, "ms_per_step": e2e_ms,
-                "h2d_bytes_per_step": dim * 8, "d2h_bytes_per_step": dim * 8 + 8},
-        "gpu_launches": launches // max(args.steps, 1) * args.steps,
-        "clocks": clocks,
-    }
-    print(json.dumps(line), flush=True)
-
+    return run_job(args, w)
 
 if __name__ == "__main__":
     main()

@@ -278,7 +278,14 @@ typedef enum {
                                   the Ritz values free of spurious copies so that the
                                   low excited states come out too; costs about
                                   4 j vector reads at step j.  Needs the Krylov
-                                  vectors kept in memory; ED_ERR_UNSUPPORTED otherwise */
+                                  vectors kept in memory; ED_ERR_UNSUPPORTED otherwise */,
+    ED_LANCZOS_VALUES_ONLY = 128 /* flag (ed_lanczos, ed_lanczos_block): the Ritz
+                                  values of the main run only -- no Ritz vector,
+                                  no second pass, no refinement; e0 is the lowest
+                                  Ritz value and residual the recurrence's own
+                                  estimate |beta_{m+1} s_m| (|B_{m+1} s_m| for
+                                  blocks) of |H psi - e0 psi|; d_vec_out must be
+                                  NULL */
 } ed_lanczos_mode;
 
 typedef struct {

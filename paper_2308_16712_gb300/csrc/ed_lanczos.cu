@@ -678,7 +678,7 @@ struct Scratch {
 
 template <bool kC>
 ed_status run_lanczos(const ed_operator *op, const ed_basis *b, const void *x0, int steps,
-                      ed_lanczos_mode mode, bool recompute, bool push, bool reorth, int n_eig,
+                      ed_lanczos_mode mode, bool recompute, bool push, bool reorth, bool values_only, int n_eig,
                       double *eigs_out, double *e0_out, void *vec_out,
                       ed_lanczos_info *info, cudaStream_t st)
 {
@@ -702,7 +702,7 @@ ed_status run_lanczos(const ed_operator *op, const ed_basis *b, const void *x0, 
     cudaMemGetInfo(&free_b, &total_b);
     free_b += ws_cached_bytes();
     const size_t vec_bytes = n * sizeof(D);
-    const bool store = !recompute && (double)(steps + 1) * vec_bytes < 0.5 * (double)free_b;
+    const bool store = !values_only && !recompute && (double)(steps + 1) * vec_bytes < 0.5 * (double)free_b;
     // push products are not bit-reproducible, so a recomputed pass would not
     // retrace the first one
     if (push && (!store || !ov.exchange_only || !(iv.htab || iv.bkt)))
@@ -818,6 +818,32 @@ ed_status run_lanczos(const ed_operator *op, const ed_basis *b, const void *x0, 
     if (n_eig > 0) {
         k_tridiag_kth<<<n_eig, 32, 0, st>>>(alpha, beta, steps, m_eff, d_eigs); count_launch();
     }
+    if (values_only) {
+        // lowest Ritz value; residual estimate |beta_{m+1} y_m| of the recurrence
+        double ritz = 0.0;
+        int me = 0;
+        ED_L_TRY(cudaMemcpyAsync(&ritz, scal + 0, sizeof(double), cudaMemcpyDeviceToHost, st));
+        ED_L_TRY(cudaMemcpyAsync(&me, m_eff, sizeof(int), cudaMemcpyDeviceToHost, st));
+        ED_L_TRY(cudaStreamSynchronize(st));
+        double bl = 0.0, yl = 0.0;
+        if (me > 0) {
+            ED_L_TRY(cudaMemcpy(&bl, beta + me, sizeof(double), cudaMemcpyDeviceToHost));
+            ED_L_TRY(cudaMemcpy(&yl, y + me - 1, sizeof(double), cudaMemcpyDeviceToHost));
+        }
+        if (n_eig > 0 && eigs_out)
+            ED_L_TRY(cudaMemcpy(eigs_out, d_eigs, n_eig * sizeof(double), cudaMemcpyDeviceToHost));
+        if (e0_out)
+            *e0_out = ritz;
+        if (info) {
+            info->steps = me;
+            info->matvecs = matvecs;
+            info->ritz = ritz;
+            info->e0 = ritz;
+            info->residual = fabs(bl * yl);
+            info->matvec_ms = timer.total_ms();
+        }
+        return ED_OK;
+    }
     if (store) {
         k_combine<kC><<<vgrid, kRedThreads, 0, st>>>(psi, V, y, m_eff, n); count_launch();
     } else {
@@ -878,7 +904,8 @@ ed_status lanczos_entry(const ed_operator *op, const ed_basis *b, const void *x0
 {
     if (!op || !b || steps < 1 || steps > 10000)
         return ED_ERR_INVALID_ARG;
-    const int base = mode_flags & ~(ED_LANCZOS_RECOMPUTE | ED_LANCZOS_PUSH | ED_LANCZOS_REORTH);
+    const int base = mode_flags & ~(ED_LANCZOS_RECOMPUTE | ED_LANCZOS_PUSH | ED_LANCZOS_REORTH |
+                                    ED_LANCZOS_VALUES_ONLY);
     if (base != ED_LANCZOS_F64 && base != ED_LANCZOS_F32_MATVEC)
         return ED_ERR_INVALID_ARG;
     if (n_eig < 0 || n_eig > steps || (n_eig > 0 && !eigs_out))
@@ -887,6 +914,9 @@ ed_status lanczos_entry(const ed_operator *op, const ed_basis *b, const void *x0
     const bool recompute = (mode_flags & ED_LANCZOS_RECOMPUTE) != 0;
     const bool push = (mode_flags & ED_LANCZOS_PUSH) != 0;
     const bool reorth = (mode_flags & ED_LANCZOS_REORTH) != 0;
+    const bool values_only = (mode_flags & ED_LANCZOS_VALUES_ONLY) != 0;
+    if (values_only && vec_out)
+        return ED_ERR_INVALID_ARG;
     if (b->dim == 0 || !x0)
         return ED_ERR_INVALID_ARG;
     if (((uintptr_t)x0 | (uintptr_t)vec_out) & 15)
@@ -897,9 +927,9 @@ ed_status lanczos_entry(const ed_operator *op, const ed_basis *b, const void *x0
     const bool cplx = !(b->real_chars && op->real);
     ed_lanczos_info local{};
     ed_lanczos_info *inf = info ? info : &local;
-    const ed_status r = cplx ? edk::run_lanczos<true>(op, b, x0, steps, mode, recompute, push, reorth, n_eig,
+    const ed_status r = cplx ? edk::run_lanczos<true>(op, b, x0, steps, mode, recompute, push, reorth, values_only, n_eig,
                                                       eigs_out, e0_out, vec_out, inf, (cudaStream_t)stream)
-                             : edk::run_lanczos<false>(op, b, x0, steps, mode, recompute, push, reorth, n_eig,
+                             : edk::run_lanczos<false>(op, b, x0, steps, mode, recompute, push, reorth, values_only, n_eig,
                                                        eigs_out, e0_out, vec_out, inf, (cudaStream_t)stream);
     if (r == ED_OK && tol > 0.0 && !(inf->residual <= tol))
         return ED_ERR_NOT_CONVERGED;

@@ -827,8 +827,8 @@ void launch_update(int nm, int yk, const float *X0h, const float *X0l, const flo
 
 template <int P>
 ed_status run_block(const ed_operator *op, const ed_basis *b, const double *x0, int steps, bool f32, bool reorth,
-                    int n_eig, double *eigs_out, double *psi_out, int *steps_out, int *matvecs_out,
-                    double *ritz_out, double *mv_ms_out, cudaStream_t st)
+                    bool values_only, int n_eig, double *eigs_out, double *psi_out, int *steps_out,
+                    int *matvecs_out, double *ritz_out, double *res_out, double *mv_ms_out, cudaStream_t st)
 {
     const uint64_t n = b->dim;
     const OpView ov = make_op_view(op);
@@ -974,9 +974,25 @@ ed_status run_block(const ed_operator *op, const ed_basis *b, const double *x0, 
     ED_BL_TRY(cudaGetLastError());
     std::vector<double> eh(ne);
     ED_BL_TRY(cudaMemcpyAsync(eh.data(), eig, ne * sizeof(double), cudaMemcpyDeviceToHost, st));
-    // Ritz vector of the lowest: from the kept blocks, or by a second,
-    // bit-identical pass
-    if (reorth) {
+    *res_out = 0.0;
+    if (values_only) {
+        // residual estimate |B_{m+1} s_m| of the lowest Ritz pair (s_m: the
+        // eigenvector's entries on the last block)
+        std::vector<double> Bm((size_t)P * P), ym(P);
+        ED_BL_TRY(cudaMemcpyAsync(Bm.data(), B + (size_t)me * P * P, P * P * sizeof(double),
+                                  cudaMemcpyDeviceToHost, st));
+        ED_BL_TRY(cudaMemcpyAsync(ym.data(), y + (size_t)(me - 1) * P, P * sizeof(double),
+                                  cudaMemcpyDeviceToHost, st));
+        ED_BL_TRY(cudaStreamSynchronize(st));
+        double r2 = 0.0;
+        for (int a = 0; a < P; ++a) {
+            double t = 0.0;
+            for (int c = 0; c < P; ++c)
+                t += Bm[a * P + c] * ym[c];
+            r2 += t * t;
+        }
+        *res_out = me < steps ? 0.0 : sqrt(r2);  // a stopped recurrence spans an invariant subspace
+    } else if (reorth) {
         for (int j = 0; j < me; ++j) {
             k_dd_ritz_acc<P><<<vgrid, 256, 0, st>>>(ph, pl, bh(j), bl(j), y, j, n, j == 0, flags + 2);
             count_launch();
@@ -988,7 +1004,9 @@ ed_status run_block(const ed_operator *op, const ed_basis *b, const double *x0, 
             return e == cudaErrorMemoryAllocation ? ED_ERR_OOM : ED_ERR_CUDA;
         }
     }
-    k_dd_to_f64<<<vgrid, 256, 0, st>>>(ph, pl, psi_out, n); count_launch();
+    if (!values_only) {
+        k_dd_to_f64<<<vgrid, 256, 0, st>>>(ph, pl, psi_out, n); count_launch();
+    }
     ED_BL_TRY(cudaStreamSynchronize(st));
     double ms = 0.0;
     for (size_t i = 0; i + 1 < ev.size(); i += 2) {
@@ -1021,7 +1039,10 @@ extern "C" ed_status ed_lanczos_block(const ed_operator *op, const ed_basis *b, 
     if (nvec != 2 && nvec != 4 && nvec != 8 && nvec != 16)
         return ED_ERR_INVALID_ARG;
     const bool reorth = (mode & ED_LANCZOS_REORTH) != 0;
-    mode &= ~ED_LANCZOS_REORTH;
+    const bool values_only = (mode & ED_LANCZOS_VALUES_ONLY) != 0;
+    mode &= ~(ED_LANCZOS_REORTH | ED_LANCZOS_VALUES_ONLY);
+    if (values_only && d_vec_out)
+        return ED_ERR_INVALID_ARG;
     if (mode != ED_LANCZOS_F64 && mode != ED_LANCZOS_F32_MATVEC)
         return ED_ERR_INVALID_ARG;
     if (n_eig < 0 || n_eig > nvec * steps || (n_eig > 0 && !eigs_out))
@@ -1048,21 +1069,25 @@ extern "C" ed_status ed_lanczos_block(const ed_operator *op, const ed_basis *b, 
         return ED_ERR_OOM;
     }
     int steps_done = 0, matvecs = 0;
-    double ritz = 0.0, mv_ms = 0.0;
+    double ritz = 0.0, mv_ms = 0.0, res_est = 0.0;
     ed_status r = ED_ERR_INVALID_ARG;
     const double *x0 = (const double *)d_x0;
     switch (nvec) {
-    case 2: r = run_block<2>(op, b, x0, steps, f32, reorth, n_eig, eigs_out, psi, &steps_done, &matvecs, &ritz, &mv_ms, st); break;
-    case 4: r = run_block<4>(op, b, x0, steps, f32, reorth, n_eig, eigs_out, psi, &steps_done, &matvecs, &ritz, &mv_ms, st); break;
-    case 8: r = run_block<8>(op, b, x0, steps, f32, reorth, n_eig, eigs_out, psi, &steps_done, &matvecs, &ritz, &mv_ms, st); break;
-    case 16: r = run_block<16>(op, b, x0, steps, f32, reorth, n_eig, eigs_out, psi, &steps_done, &matvecs, &ritz, &mv_ms, st); break;
+    case 2: r = run_block<2>(op, b, x0, steps, f32, reorth, values_only, n_eig, eigs_out, psi, &steps_done, &matvecs, &ritz, &res_est, &mv_ms, st); break;
+    case 4: r = run_block<4>(op, b, x0, steps, f32, reorth, values_only, n_eig, eigs_out, psi, &steps_done, &matvecs, &ritz, &res_est, &mv_ms, st); break;
+    case 8: r = run_block<8>(op, b, x0, steps, f32, reorth, values_only, n_eig, eigs_out, psi, &steps_done, &matvecs, &ritz, &res_est, &mv_ms, st); break;
+    case 16: r = run_block<16>(op, b, x0, steps, f32, reorth, values_only, n_eig, eigs_out, psi, &steps_done, &matvecs, &ritz, &res_est, &mv_ms, st); break;
     }
     // fp64 refinement of the Ritz vector: a short single-vector fp64 Lanczos
     // run from it, whose fp64 Rayleigh quotient and residual are returned
     ed_lanczos_info ri{};
     double e0 = 0.0;
-    if (r == ED_OK)
+    if (r == ED_OK && values_only) {
+        e0 = ritz;
+        ri.residual = res_est;
+    } else if (r == ED_OK) {
         r = ed_lanczos(op, b, psi, 6, ED_LANCZOS_F64, &e0, d_vec_out, &ri, stream);
+    }
     ws_free(psi, st);
     if (r != ED_OK)
         return r;

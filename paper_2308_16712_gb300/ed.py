@@ -21,6 +21,7 @@ ED_OK = 0
 ED_F64, ED_F32, ED_C128, ED_C64 = 0, 1, 2, 3
 ED_LANCZOS_F64, ED_LANCZOS_F32_MATVEC, ED_LANCZOS_RECOMPUTE, ED_LANCZOS_PUSH = 0, 1, 16, 32
 ED_LANCZOS_REORTH = 64
+ED_LANCZOS_VALUES_ONLY = 128
 
 STATUS_NAMES = {
     0: "ED_OK", 1: "ED_ERR_INVALID_ARG", 2: "ED_ERR_NOT_A_GROUP", 3: "ED_ERR_BAD_CHARACTER",

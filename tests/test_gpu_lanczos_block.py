@@ -121,3 +121,23 @@ def test_block_argument_errors():
     with pytest.raises(ed.EDError) as e:
         ed.lanczos_block(C["O"], C["B"], start_block(C["dim"], 4), 4, 5)
     assert e.value.status == 9
+
+
+def test_values_only_modes():
+    """ED_LANCZOS_VALUES_ONLY: the Ritz values of the main run alone (no Ritz
+    vector, no refinement) -- equal to the dense lowest eigenvalue once
+    converged, with a small residual estimate; a vector output is refused."""
+    torch, ed = gpu()
+    w = ei.workload("ring16")
+    S = build_pair(16, 8, +1, w["perms"], w["chars"], w["op"])
+    ev = dense_spectrum(S)
+    x1 = to_torch(ei.x_by_index(0, S["dim"])[:, 0], np.float64)
+    r = ed.lanczos(S["O"], S["B"], x1, 60, ed.ED_LANCZOS_F64 | ed.ED_LANCZOS_VALUES_ONLY)
+    assert abs(r.e0 - ev[0]) < 1e-10 and r.residual < 1e-6 and r.matvecs == 60
+    x0 = start_block(S["dim"], 8)
+    eigs, rb = ed.lanczos_block(S["O"], S["B"], x0, 8, 20, ed.ED_LANCZOS_F64 | ed.ED_LANCZOS_VALUES_ONLY, n_eig=1)
+    assert abs(rb.e0 - ev[0]) < 1e-10 and rb.e0 == eigs[0] and rb.matvecs == 20 and rb.residual < 1e-6
+    with pytest.raises(ed.EDError) as e:
+        ed.lanczos_block(S["O"], S["B"], x0, 8, 5, ed.ED_LANCZOS_F64 | ed.ED_LANCZOS_VALUES_ONLY,
+                         vec_out=torch.empty(S["dim"], dtype=torch.float64, device="cuda"))
+    assert e.value.status == 1
