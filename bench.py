@@ -415,6 +415,24 @@ def run_one_step(args, w):
     print(json.dumps({"mode": "step", "workload": w["name"], "steps": marks}))
 
 
+def run_block_steps(args, w):
+    """--steps block-Lanczos steps (fp32 block products, values only) on a
+    workload: a short program for profiler captures of the block kernels."""
+    import torch
+    from paper_2308_16712_gb300 import ed
+    n = w["n_sites"]
+    O = ed.operator_create(n, w["op"]["sites"], w["op"]["coeff"], w["op"]["local"])
+    B = ed.basis_build(n, w["n_up"], w["spin_inversion"], w["perms"], w["chars"])
+    dim = ed.basis_size(B)
+    states, _ = ed.basis_states(B)
+    X0 = ei.x_by_state_torch_chunked(0, states, args.nvec, False, dtype=torch.float64)
+    t0 = time.perf_counter()
+    _, r = ed.lanczos_block(O, B, X0, args.nvec, args.steps, ed.ED_LANCZOS_F32_MATVEC | ed.ED_LANCZOS_VALUES_ONLY)
+    torch.cuda.synchronize()
+    print(json.dumps({"mode": "block", "workload": w["name"], "dim": dim, "nvec": args.nvec, "steps": r.steps,
+                      "ritz": r.e0, "wall_s": time.perf_counter() - t0, "product_ms": r.matvec_ms / r.matvecs}))
+
+
 def run_solve(args, w):
     """One ground-state solve per Lanczos mode (fp32 matvec and fp64), timed,
     for workloads too large for the benchmark loop (e.g. the N=40 ring)."""
@@ -828,7 +846,7 @@ def main():
                     help="Lanczos steps of the batched solve in --mode multi (0: skip)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--mode", default="job", choices=["job", "matvec", "step", "solve", "multi", "push",
-                                                      "peaks"],
+                                                      "peaks", "block"],
                     help="job: the benchmark; matvec: only the basis build and --steps matvec "
                          "launches per dtype; step: one untimed and one more whole step "
                          "(short programs for profiler captures)")
@@ -843,6 +861,8 @@ def main():
         return run_one_step(args, w)
     if args.mode == "peaks":
         return run_peaks(args, w)
+    if args.mode == "block":
+        return run_block_steps(args, w)
     if args.mode == "solve":
         return run_solve(args, w)
     if args.mode == "push":
