@@ -128,9 +128,10 @@ ed_status ed_basis_build(int n_sites, int n_up, int spin_inversion, int n_elems,
  * ed_basis_count -- the sector dimension only: the count pass of the
  * enumeration and its scan, without keeping the basis (Table 2 of the paper
  * lists such dimensions, up to 48 spins, which no single GPU could store).
- * Arguments as ed_basis_build; the dimension may exceed 2^32.  Takes its work
- * arrays from the library's memory pool and returns them; synchronises
- * `stream`.
+ * Arguments as ed_basis_build; the dimension may exceed 2^32.  The per-chunk
+ * counts and the scan's arrays come from the library's memory pool and go
+ * back to it; the group and binomial tables are allocated with cudaMalloc and
+ * freed (which synchronises the device).  Synchronises `stream`.
  */
 ed_status ed_basis_count(int n_sites, int n_up, int spin_inversion, int n_elems,
                          const int32_t *perms, const double *chars, void *stream, uint64_t *dim);
@@ -169,7 +170,11 @@ void ed_basis_destroy(ed_basis *basis);
  *
  *   arguments   as ed_basis_build, with at most 512 lattice elements
  *               (n_elems > 512 returns ED_ERR_INVALID_ARG: the scratch has a
- *               fixed size)
+ *               fixed size) and at most 2^42 enumerated states (C(n_sites,
+ *               n_up), or 2^n_sites without U(1); C(44, 22) fits): the
+ *               enumeration has at most 2^18 chunks of at most 2^24 states,
+ *               and a larger sector returns ED_ERR_UNSUPPORTED before any
+ *               CUDA call (count it with ed_basis_count)
  *   dim_out     host, receives the dimension
  *
  * All scratch (group tables, per-chunk counts, scan offsets; about 3.2 MB) is
@@ -179,7 +184,8 @@ void ed_basis_destroy(ed_basis *basis);
  * Every call reuses the same array: calls that overlap on the GPU (different
  * streams or host threads at once) race and must be serialised by the caller.
  * The call enqueues on `stream` and synchronises it before returning.
- * Errors: as ed_basis_build, plus ED_ERR_INVALID_ARG for n_elems > 512.
+ * Errors: as ed_basis_build, plus ED_ERR_INVALID_ARG for n_elems > 512 and
+ * ED_ERR_UNSUPPORTED for more than 2^42 enumerated states.
  */
 ed_status ed_basis_count_noalloc(int n_sites, int n_up, int spin_inversion, int n_elems,
                                  const int32_t *perms, const double *chars, void *stream,

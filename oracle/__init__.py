@@ -283,8 +283,9 @@ def sector_dim(G: Group, n_up: int) -> int:
 def lanczos(apply_h, v0, steps: int, reorth: bool = False):
     """Plain fp64 Lanczos: v_0 = v0/|v0|; w = H v_j - alpha_j v_j - beta_j v_{j-1};
     beta_{j+1} = |w|.  Returns (alphas, betas, lowest Ritz value).  With
-    ``reorth`` every w is re-orthogonalised against all earlier v (classical
-    Gram-Schmidt, twice)."""
+    ``reorth`` every w is re-orthogonalised against all earlier v (modified
+    Gram-Schmidt -- each coefficient taken from the already updated w -- in
+    two passes)."""
     from scipy.linalg import eigh_tridiagonal
     v = v0 / np.linalg.norm(v0)
     vprev = np.zeros_like(v)

@@ -683,15 +683,11 @@ ed_status basis_build_impl(int n_sites, int n_up, int spin_inversion, int n_elem
         return ED_ERR_INVALID_ARG;
     if (out)
         *out = nullptr;
-    if (n_sites < 1 || n_sites > 64 || n_elems < 1 || n_elems > 1024)
-        return ED_ERR_INVALID_ARG;
-    if (n_up < -1 || n_up > n_sites || (n_up == -1 && n_sites > 40))
-        return ED_ERR_INVALID_ARG;
-    if (spin_inversion < -1 || spin_inversion > 1)
-        return ED_ERR_INVALID_ARG;
-    if (spin_inversion != 0 && n_up != -1 && 2 * n_up != n_sites)
-        return ED_ERR_INVALID_ARG;
-    ed_status st = validate_group(n_sites, n_elems, perms, chars);
+    // argument and group validation, the chi == 1 bitset and the Benes masks:
+    // the same host tables as the allocation-free count
+    std::vector<uint32_t> m32, one;
+    std::vector<uint64_t> m64;
+    ed_status st = edk::count_tables_host(n_sites, n_up, spin_inversion, n_elems, perms, chars, m32, m64, one);
     if (st != ED_OK)
         return st;
     cudaStream_t stream = (cudaStream_t)stream_;
@@ -709,7 +705,6 @@ ed_status basis_build_impl(int n_sites, int n_up, int spin_inversion, int n_elem
     // expanded characters: plain elements, then flipped ones (times z)
     std::vector<double2> chi(b->order);
     std::vector<float2> chif(b->order);
-    std::vector<uint32_t> one((b->order + 31) / 32, 0);
     b->trivial_chars = true;
     b->real_chars = true;
     for (int g = 0; g < b->order; ++g) {
@@ -719,25 +714,8 @@ ed_status basis_build_impl(int n_sites, int n_up, int spin_inversion, int n_elem
             c *= (double)spin_inversion;
         chi[g] = make_double2(c.real(), c.imag());
         chif[g] = make_float2((float)c.real(), (float)c.imag());
-        const bool is_one = std::abs(c - 1.0) < kChiTol;
-        if (is_one)
-            one[g / 32] |= 1u << (g % 32);
-        b->trivial_chars = b->trivial_chars && is_one;
+        b->trivial_chars = b->trivial_chars && ((one[g / 32] >> (g % 32)) & 1u);
         b->real_chars = b->real_chars && std::abs(c.imag()) < kChiTol;
-    }
-    // Benes masks for 32- and 64-bit words
-    std::vector<uint32_t> m32((size_t)n_elems * edk::kMaskStride, 0);
-    std::vector<uint64_t> m64((size_t)n_elems * edk::kMaskStride, 0);
-    for (int g = 0; g < n_elems; ++g) {
-        const int32_t *pm = perms + (size_t)g * n_sites;
-        if (n_sites <= 32) {
-            auto m = benes_masks(5, n_sites, pm);
-            for (int s = 0; s < 9; ++s)
-                m32[(size_t)g * edk::kMaskStride + s] = (uint32_t)m[s];
-        }
-        auto m = benes_masks(6, n_sites, pm);
-        for (int s = 0; s < 11; ++s)
-            m64[(size_t)g * edk::kMaskStride + s] = m[s];
     }
 #define ED_B_TRY(expr)                           \
     do {                                         \

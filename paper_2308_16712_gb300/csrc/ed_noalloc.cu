@@ -24,6 +24,10 @@ namespace {
 
 constexpr int kNoAllocMaxElems = 512;                // lattice elements (before spin inversion)
 constexpr uint64_t kNoAllocMaxChunks = 1ULL << 18;   // enumeration chunks per call
+// States one thread enumerates (a chunk).  The per-chunk count is a uint32,
+// and the bound also caps a thread's work: at most 2^18 x 2^24 = 2^42 states
+// per call (C(44, 22) = 2.1e12 fits; larger sectors need ed_basis_count).
+constexpr uint64_t kNoAllocMaxChunkStates = 1ULL << 24;
 constexpr int kNoAllocMaxDevices = 64;
 
 // byte offsets of the carved regions (each 256-byte aligned)
@@ -35,6 +39,8 @@ constexpr size_t kOffBinom = al(kOffChiOne + (2 * kNoAllocMaxElems + 31) / 32 * 
 constexpr size_t kOffCounts = al(kOffBinom + 65 * 65 * 8);
 constexpr size_t kOffOffsets = al(kOffCounts + kNoAllocMaxChunks * 4);
 constexpr size_t kOffTmp = al(kOffOffsets + (kNoAllocMaxChunks + 1) * 8);
+// the scan's work region: scan_tmp_words(n) words, n / 4096 + 1 for the
+// current scan tile, checked against this size before every launch
 constexpr size_t kScratchBytes = al(kOffTmp + ((kNoAllocMaxChunks + 4095) / 4096 + 1) * 8);
 
 // The scratch of every call, on every device that loads the library (about
@@ -82,6 +88,17 @@ extern "C" ed_status ed_basis_count_noalloc(int n_sites, int n_up, int spin_inve
                                                 chars, m32, m64, one);
     if (st != ED_OK)
         return st;
+    // the enumeration plan, and its size checks, before any CUDA call
+    edk::EnumPlan plan;
+    plan.n_sites = n_sites;
+    plan.n_up = n_up;
+    plan.total = n_up < 0 ? (1ULL << n_sites) : edk::binomial_host(n_sites, n_up);
+    plan.chunk = std::max<uint64_t>(16, (plan.total + kNoAllocMaxChunks - 1) / kNoAllocMaxChunks);
+    plan.n_chunks = (plan.total + plan.chunk - 1) / plan.chunk;
+    if (plan.chunk > kNoAllocMaxChunkStates)
+        return ED_ERR_UNSUPPORTED;  // more states than the fixed scratch and per-thread bound allow
+    if (edk::scan_tmp_words(plan.n_chunks) * sizeof(uint64_t) > kScratchBytes - kOffTmp)
+        return ED_ERR_INTERNAL;     // the scan's work region would not fit the scratch
     cudaStream_t stream = (cudaStream_t)stream_;
     unsigned char *base = nullptr;
 #define ED_NA_TRY(expr)                       \
@@ -123,12 +140,6 @@ extern "C" ed_status ed_basis_count_noalloc(int n_sites, int n_up, int spin_inve
     g.chi_one = d_one;
     g.fact = 0;
 
-    edk::EnumPlan plan;
-    plan.n_sites = n_sites;
-    plan.n_up = n_up;
-    plan.total = n_up < 0 ? (1ULL << n_sites) : edk::binomial_host(n_sites, n_up);
-    plan.chunk = std::max<uint64_t>(16, (plan.total + kNoAllocMaxChunks - 1) / kNoAllocMaxChunks);
-    plan.n_chunks = (plan.total + plan.chunk - 1) / plan.chunk;
     plan.binom = d_binom;
 
     ED_NA_TRY(edk::launch_enum_count(plan, g, d_counts, stream));

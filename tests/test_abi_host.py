@@ -196,6 +196,25 @@ def test_argument_errors_before_any_launch(lib):
                                   loc.ctypes.data_as(P), ctypes.byref(out)) == 1
 
 
+def test_noalloc_count_rejects_sectors_beyond_its_bound(lib):
+    """The allocation-free count has a fixed scratch: at most 2^18 chunks of at
+    most 2^24 states.  A larger sector (C(64, 32) = 1.8e18 states) returns
+    ED_ERR_UNSUPPORTED before any CUDA call (this host has no GPU), and so does
+    C(46, 23) = 8.2e12 > 2^42; the group validation still comes first."""
+    P = ctypes.c_void_p
+    dim = ctypes.c_uint64(0)
+    for n in (64, 46):
+        p, c = ei.ring_group(n, 0, +1)
+        pp, cc = np.ascontiguousarray(p), np.ascontiguousarray(c)
+        st = lib.ed_basis_count_noalloc(n, n // 2, 1, len(p), pp.ctypes.data_as(P), cc.ctypes.data_as(P),
+                                        None, ctypes.byref(dim))
+        assert st == 9, (n, st)
+    p, c = ei.ring_group(64, 0, +1)
+    pp, cc = np.ascontiguousarray(p[:5]), np.ascontiguousarray(c[:5])  # not a group
+    assert lib.ed_basis_count_noalloc(64, 32, 1, 5, pp.ctypes.data_as(P), cc.ctypes.data_as(P), None,
+                                      ctypes.byref(dim)) == 2
+
+
 # ----------------------------------------------------------------------------
 # factored form of lattice groups (rotation subgroup x coset representatives)
 # ----------------------------------------------------------------------------

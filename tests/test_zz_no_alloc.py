@@ -35,6 +35,18 @@ def test_count_without_allocation_matches_basis_build():
             assert ed.basis_count_noalloc(n, n_up, z, p, c) == w
 
 
+def test_count_without_allocation_large_chunks():
+    """A sector whose enumeration needs the 2^18-chunk cap (C(28, 14) = 4.0e7
+    states: 153 states per chunk, and the scan over all 2^18 chunk counts),
+    against the allocating count, twice in a row."""
+    from paper_2308_16712_gb300 import ed
+    p, c = ei.ring_group(28, 0)
+    want = ed.basis_count(28, 14, +1, p, c)
+    assert want > 0
+    for _ in range(2):
+        assert ed.basis_count_noalloc(28, 14, +1, p, c) == want
+
+
 def test_count_without_allocation_rejects_groups_beyond_capacity():
     from paper_2308_16712_gb300 import ed
     # 513 elements exceed the fixed scratch; the size check comes first
