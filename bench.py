@@ -211,7 +211,7 @@ def time_oracle_rows_all_cores(w, rows, cores):
         return time.perf_counter() - t0
 
 
-def cpu_baseline(w, budget_s=15.0, par_wall_s=5.0):
+def cpu_baseline(w, budget_s=8.0, par_wall_s=4.0):
     G, H, rows = oracle_rows(w, 64)
     dt, _ = time_oracle_rows(G, H, rows[:8])
     per_row = max(dt / 8, 1e-6)
@@ -684,21 +684,19 @@ def run_job(args, w):
     value = sum_over_ranks(rows_blk, world) if world > 1 else rows_blk
     prod_ms = rb.matvec_ms / max(rb.matvecs, 1)  # the block product, CUDA events in the step
 
-    # ---- FP64 plain: single-vector fp64 Lanczos steps --------------------------
-    ed.lanczos(O, B, x1, args.warmup, ed.ED_LANCZOS_F64 | VO)
-    ms_plain, rp_t = timed(lambda: ed.lanczos(O, B, x1, args.steps, ed.ED_LANCZOS_F64 | VO))
+    # ---- FP64 plain: the 150-step single-vector fp64 Lanczos solve, timed
+    # (CUDA events) as a whole; its lowest Ritz value is the plain E0 --------
+    plain_steps = w["lanczos_steps"]
+    ms_plain, rplain = timed(lambda: ed.lanczos(O, B, x1, plain_steps, ed.ED_LANCZOS_F64 | VO))
     ms_plain = max_over_ranks(ms_plain, world)
-    rows_plain = dim * args.steps / (ms_plain * 1e-3)
-    prod64_ms = rp_t.matvec_ms / max(rp_t.matvecs, 1)
+    rows_plain = dim * rplain.steps / (ms_plain * 1e-3)
+    prod64_ms = rplain.matvec_ms / max(rplain.matvecs, 1)
+    t_plain_solve = ms_plain * 1e-3
 
-    # ---- dE0: full solves outside the timed loops -------------------------------
+    # ---- dE0: the full FP32 batched solve outside the timed loop --------------
     t0 = time.perf_counter()
     _, rfull = ed.lanczos_block(O, B, X0, nvec, args.block_steps, ed.ED_LANCZOS_F32_MATVEC)
     t_blk_solve = time.perf_counter() - t0
-    plain_steps = w["lanczos_steps"]
-    t0 = time.perf_counter()
-    rplain = ed.lanczos(O, B, x1, plain_steps, ed.ED_LANCZOS_F64 | VO)
-    t_plain_solve = time.perf_counter() - t0
     dE0 = abs(rfull.e0 - rplain.e0)
     del x1
     torch.cuda.empty_cache()
@@ -802,7 +800,8 @@ def run_job(args, w):
                    "parallelism": f"replicas x{world}", "basis_build_ms": build_ms},
         "batched_product": {"ms": prod_ms, "rows_per_s": dim / t_s, "vector_rows_per_s": nvec * dim / t_s,
                             "nonzeros_per_s": nvec * nnz_total / t_s},
-        "fp64_plain": {"value": rows_plain, "unit": UNIT, "ms_per_step": ms_plain / args.steps,
+        "fp64_plain": {"value": rows_plain, "unit": UNIT, "ms_per_step": ms_plain / max(rplain.steps, 1),
+                       "timed": f"the {plain_steps}-step fp64 Lanczos solve (values only), CUDA events",
                        "product_ms": prod64_ms, "rows_per_s_product": dim / (prod64_ms * 1e-3),
                        "nonzeros_per_s_product": nnz_total / (prod64_ms * 1e-3)},
         "speedup_fp32_batched_vs_fp64_plain": value / sum_over_ranks(rows_plain, world) if world > 1
@@ -840,7 +839,7 @@ def main():
     ap.add_argument("--workload", default="ring40")
     ap.add_argument("--nvec", type=int, default=8,
                     help="block size of the FP32 batched path (and vectors per product in --mode matvec)")
-    ap.add_argument("--block-steps", type=int, default=60,
+    ap.add_argument("--block-steps", type=int, default=40,
                     help="block steps of the full FP32 batched solve behind dE0")
     ap.add_argument("--lanczos-steps", type=int, default=100,
                     help="Lanczos steps of the batched solve in --mode multi (0: skip)")

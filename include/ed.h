@@ -58,7 +58,8 @@ typedef enum {
     ED_ERR_CUDA = 6,             /* a CUDA runtime call failed */
     ED_ERR_INTERNAL = 7,         /* a device-side invariant check failed */
     ED_ERR_NOT_CONVERGED = 8,    /* Lanczos residual above the requested tolerance */
-    ED_ERR_UNSUPPORTED = 9       /* valid request outside what this build implements */
+    ED_ERR_UNSUPPORTED = 9,      /* valid request outside what this build implements */
+    ED_ERR_TIMEOUT = 10          /* a bounded device-side wait ran out (reported by ed_stream_status) */
 } ed_status;
 
 typedef enum {
@@ -90,10 +91,12 @@ const char *ed_status_string(ed_status status);
  * The paper's runtime needs no such call (its errors surface synchronously);
  * here kernels run asynchronously and record violated invariants in a device
  * status word instead of trapping (e.g. the enumeration's write pass finding a
- * chunk whose count differs from its count pass).  Synchronises `stream`,
- * then reads and clears the word.
- * Returns ED_OK, ED_ERR_INTERNAL (an invariant failed) or ED_ERR_CUDA (an
- * asynchronous launch or execution error).
+ * chunk whose count differs from its count pass; a batched launch whose
+ * blocks gave up a bounded wait).  Synchronises `stream`, then reads and
+ * clears the words.
+ * Returns ED_OK, ED_ERR_INTERNAL (an invariant failed), ED_ERR_TIMEOUT (a
+ * bounded wait ran out; the launch ended without touching its outputs) or
+ * ED_ERR_CUDA (an asynchronous launch or execution error).
  */
 ed_status ed_stream_status(void *stream);
 
@@ -248,7 +251,12 @@ typedef struct {
  * ed_matvec_multi -- y_s = H x_s for up to 160 symmetry sectors in one
  * persistent launch (the matvec of Sec. "Matrix-vector product" applied to a
  * batch of sectors of uneven dimension, so that no launch tail is paid per
- * sector).  Every basis must be built from the same n_sites and the same list
+ * sector).  The launch's warps take 32-row tiles from a device work queue (an
+ * atomic counter over the tiles of all sectors, largest sectors first), the
+ * role the paper's producer/consumer balancing plays across nodes; when every
+ * sector alone fills the GPU and the term-parallel kernel applies, one
+ * launch per sector is issued instead (measured faster for sectors of about a
+ * million rows).  Every basis must be built from the same n_sites and the same list
  * of lattice permutations (characters, spin inversion and n_up may differ);
  * dtype must be complex if any sector is.  Sectors with dimension 0 are
  * skipped.  Results equal those of ed_matvec on each sector, bit for bit.
@@ -449,6 +457,55 @@ ed_status ed_lanczos_block(const ed_operator *op, const ed_basis *basis, const v
 ed_status ed_lanczos_multi(const ed_operator *op, const ed_sector *sectors, int n_sectors, int steps,
                            int mode, ed_dtype dtype, double *e0_out, ed_lanczos_info *info,
                            void *stream);
+
+/*
+ * ed_autotune -- choose, by measurement on this GPU, how ed_matvec (and the
+ * solvers) run the product for this basis, nvec and dtype: the row-per-lane or
+ * the term-parallel kernel (the latter for single vectors of operators whose
+ * off-diagonal entries only exchange antiparallel spins), and the pruned or
+ * the exhaustive rotation search (rings: rotation step one site).  The paper
+ * has no counterpart (its kernels are generated once for a CPU).  Every
+ * candidate runs a warm-up and three timed products (CUDA events on
+ * `stream`, best of three) on the caller's x and y (as ed_matvec: device,
+ * dim x nvec, 16-byte aligned; y is overwritten); the fastest is kept in the
+ * library's tuning table, keyed by (GPU name, n_sites, group order, spin
+ * inversion, log2 of the dimension, nvec, dtype, index kind), and used by
+ * every later product on a matching basis.  With the environment variable
+ * ED_TUNE_FILE naming a file, the table is read from it on first use and
+ * each choice is appended to it.  Synchronises `stream`.
+ *
+ *   out   host (may be NULL): kernel (0 the library's rule, 1 row-per-lane,
+ *         2 term-parallel), search (-1 not applicable, 0 every rotation,
+ *         1 pruned), index (1 hash, 2 bucketed), ms_default (the rule's
+ *         product), ms_best (the chosen one), variants_timed
+ * Errors: ED_ERR_INVALID_ARG, ED_ERR_SYMMETRY_MISMATCH, ED_ERR_CUDA.
+ */
+typedef struct {
+    int kernel;
+    int search;
+    int index;
+    double ms_default;
+    double ms_best;
+    int variants_timed;
+} ed_tune_result;
+
+ed_status ed_autotune(const ed_operator *op, const ed_basis *basis, const void *d_x, void *d_y, int nvec,
+                      ed_dtype dtype, ed_tune_result *out, void *stream);
+
+/*
+ * ed_autotune_index -- choose the index (hash index, or bucketed index with
+ * one 32-byte bucket per lookup) that later ed_basis_build calls make for
+ * sectors like this one (same GPU, n_sites, group order, spin inversion and
+ * log2 of the dimension): builds the sector with each index (arguments as
+ * ed_basis_build; both bases exist at once), runs ed_autotune on each with
+ * zero vectors of nvec columns of dtype from the library's memory pool, and
+ * keeps the faster index (written to ED_TUNE_FILE as ed_autotune does).  out
+ * receives the chosen index's result, with ms_default = the default product
+ * on the hash index.  Errors: as ed_basis_build and ed_autotune, ED_ERR_OOM.
+ */
+ed_status ed_autotune_index(const ed_operator *op, int n_sites, int n_up, int spin_inversion, int n_elems,
+                            const int32_t *perms, const double *chars, int nvec, ed_dtype dtype,
+                            ed_tune_result *out, void *stream);
 
 #ifdef __cplusplus
 }

@@ -519,6 +519,9 @@ namespace edk {
 
 OpView make_op_view(const ed_operator *op) { return op_view(op); }
 
+int index_policy_get() { return g_index_policy; }
+void index_policy_set(int policy) { g_index_policy = policy; }
+
 // Validated host tables for counting a sector with the generic group search
 // (used by the allocation-free count entry point).
 ed_status count_tables_host(int n_sites, int n_up, int spin_inversion, int n_elems,
@@ -645,12 +648,14 @@ ed_status ed_stream_status(void *stream)
         (void)cudaGetLastError();
         return ED_ERR_CUDA;
     }
-    unsigned int st = 0;
-    if (edk::basis_status_take(&st) != cudaSuccess) {
+    unsigned int st = 0, bst = 0;
+    if (edk::basis_status_take(&st) != cudaSuccess || edk::batch_status_take(&bst) != cudaSuccess) {
         (void)cudaGetLastError();
         return ED_ERR_CUDA;
     }
-    return st ? ED_ERR_INTERNAL : ED_OK;
+    if (st)
+        return ED_ERR_INTERNAL;
+    return (bst & edk::kStatusTimeout) ? ED_ERR_TIMEOUT : ED_OK;
 }
 
 const char *ed_status_string(ed_status s)
@@ -664,6 +669,7 @@ const char *ed_status_string(ed_status s)
     case ED_ERR_OOM: return "device out of memory";
     case ED_ERR_CUDA: return "CUDA runtime error";
     case ED_ERR_INTERNAL: return "device-side invariant check failed";
+    case ED_ERR_TIMEOUT: return "a bounded device-side wait ran out";
     case ED_ERR_NOT_CONVERGED: return "not converged";
     case ED_ERR_UNSUPPORTED: return "unsupported by this build";
     }
@@ -873,7 +879,11 @@ ed_status basis_build_impl(int n_sites, int n_up, int spin_inversion, int n_elem
         flag[0] |= (int)dev_status;
     }
     bool bucketed = false;
-    if (dim && g_index_policy != 1 && (g_index_policy == 2 || dim >= kBucketAutoDim)) {
+    // index kind: the test policy, else the autotuner's choice for sectors
+    // like this one, else the bucketed index from kBucketAutoDim states on
+    const int tuned = g_index_policy == 0 ? edk::tuned_index_kind(n_sites, b->order, spin_inversion != 0, dim) : 0;
+    const bool want_bucket = g_index_policy == 2 || (g_index_policy == 0 && (tuned ? tuned == 2 : dim >= kBucketAutoDim));
+    if (dim && want_bucket) {
         int nb = 1;
         while ((1 << nb) <= b->order)
             ++nb;
@@ -1092,8 +1102,8 @@ ed_status ed_matvec(const ed_operator *op, const ed_basis *b, const void *x, voi
         return st;
     if (!b->dim)
         return ED_OK;
-    ED_CUDA_TRY(edk::launch_matvec(op_view(op), b->group_view(), b->index_view(), !b->trivial_chars,
-                                   x, y, nvec, dtype, (cudaStream_t)stream));
+    ED_CUDA_TRY(edk::launch_matvec_v(op_view(op), b->group_view(), b->index_view(), !b->trivial_chars, x, y,
+                                     nvec, dtype, edk::tuned_variant(b, nvec, dtype), (cudaStream_t)stream));
     return ED_OK;
 }
 

@@ -39,6 +39,10 @@ struct EnumPlan {
 
 // Reads and clears the basis kernels' device status word (synchronous).
 cudaError_t basis_status_take(unsigned int *status);
+// Status word of the batched matvec launches: kStatusTimeout = a block gave up
+// a bounded wait.  Reads and clears the word of the current device.
+constexpr unsigned kStatusTimeout = 2u;
+cudaError_t batch_status_take(unsigned int *st);
 // Pass 1: per-chunk representative counts.
 cudaError_t launch_enum_count(const EnumPlan &plan, const GroupView &g, uint32_t *counts,
                               cudaStream_t stream);
@@ -99,6 +103,11 @@ ed_status count_tables_host(int n_sites, int n_up, int spin_inversion, int n_ele
                             std::vector<uint32_t> &chi_one);
 uint64_t binomial_host(int n, int k);
 
+// The index ed_basis_build makes (test hook and autotuner): 0 automatic,
+// 1 hash index, 2 bucketed index where its entry fits.
+int index_policy_get();
+void index_policy_set(int policy);
+
 // Operator/basis compatibility check (n_sites, symmetry); cached per basis.
 ed_status check_pair(const ed_operator *op, const ed_basis *b);
 OpView make_op_view(const ed_operator *op);
@@ -110,6 +119,22 @@ cudaError_t launch_count_nnz(const OpView &op, const GroupView &g, const IndexVi
 
 cudaError_t launch_matvec(const OpView &op, const GroupView &g, const IndexView &ix, bool track,
                           const void *x, void *y, int nvec, ed_dtype dtype, cudaStream_t stream);
+// A product variant: kernel 0 = the library's rule (use_term_parallel),
+// 1 = row-per-lane, 2 = term-parallel (where it applies); prune -1 = the
+// group's own setting, 0 = every rotation, 1 = the pruned search (rotation
+// step one site only).
+struct MatvecVariant {
+    int kernel = 0;
+    int prune = -1;
+};
+cudaError_t launch_matvec_v(const OpView &op, GroupView g, const IndexView &ix, bool track, const void *x,
+                            void *y, int nvec, ed_dtype dtype, MatvecVariant v, cudaStream_t stream);
+// The variant ed_autotune found fastest for this basis, nvec and dtype on the
+// current GPU (the default variant when none was tuned).
+MatvecVariant tuned_variant(const ed_basis *b, int nvec, ed_dtype dtype);
+// The index kind (1 hash, 2 bucketed) ed_autotune_index found faster for
+// sectors like this one on the current GPU, or 0 when none was tuned.
+int tuned_index_kind(int n_sites, int order, int flip, uint64_t dim);
 // The transposed (push) form, one vector, for the ablation hook: y zeroed,
 // then every contribution added atomically (order-dependent rounding).
 cudaError_t launch_matvec_push(const OpView &op, const GroupView &g, const IndexView &ix, bool track,

@@ -761,7 +761,7 @@ ed_status run_lanczos(const ed_operator *op, const ed_basis *b, const void *x0, 
         cudaError_t e = timer.mark(st);
         if (e == cudaSuccess)
             e = push ? launch_matvec_push(ov, gv, iv, track, in, out, dt, st)
-                     : launch_matvec(ov, gv, iv, track, in, out, 1, dt, st);
+                     : launch_matvec_v(ov, gv, iv, track, in, out, 1, dt, tuned_variant(b, 1, dt), st);
         if (e == cudaSuccess)
             e = timer.mark(st);
         return e;

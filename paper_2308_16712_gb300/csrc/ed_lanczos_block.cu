@@ -188,6 +188,10 @@ struct Prefetch {
     }
 };
 
+// Stride of the staged X tiles of the Gram kernel: one tile plus 8 floats, so
+// that the two matrices' elements of one row fall in different banks.
+template <int P> constexpr int kXStride = kTileRows * P + 8;
+
 // Gram entries of a tile: entries are taken in 2 x 2 groups (a0, a0+1) x
 // (b0, b0+1) of matrix m; a thread owns one group and a slice of the tile's
 // rows (rows sl, sl + SL, ...), sums its four entries over them in double-
@@ -225,7 +229,7 @@ struct GramLayout {
     static constexpr int E = NM * P * P;
 };
 
-template <int P, int NM, bool kYlow>
+template <int P, int NM, bool kYlow, int kXs = kTileRows * P>
 __device__ __forceinline__ void gram_tile(const float *sxh, const float *sxl, const float *syh, const float *syl,
                                           GramAcc &acc)
 {
@@ -235,7 +239,7 @@ __device__ __forceinline__ void gram_tile(const float *sxh, const float *sxl, co
         return;
     const int m = grp / (L::kHalf * L::kHalf), rem = grp % (L::kHalf * L::kHalf);
     const int a0 = 2 * (rem / L::kHalf), b0 = 2 * (rem % L::kHalf);
-    const float *xh = sxh + m * kTileRows * P, *xl = sxl + m * kTileRows * P;
+    const float *xh = sxh + m * kXs, *xl = sxl + m * kXs;
     float s[4] = {0.f, 0.f, 0.f, 0.f}, c[4] = {0.f, 0.f, 0.f, 0.f};
     for (int r = sl; r < kTileRows; r += L::kSlices) {
         const float x0h = xh[r * P + a0], x1h = xh[r * P + a0 + 1];
@@ -291,7 +295,7 @@ __global__ void __launch_bounds__(kBlThreads) k_dd_gram(const float *X0h, const 
 {
     if (*stop)
         return;
-    __shared__ float sxh[NM * kTileRows * P], sxl[NM * kTileRows * P];
+    __shared__ float sxh[NM * kXStride<P>], sxl[NM * kXStride<P>];
     __shared__ float syh[kTileRows * P], syl[kTileRows * P];
     __shared__ double red[kBlThreads * 4];
     GramAcc acc;
@@ -310,12 +314,12 @@ __global__ void __launch_bounds__(kBlThreads) k_dd_gram(const float *X0h, const 
     for (uint64_t t = blockIdx.x; t < tiles; t += gridDim.x) {
         p0.store(sxh, sxl);
         if (NM > 1)
-            p1.store(sxh + kTileRows * P, sxl + kTileRows * P);
+            p1.store(sxh + kXStride<P>, sxl + kXStride<P>);
         py.store(syh, syl);
         __syncthreads();
         if (t + gridDim.x < tiles)
             fetch(t + gridDim.x);
-        gram_tile<P, NM, YK != 0>(sxh, sxl, syh, syl, acc);
+        gram_tile<P, NM, YK != 0, kXStride<P>>(sxh, sxl, syh, syl, acc);
         __syncthreads();
     }
     gram_finish<P, NM>(acc, red, part, ticket, out);
@@ -890,6 +894,7 @@ ed_status run_block(const ed_operator *op, const ed_basis *b, const double *x0, 
     double *C = sm, *G = sm + 2 * P * P, *R1i = sm + 4 * P * P, *G2 = sm + 5 * P * P, *R2i = sm + 7 * P * P;
     int *stop = flags;
     const int yk = f32 ? 0 : 1;
+    const MatvecVariant tuned = tuned_variant(b, P, f32 ? ED_F32 : ED_F64);
     const void *Yh = f32 ? (const void *)W32 : (const void *)W64;
     auto bh = [&](int k) { return Vh + (size_t)(reorth ? k : (k & 1)) * blk; };
     auto bl = [&](int k) { return Vl + (size_t)(reorth ? k : (k & 1)) * blk; };
@@ -928,8 +933,8 @@ ed_status run_block(const ed_operator *op, const ed_basis *b, const double *x0, 
             if (!f32) {
                 k_dd_to_f64<<<vgrid, 256, 0, st>>>(Vjh, Vjl, V64, blk); count_launch();
             }
-            e = launch_matvec(ov, gv, iv, track, f32 ? (const void *)Vjh : (const void *)V64,
-                              f32 ? (void *)W32 : (void *)W64, P, f32 ? ED_F32 : ED_F64, st);
+            e = launch_matvec_v(ov, gv, iv, track, f32 ? (const void *)Vjh : (const void *)V64,
+                                f32 ? (void *)W32 : (void *)W64, P, f32 ? ED_F32 : ED_F64, tuned, st);
             if (e != cudaSuccess)
                 return e;
             if ((e = mark()) != cudaSuccess)

@@ -562,6 +562,9 @@ ed_status run_multi(const ed_operator *op, const ed_sector *sectors, int ns, int
             tiles += (b->dim + 31) / 32;
         }
         a.total_tiles = tiles;
+        const cudaError_t ce = batch_ctl(s, &a.ctl);  // first used in the eager step 0, before any capture
+        if (ce != cudaSuccess)
+            return ce;
         return multi_launch_any(a, track, single ? (C ? ED_C64 : ED_F32) : (C ? ED_C128 : ED_F64), s);
     };
 

@@ -18,6 +18,7 @@ static TpArgs<1> single_tp_args(const OpView &op, const GroupView &g, const Inde
     TpArgs<1> t;
     t.op = op;
     t.g = g;
+    t.ctl = BatchCtl{nullptr, nullptr, nullptr};  // one sector: static tiles, no gate
     t.n_sectors = 1;
     t.max_order = g.order;
     t.total_tiles = (ix.dim + 31) / 32;
@@ -60,7 +61,17 @@ cudaError_t launch_matvec_push(const OpView &op, const GroupView &g, const Index
 cudaError_t launch_matvec(const OpView &op, const GroupView &g, const IndexView &ix, bool track,
                           const void *x, void *y, int nvec, ed_dtype dtype, cudaStream_t stream)
 {
-    if ((ix.htab || ix.bkt) && use_term_parallel(nvec, op, dtype)) {
+    return launch_matvec_v(op, g, ix, track, x, y, nvec, dtype, MatvecVariant{}, stream);
+}
+
+cudaError_t launch_matvec_v(const OpView &op, GroupView g, const IndexView &ix, bool track, const void *x,
+                            void *y, int nvec, ed_dtype dtype, MatvecVariant v, cudaStream_t stream)
+{
+    if (v.prune >= 0 && g.fact && g.rot_d == 1)
+        g.prune = v.prune;
+    const bool tp_ok = (ix.htab || ix.bkt) && nvec == 1 && op.exchange_only;
+    const bool tp = tp_ok && (v.kernel == 2 || (v.kernel == 0 && use_term_parallel(nvec, op, dtype)));
+    if (tp) {
         const TpArgs<1> t = single_tp_args(op, g, ix, x, y);
         const int k = tp_index_kind(t.sec[0]);
         switch (dtype) {

@@ -7,6 +7,71 @@
 #include "ed_matvec_tp.cuh"
 
 namespace edk {
+
+// Per-device control words of the batched launches: a ring of work-queue
+// counters (a call takes the next one and zeroes it on its stream, so calls
+// in flight on different streams use different counters unless more than
+// kQueueRing overlap), the status word and the gate word of the stall test.
+namespace {
+constexpr int kQueueRing = 64;
+constexpr int kCtlDevices = 64;
+struct CtlWords {
+    unsigned long long *queues = nullptr;  // kQueueRing counters
+    unsigned int *status = nullptr;
+    int *gate = nullptr;                   // stays 0: nothing opens it
+    unsigned next = 0;
+};
+std::mutex g_ctl_mutex;
+CtlWords g_ctl[kCtlDevices];
+bool g_inject_stall = false;
+}  // namespace
+
+cudaError_t batch_ctl(cudaStream_t s, BatchCtl *out)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess)
+        return e;
+    if (dev < 0 || dev >= kCtlDevices)
+        return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(g_ctl_mutex);
+    CtlWords &c = g_ctl[dev];
+    if (!c.queues) {
+        void *p = nullptr;
+        const size_t bytes = kQueueRing * sizeof(unsigned long long) + 2 * sizeof(int);
+        if ((e = cudaMalloc(&p, bytes)) != cudaSuccess)
+            return e;
+        if ((e = cudaMemset(p, 0, bytes)) != cudaSuccess)
+            return e;
+        c.queues = static_cast<unsigned long long *>(p);
+        c.status = reinterpret_cast<unsigned int *>(c.queues + kQueueRing);
+        c.gate = reinterpret_cast<int *>(c.status + 1);
+    }
+    unsigned long long *q = c.queues + (c.next++ % kQueueRing);
+    if ((e = cudaMemsetAsync(q, 0, sizeof(*q), s)) != cudaSuccess)
+        return e;
+    *out = BatchCtl{q, c.status, g_inject_stall ? c.gate : nullptr};
+    return cudaSuccess;
+}
+
+cudaError_t batch_status_take(unsigned int *st)
+{
+    *st = 0;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess || dev < 0 || dev >= kCtlDevices)
+        return e;
+    std::lock_guard<std::mutex> lock(g_ctl_mutex);
+    CtlWords &c = g_ctl[dev];
+    if (!c.status)
+        return cudaSuccess;
+    if ((e = cudaMemcpy(st, c.status, sizeof(unsigned int), cudaMemcpyDeviceToHost)) != cudaSuccess)
+        return e;
+    return *st ? cudaMemset(c.status, 0, sizeof(unsigned int)) : cudaSuccess;
+}
+
+void set_inject_stall(bool on) { g_inject_stall = on; }
+
 cudaError_t multi_f64(const MultiArgs &a, bool track, cudaStream_t s) { return multi_dispatch_prec<double, false>(a, track, s); }
 cudaError_t multi_f32(const MultiArgs &a, bool track, cudaStream_t s) { return multi_dispatch_prec<float, false>(a, track, s); }
 cudaError_t multi_c128(const MultiArgs &a, bool track, cudaStream_t s) { return multi_dispatch_prec<double, true>(a, track, s); }
@@ -28,6 +93,7 @@ cudaError_t multi_launch_any(const MultiArgs &a, bool track, ed_dtype dtype, cud
         t.n_sectors = a.n_sectors;
         t.max_order = a.max_order;
         t.total_tiles = a.total_tiles;
+        t.ctl = a.ctl;
         for (int k = 0; k < a.n_sectors; ++k)
             t.sec[k] = a.sec[k];
         switch (dtype) {
@@ -47,6 +113,11 @@ cudaError_t multi_launch_any(const MultiArgs &a, bool track, ed_dtype dtype, cud
     return cudaErrorInvalidValue;
 }
 }  // namespace edk
+
+// Test hook: 1 = every later batched launch first waits on a gate word that
+// nothing opens (an injected stall of the producer); its bounded wait runs
+// out and ed_stream_status reports ED_ERR_TIMEOUT.
+extern "C" void edx_inject_stall(int on) { edk::set_inject_stall(on != 0); }
 
 extern "C" ed_status ed_matvec_multi(const ed_operator *op, const ed_sector *sectors, int n_sectors, int nvec,
                                      ed_dtype dtype, void *stream)
@@ -70,7 +141,17 @@ extern "C" ed_status ed_matvec_multi(const ed_operator *op, const ed_sector *sec
     bool track = false;
     int m = 0;
     uint64_t tiles = 0;
-    for (int s = 0; s < n_sectors; ++s) {
+    // the tile list (and the work queue) runs through the sectors largest first
+    std::vector<int> order(n_sectors);
+    for (int s = 0; s < n_sectors; ++s)
+        order[s] = s;
+    std::stable_sort(order.begin(), order.end(), [&](int u, int v) {
+        const uint64_t du = sectors[u].basis ? sectors[u].basis->dim : 0;
+        const uint64_t dv = sectors[v].basis ? sectors[v].basis->dim : 0;
+        return du > dv;
+    });
+    for (int oi = 0; oi < n_sectors; ++oi) {
+        const int s = order[oi];
         const ed_basis *b = sectors[s].basis;
         if (!b || b->n_sites != b0->n_sites || b->n_perm != b0->n_perm || b->perms != b0->perms)
             return ED_ERR_INVALID_ARG;  // every sector must use the same lattice permutations
@@ -132,7 +213,9 @@ extern "C" ed_status ed_matvec_multi(const ed_operator *op, const ed_sector *sec
                                   sectors[s].d_y, nvec, dtype, (cudaStream_t)stream);
         }
     } else {
-        e = multi_launch_any(args, track, dtype, (cudaStream_t)stream);
+        e = batch_ctl((cudaStream_t)stream, &args.ctl);
+        if (e == cudaSuccess)
+            e = multi_launch_any(args, track, dtype, (cudaStream_t)stream);
     }
     if (e != cudaSuccess) {
         (void)cudaGetLastError();

@@ -35,6 +35,68 @@ struct SectorDesc {
     int hbits, hwide, norm_bits, flip;
 };
 
+// ---------------------------------------------------------------------------
+// Work queue and failure detection of the batched (many-sector) launches.
+// Tiles are handed out by a device counter (warp lane 0 takes the next tile
+// with an atomic add), in the order of the sector table -- largest sectors
+// first -- so that the small sectors' tiles fill the tail of the launch.
+// Optionally (a test hook) every block first waits for a gate word that a
+// producer would set; the wait is bounded (0.5 s by the global timer, and an
+// iteration cap), and when it runs out the block records kStatusTimeout in
+// the status word and leaves without touching any vector: the launch ends,
+// the context stays usable, and ed_stream_status reports ED_ERR_TIMEOUT.
+// ---------------------------------------------------------------------------
+constexpr unsigned long long kGateTimeoutNs = 500000000ull;
+
+struct BatchCtl {
+    unsigned long long *queue;  // next tile to hand out, zeroed before the launch (null: static tiles)
+    unsigned int *status;       // device status word (or null)
+    const volatile int *gate;   // wait until *gate != 0 before any work (null: no wait)
+};
+
+__device__ __forceinline__ unsigned long long global_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Bounded wait of the block on the gate; false (status recorded) when it ran out.
+__device__ __forceinline__ bool pass_gate(const BatchCtl &c)
+{
+    __shared__ int open_gate;
+    if (threadIdx.x == 0) {
+        open_gate = 1;
+        if (c.gate) {
+            const unsigned long long t0 = global_ns();
+            for (int it = 0; *c.gate == 0; ++it) {
+                if (global_ns() - t0 > kGateTimeoutNs || it > (1 << 22)) {
+                    if (c.status)
+                        atomicOr(c.status, kStatusTimeout);
+                    open_gate = 0;
+                    break;
+                }
+                __nanosleep(1000);
+            }
+        }
+    }
+    __syncthreads();
+    return open_gate != 0;
+}
+
+// next tile of a warp: from the queue (lane 0's atomic add, broadcast), or
+// the static round-robin sequence gw, gw + nw, ... (k = tiles taken so far)
+__device__ __forceinline__ uint64_t next_tile(const BatchCtl &c, uint64_t &k, uint64_t gw, uint64_t nw)
+{
+    if (c.queue) {
+        unsigned long long t = 0;
+        if ((threadIdx.x & 31) == 0)
+            t = atomicAdd(c.queue, 1ull);
+        return __shfl_sync(0xffffffffu, t, 0);
+    }
+    return (k++) * nw + gw;
+}
+
 // the index of a basis as a sector descriptor sees it (the hash index, or the
 // bucketed index where the basis has one)
 inline void sector_index_from(SectorDesc &d, const ed_basis *b)
@@ -58,7 +120,8 @@ struct MultiArgs {
     int nvec;
     int max_order;            // largest expanded group order in the batch
     uint64_t total_tiles;
-    SectorDesc sec[kMaxSectors];
+    BatchCtl ctl;
+    SectorDesc sec[kMaxSectors];  // read from the launch parameters (constant bank)
 };
 
 template <typename W, typename T, bool kTrack, bool kFact>
@@ -81,7 +144,7 @@ __host__ __device__ inline size_t multi_smem_bytes(const GroupView &g, const OpV
 {
     size_t off[7];
     multi_smem_layout<W, T, kTrack, kFact>(g, op, n_sectors, max_order, off);
-    return align16(off[6] + (size_t)n_sectors * sizeof(SectorDesc));
+    return align16(off[6]);
 }
 
 // group search with a per-lane spin-inversion flag (the candidate loop itself
@@ -145,7 +208,9 @@ __global__ void __launch_bounds__(kMvThreads) k_matvec_multi(const __grid_consta
     uint8_t *sm_kind = smem + off[4];
     T *sm_sq = reinterpret_cast<T *>(smem + off[5]);
     T *sm_isq = sm_sq + (a.max_order + 1);
-    SectorDesc *sm_sec = reinterpret_cast<SectorDesc *>(smem + off[6]);
+    const SectorDesc *sm_sec = a.sec;  // launch parameters: warp-uniform reads
+    if (!pass_gate(a.ctl))
+        return;
     {
         const int nm = kFact ? a.g.n_cos : a.g.n_perm;
         const W *gm;
@@ -174,8 +239,6 @@ __global__ void __launch_bounds__(kMvThreads) k_matvec_multi(const __grid_consta
             sm_sq[e] = sqrt((T)e);
             sm_isq[e] = e ? T(1) / sqrt((T)e) : T(0);
         }
-        for (int e = threadIdx.x; e < a.n_sectors; e += blockDim.x)
-            sm_sec[e] = a.sec[e];
     }
     __syncthreads();
 
@@ -188,8 +251,6 @@ __global__ void __launch_bounds__(kMvThreads) k_matvec_multi(const __grid_consta
     const unsigned lanes_below = (1u << lane) - 1u;
     const uint64_t gw = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
-    // flat tile of the p-th row this warp takes, and its row within the tile
-    auto tile_of = [&](uint64_t p) { return (p >> 5) * nw + gw; };
     auto sector_of = [&](uint64_t tile) {
         int lo = 0, hi = a.n_sectors - 1;  // last sector with tile_begin <= tile
         while (lo < hi) {
@@ -251,13 +312,22 @@ __global__ void __launch_bounds__(kMvThreads) k_matvec_multi(const __grid_consta
                 store_cs(y + row * nvec + v, acc[v]);
     };
 
-    bool rows_left = tile_of(0) < a.total_tiles;
+    // The warp's rows come in the order of the tiles it takes: positions
+    // [base, base + 32) are the rows of tile t_cur, [base + 32, base + 64)
+    // those of t_nxt (taken when a ballot round reaches into it).
+    const uint64_t kNone = ~0ull;
+    uint64_t taken = 0, base = 0;
+    uint64_t t_cur = next_tile(a.ctl, taken, gw, nw), t_nxt = kNone;
+    bool rows_left = t_cur < a.total_tiles;
     while (true) {
         unsigned need = __ballot_sync(kAll, !has);
         while (need != 0 && rows_left) {
+            const uint32_t cnt = __popc(need);
+            if (next + cnt > base + 32 && t_nxt == kNone)
+                t_nxt = next_tile(a.ctl, taken, gw, nw);
             const uint64_t p = next + __popc(need & lanes_below);
-            next += __popc(need);
-            const uint64_t tile = tile_of(p);
+            next += cnt;
+            const uint64_t tile = p < base + 32 ? t_cur : t_nxt;
             if (!has && tile < a.total_tiles) {
                 sec = sector_of(tile);
                 const SectorDesc &sd = sm_sec[sec];
@@ -312,7 +382,14 @@ __global__ void __launch_bounds__(kMvThreads) k_matvec_multi(const __grid_consta
                         store_row();
                 }
             }
-            rows_left = tile_of(next) < a.total_tiles;
+            if (next >= base + 32) {
+                base += 32;
+                t_cur = t_nxt;
+                t_nxt = kNone;
+                if (t_cur == kNone)
+                    t_cur = next_tile(a.ctl, taken, gw, nw);
+            }
+            rows_left = t_cur < a.total_tiles;
             need = __ballot_sync(kAll, !has);
         }
         if (need == kAll)
@@ -421,6 +498,11 @@ cudaError_t multi_dispatch_prec(const MultiArgs &a, bool track, cudaStream_t str
 #undef ED_MM_FA
 #undef ED_MM_NV
 }
+
+// control words of a batched launch on stream s (a fresh work-queue counter,
+// zeroed on s; the status word; the gate when a stall is injected)
+cudaError_t batch_ctl(cudaStream_t s, BatchCtl *out);
+void set_inject_stall(bool on);
 
 cudaError_t multi_f64(const MultiArgs &a, bool track, cudaStream_t s);
 cudaError_t multi_f32(const MultiArgs &a, bool track, cudaStream_t s);

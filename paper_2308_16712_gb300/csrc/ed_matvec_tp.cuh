@@ -37,7 +37,8 @@ struct TpArgs {
     int n_sectors;
     int max_order;          // largest expanded group order among the sectors
     uint64_t total_tiles;
-    SectorDesc sec[kSec];
+    BatchCtl ctl;           // work queue, status word, gate (zero: static tiles, no wait)
+    SectorDesc sec[kSec];   // read from the launch parameters (constant bank)
 };
 
 // per-warp scratch: the tile's rows
@@ -68,8 +69,9 @@ __host__ __device__ inline void tp_smem_layout(const GroupView &g, const OpView 
     off[3] = align16(off[2] + (size_t)op.n_mats * 16 * sizeof(Cplx<T>));         // offmask
     off[4] = align16(off[3] + (size_t)op.n_mats * 4);                            // coset kinds
     off[5] = align16(off[4] + (kFact ? (size_t)g.n_cos : 0));                    // sqrt tables
-    off[6] = align16(off[5] + 2 * (size_t)(max_order + 1) * sizeof(T));          // sectors
-    off[7] = align16(off[6] + (size_t)n_sectors * sizeof(SectorDesc));           // warps
+    off[6] = align16(off[5] + 2 * (size_t)(max_order + 1) * sizeof(T));          // (sectors: parameters)
+    off[7] = off[6];                                                             // warps
+    (void)n_sectors;
 }
 
 template <typename W, typename T, typename V>
@@ -154,7 +156,7 @@ __global__ void __launch_bounds__(kTpThreads, 8) k_matvec_tp(const __grid_consta
     uint8_t *sm_kind = smem + off[4];
     T *sm_sq = reinterpret_cast<T *>(smem + off[5]);
     T *sm_isq = sm_sq + (a.max_order + 1);
-    SectorDesc *sm_sec = reinterpret_cast<SectorDesc *>(smem + off[6]);
+    const SectorDesc *sm_sec = a.sec;  // launch parameters: warp-uniform reads
     TpWarp<W, T, V> *sm_warp = reinterpret_cast<TpWarp<W, T, V> *>(smem + off[7]);
     const int tstride = tp_term_stride(a.g, a.op);
     uint8_t *sm_terms = smem + tp_terms_offset<W, T, V>(off[7]) + (size_t)(threadIdx.x >> 5) * 32 * tstride;
@@ -186,10 +188,9 @@ __global__ void __launch_bounds__(kTpThreads, 8) k_matvec_tp(const __grid_consta
             sm_sq[e] = sqrt((T)e);
             sm_isq[e] = e ? T(1) / sqrt((T)e) : T(0);
         }
-        for (int e = threadIdx.x; e < a.n_sectors; e += blockDim.x)
-            sm_sec[e] = a.sec[e];
     }
-    __syncthreads();
+    if (!pass_gate(a.ctl))  // includes the barrier after the table loads
+        return;
 
     const unsigned kAll = 0xffffffffu;
     const int n_fam = a.op.n_fam;
@@ -200,7 +201,9 @@ __global__ void __launch_bounds__(kTpThreads, 8) k_matvec_tp(const __grid_consta
     const uint64_t gw = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
 
-    for (uint64_t tile = gw; tile < a.total_tiles; tile += nw) {
+    uint64_t taken = 0;
+    for (uint64_t tile = next_tile(a.ctl, taken, gw, nw); tile < a.total_tiles;
+         tile = next_tile(a.ctl, taken, gw, nw)) {
         int sec = 0;
         if (kSec > 1) {  // last sector with tile_begin <= tile (warp-uniform)
             int lo = 0, hi = a.n_sectors - 1;

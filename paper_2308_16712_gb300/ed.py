@@ -26,7 +26,7 @@ ED_LANCZOS_VALUES_ONLY = 128
 STATUS_NAMES = {
     0: "ED_OK", 1: "ED_ERR_INVALID_ARG", 2: "ED_ERR_NOT_A_GROUP", 3: "ED_ERR_BAD_CHARACTER",
     4: "ED_ERR_SYMMETRY_MISMATCH", 5: "ED_ERR_OOM", 6: "ED_ERR_CUDA", 7: "ED_ERR_INTERNAL",
-    8: "ED_ERR_NOT_CONVERGED", 9: "ED_ERR_UNSUPPORTED",
+    8: "ED_ERR_NOT_CONVERGED", 9: "ED_ERR_UNSUPPORTED", 10: "ED_ERR_TIMEOUT",
 }
 
 if not os.path.exists(LIB_PATH):
@@ -40,6 +40,11 @@ _i32, _u64, _i64, _d = ctypes.c_int, ctypes.c_uint64, ctypes.c_int64, ctypes.c_d
 
 class Sector(ctypes.Structure):
     _fields_ = [("basis", ctypes.c_void_p), ("d_x", ctypes.c_void_p), ("d_y", ctypes.c_void_p)]
+
+
+class TuneResult(ctypes.Structure):
+    _fields_ = [("kernel", ctypes.c_int), ("search", ctypes.c_int), ("index", ctypes.c_int),
+                ("ms_default", ctypes.c_double), ("ms_best", ctypes.c_double), ("variants_timed", ctypes.c_int)]
 
 
 class LanczosInfo(ctypes.Structure):
@@ -71,11 +76,15 @@ _SIGS = {
                                 ctypes.POINTER(LanczosInfo), _P]),
     "ed_lanczos_multi": (_i32, [_P, _P, _i32, _i32, _i32, _i32, ctypes.POINTER(_d),
                                 ctypes.POINTER(LanczosInfo), _P]),
+    "ed_autotune": (_i32, [_P, _P, _P, _P, _i32, _i32, ctypes.POINTER(TuneResult), _P]),
+    "ed_autotune_index": (_i32, [_P, _i32, _i32, _i32, _i32, _P, _P, _i32, _i32, ctypes.POINTER(TuneResult), _P]),
+    "edx_tune_reset": (None, []),
     "ed_basis_count_noalloc": (_i32, [_i32, _i32, _i32, _i32, _P, _P, _P, ctypes.POINTER(_u64)]),
     "edx_launch_count": (ctypes.c_ulonglong, []),
     "edx_force_generic": (None, [_i32]),
     "edx_force_all_rotations": (None, [_i32]),
     "edx_index_policy": (None, [_i32]),
+    "edx_inject_stall": (None, [_i32]),
     "edx_peak": (_d, [_i32, _P, _u64, ctypes.POINTER(_d), _P]),
     "edx_basis_bucket": (_i32, [_P, ctypes.POINTER(_i32), ctypes.POINTER(ctypes.c_uint32)]),
     "edx_count_nnz": (_i32, [_P, _P, ctypes.POINTER(ctypes.c_ulonglong)]),
@@ -320,6 +329,46 @@ def peak(kind: str, buf=None, stream=None):
     if r < 0:
         raise RuntimeError(f"edx_peak({kind}) failed")
     return r, ms.value
+
+
+def _dtype_code(t):
+    import torch
+    return {torch.float64: ED_F64, torch.float32: ED_F32, torch.complex128: ED_C128,
+            torch.complex64: ED_C64}[t.dtype]
+
+
+def autotune(op: Operator, basis: Basis, x, y, nvec: int = 1, stream=None) -> dict:
+    """ed_autotune: time the product variants for this basis on x (y is
+    overwritten) and keep the fastest for later products."""
+    r = TuneResult()
+    _check(_lib.ed_autotune(op.handle, basis.handle, _ptr(x), _ptr(y), nvec, _dtype_code(x), ctypes.byref(r),
+                            _stream(stream)), "ed_autotune")
+    return {k: getattr(r, k) for k, _ in TuneResult._fields_}
+
+
+def autotune_index(op: Operator, n_sites: int, n_up: int, spin_inversion: int, perms, chars, nvec: int = 1,
+                   dtype: int = ED_F32, stream=None) -> dict:
+    """ed_autotune_index: build the sector with each index, keep the faster one
+    for later builds of sectors like it."""
+    p = _host(perms, np.int32)
+    c = _host(chars, np.float64)
+    r = TuneResult()
+    _check(_lib.ed_autotune_index(op.handle, n_sites, n_up, spin_inversion, p.shape[0],
+                                  p.ctypes.data_as(_P), c.ctypes.data_as(_P), nvec, dtype, ctypes.byref(r),
+                                  _stream(stream)), "ed_autotune_index")
+    return {k: getattr(r, k) for k, _ in TuneResult._fields_}
+
+
+def tune_reset() -> None:
+    """Test hook: forget every tuned choice."""
+    _lib.edx_tune_reset()
+
+
+def inject_stall(on: bool) -> None:
+    """Test hook: later batched launches wait on a gate that nothing opens
+    (an injected producer stall); the bounded wait runs out and
+    stream_status() returns ED_ERR_TIMEOUT (10)."""
+    _lib.edx_inject_stall(1 if on else 0)
 
 
 def count_nnz(op: Operator, basis: Basis) -> int:

@@ -84,3 +84,38 @@ def test_multi_rejects_mixed_groups():
     with pytest.raises(ed.EDError) as e:
         ed.matvec_multi(O, [(B1, x1, torch.empty_like(x1)), (B2, x2, torch.empty_like(x2))])
     assert e.value.status == 1
+
+
+@pytest.mark.parametrize("nvec,dt", [(1, "complex64"), (8, "complex128")])
+def test_injected_stall_times_out_and_the_context_survives(nvec, dt):
+    """Failure detection of the batched launch: with a stall injected (every
+    block first waits on a gate word that nothing opens) the bounded wait runs
+    out, ed_stream_status reports ED_ERR_TIMEOUT, the outputs are untouched,
+    and the next launch on the same context computes the right products."""
+    torch, ed = gpu()
+    n = 12
+    op = ei.xxz_ring(n, 1.0, 1.5)
+    O = ed.operator_create(n, op["sites"], op["coeff"], op["local"])
+    dtype = getattr(torch, dt)
+    items = []
+    for n_up, z, p, c in xxz_sectors(n)[:9]:
+        B = ed.basis_build(n, n_up, z, p, c)
+        st, _ = ed.basis_states(B)
+        x = ei.x_by_state_torch(5, st, nvec, True, dtype=dtype).contiguous()
+        items.append((B, x, torch.full_like(x, 7.0)))
+    assert ed.stream_status() == 0
+    ed.inject_stall(True)
+    try:
+        ed.matvec_multi(O, items, nvec)
+        assert ed.stream_status() == 10  # ED_ERR_TIMEOUT
+    finally:
+        ed.inject_stall(False)
+    for _, _, y in items:
+        assert bool((y == 7.0).all())
+    assert ed.stream_status() == 0
+    ed.matvec_multi(O, items, nvec)
+    assert ed.stream_status() == 0
+    for B, x, y in items:
+        y1 = torch.empty_like(x)
+        ed.matvec(O, B, x, y1, nvec)
+        assert torch.equal(y, y1)
