@@ -546,9 +546,14 @@ def run_multi(args):
             return best
 
         ms_multi = timed(lambda: ed.matvec_multi(O, items, nvec))
+        ed.multi_policy("batched")
+        try:
+            ms_batched = timed(lambda: ed.matvec_multi(O, items, nvec))
+        finally:
+            ed.multi_policy("auto")
         ms_single = timed(lambda: [ed.matvec(O, b, x, y, nvec) for b, x, y in items])
         out[str(dt).replace("torch.", "")] = {
-            "multi_ms": ms_multi, "per_sector_ms": ms_single,
+            "multi_ms": ms_multi, "batched_launch_ms": ms_batched, "per_sector_ms": ms_single,
             "vector_rows_per_s_multi": nvec * sum(dims) / (ms_multi * 1e-3),
             "vector_rows_per_s_per_sector": nvec * sum(dims) / (ms_single * 1e-3)}
         del items
@@ -670,6 +675,13 @@ def run_job(args, w):
         e1.record(stream)
         torch.cuda.synchronize()
         return e0.elapsed_time(e1), res
+
+    # ---- the product variant for the batched fp32 block, chosen by the
+    # library's autotuner on this GPU (the timed steps then use it) -----------
+    xt = X0.to(torch.float32)
+    tuning = ed.autotune(O, B, xt, torch.empty_like(xt), nvec)
+    del xt
+    torch.cuda.empty_cache()
 
     # ---- FP32 batched: block-Lanczos steps (the timed headline) --------------
     ed.lanczos_block(O, B, X0, nvec, args.warmup, ed.ED_LANCZOS_F32_MATVEC | VO)
@@ -823,6 +835,9 @@ def run_job(args, w):
                 "d2h_bytes_per_step": 8 * nvec / args.steps,
                 "path": "pinned host start block -> device, ed_lanczos_block over the same steps, Ritz "
                         "values -> host"},
+        "autotune": {"product": tuning, "kernel_names": {"0": "library rule", "1": "row-per-lane",
+                                                          "2": "term-parallel"},
+                     "search_names": {"-1": "n/a", "0": "every rotation", "1": "pruned to the longest runs"}},
         "gpu_launches": launches,
         "clocks": clocks,
         "secondary": secondary,

@@ -253,10 +253,7 @@ typedef struct {
  * batch of sectors of uneven dimension, so that no launch tail is paid per
  * sector).  The launch's warps take 32-row tiles from a device work queue (an
  * atomic counter over the tiles of all sectors, largest sectors first), the
- * role the paper's producer/consumer balancing plays across nodes; when every
- * sector alone fills the GPU and the term-parallel kernel applies, one
- * launch per sector is issued instead (measured faster for sectors of about a
- * million rows).  Every basis must be built from the same n_sites and the same list
+ * role the paper's producer/consumer balancing plays across nodes.  Every basis must be built from the same n_sites and the same list
  * of lattice permutations (characters, spin inversion and n_up may differ);
  * dtype must be complex if any sector is.  Sectors with dimension 0 are
  * skipped.  Results equal those of ed_matvec on each sector, bit for bit.
@@ -420,9 +417,8 @@ ed_status ed_lanczos_block(const ed_operator *op, const ed_basis *basis, const v
  * sectors, by the recurrence of ed_lanczos run on all sectors together
  * (Sec. "Introduction": symmetries make H block diagonal, one independent
  * eigenproblem of reduced dimension per block; here many blocks at once).
- * Every product is one multi-sector launch as in ed_matvec_multi, or, when
- * every sector alone fills the GPU (at least one row per resident thread), one
- * ed_matvec launch per sector; the vector updates and the compensated fp64 dot
+ * Every product is one multi-sector launch as in ed_matvec_multi (tiles from
+ * a device work queue); the vector updates and the compensated fp64 dot
  * products are segmented per sector; each run of steps is captured once as a
  * CUDA graph of two steps and replayed.
  * The sectors follow the rules of ed_matvec_multi (same n_sites and lattice

@@ -504,17 +504,16 @@ ed_status run_multi(const ed_operator *op, const ed_sector *sectors, int ns, int
         ref_st.base = p;
     }
 
-    // The products: one multi-sector launch, or one ed_matvec launch per
-    // sector when every sector alone fills the GPU (one row per resident
-    // thread), where separate launches are faster than the per-lane sector
-    // indirection of the multi-sector kernel.
+    // The products: one multi-sector launch fed by the device work queue (one
+    // ed_matvec launch per sector only under the per-sector test policy, for
+    // sectors that each fill the GPU).
     int dev = 0, sms = 0;
     LM_TRY(cudaGetDevice(&dev));
     LM_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     uint64_t min_dim = ~0ull;
     for (int k = 0; k < ns; ++k)
         min_dim = std::min<uint64_t>(min_dim, sectors[k].basis->dim);
-    const bool per_sector = min_dim >= (uint64_t)sms * 2048;
+    const bool per_sector = multi_policy_get() == 2 && min_dim >= (uint64_t)sms * 2048;
     const OpView ov = make_op_view(op);
     const ed_basis *b0 = sectors[0].basis;
     bool track = false;

@@ -503,6 +503,7 @@ cudaError_t multi_dispatch_prec(const MultiArgs &a, bool track, cudaStream_t str
 // zeroed on s; the status word; the gate when a stall is injected)
 cudaError_t batch_ctl(cudaStream_t s, BatchCtl *out);
 void set_inject_stall(bool on);
+int multi_policy_get();
 
 cudaError_t multi_f64(const MultiArgs &a, bool track, cudaStream_t s);
 cudaError_t multi_f32(const MultiArgs &a, bool track, cudaStream_t s);

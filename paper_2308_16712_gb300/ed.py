@@ -85,6 +85,7 @@ _SIGS = {
     "edx_force_all_rotations": (None, [_i32]),
     "edx_index_policy": (None, [_i32]),
     "edx_inject_stall": (None, [_i32]),
+    "edx_multi_policy": (None, [_i32]),
     "edx_peak": (_d, [_i32, _P, _u64, ctypes.POINTER(_d), _P]),
     "edx_basis_bucket": (_i32, [_P, ctypes.POINTER(_i32), ctypes.POINTER(ctypes.c_uint32)]),
     "edx_count_nnz": (_i32, [_P, _P, ctypes.POINTER(ctypes.c_ulonglong)]),
@@ -362,6 +363,11 @@ def autotune_index(op: Operator, n_sites: int, n_up: int, spin_inversion: int, p
 def tune_reset() -> None:
     """Test hook: forget every tuned choice."""
     _lib.edx_tune_reset()
+
+
+def multi_policy(policy: str) -> None:
+    """Test hook: "auto", "batched" (always one launch) or "per_sector"."""
+    _lib.edx_multi_policy({"auto": 0, "batched": 1, "per_sector": 2}[policy])
 
 
 def inject_stall(on: bool) -> None:
