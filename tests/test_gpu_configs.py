@@ -177,8 +177,8 @@ def test_xxz28_all_sectors():
         assert torch.equal(y, y1)
     del items
     torch.cuda.empty_cache()
-    # one vector in single precision: per-sector term-parallel launches inside
-    # the batched call (every sector fills the GPU), the same bits as ed_matvec
+    # one vector in single precision: the batched term-parallel launch (tiles
+    # from the work queue), the same bits as ed_matvec
     items = []
     for s in sectors[::5]:
         B = ed.basis_build(28, s["n_up"], s["spin_inversion"], s["perms"], s["chars"])
