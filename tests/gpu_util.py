@@ -35,6 +35,17 @@ def to_torch(a, dtype):
     return torch.from_numpy(np.ascontiguousarray(a).astype(dtype)).cuda()
 
 
+def elem_rel_err(got, want, floor=1e-3):
+    """Largest element-wise relative error over the elements whose magnitude is
+    at least `floor` times the largest (where a relative error is meaningful)."""
+    got = np.asarray(got)
+    want = np.asarray(want)
+    if not want.size:
+        return 0.0
+    big = np.abs(want) >= floor * np.abs(want).max()
+    return float((np.abs(got - want)[big] / np.abs(want)[big]).max()) if big.any() else 0.0
+
+
 def rel_err(got, want):
     got = np.asarray(got)
     want = np.asarray(want)

@@ -12,7 +12,7 @@ import pytest
 
 import ed_inputs as ei
 import oracle
-from gpu_util import build_pair, gpu, gpu_basis_numpy, rel_err, to_torch
+from gpu_util import build_pair, elem_rel_err, gpu, gpu_basis_numpy, rel_err, to_torch
 
 pytestmark = pytest.mark.gpu
 
@@ -167,6 +167,8 @@ def test_matvec_f64_parity(case, nvec):
     ed.matvec(S["O"], S["B"], xt, yt, nvec)
     got = yt.cpu().numpy()
     assert rel_err(got, want if cplx else want.real) < F64_TOL
+    # element-wise, where a relative error is meaningful
+    assert elem_rel_err(got, want if cplx else want.real, 1e-3) < 1e-9
     # determinism: a second product is bit-identical
     y2 = torch.empty_like(xt)
     ed.matvec(S["O"], S["B"], xt, y2, nvec)
