@@ -445,17 +445,32 @@ def run_solve(args, w):
     build_s = time.perf_counter() - t0
     dim = ed.basis_size(B)
     cplx = not ed.basis_is_real(B)
-    x0 = torch.from_numpy(ei.x_by_index(0, dim, 1, cplx)[:, 0]).cuda()
+    if dim <= 1 << 30:
+        x0 = torch.from_numpy(ei.x_by_index(0, dim, 1, cplx)[:, 0]).cuda()
+        x0_kind = "uniform[-1,1) keyed by index, seed 0"
+    else:  # billions of rows: generated on the device, keyed by state
+        states, _ = ed.basis_states(B)
+        x0 = ei.x_by_state_torch_chunked(0, states, 1, cplx).reshape(-1)
+        del states
+        torch.cuda.synchronize()
+        torch.cuda.empty_cache()  # the generator's temporaries, for the solver's vectors
+        ed.release_cached_memory()
+        x0_kind = "uniform[-1,1) keyed by state, seed 0"
     out = {"mode": "solve", "workload": w["name"], "dim": dim, "basis_build_s": build_s,
-           "lanczos_steps": w["lanczos_steps"]}
-    for name, mode in (("f32_matvec", ed.ED_LANCZOS_F32_MATVEC), ("f64", ed.ED_LANCZOS_F64)):
+           "lanczos_steps": w["lanczos_steps"], "x0": x0_kind,
+           "index": "bucketed" if ed.basis_bucket(B)[0] else "hash"}
+    modes = [m for m in (("f32_matvec", ed.ED_LANCZOS_F32_MATVEC), ("f64", ed.ED_LANCZOS_F64))
+             if m[0] in args.solve_modes.split(",")]
+    for name, mode in modes:
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         r = ed.lanczos(O, B, x0, w["lanczos_steps"], mode)
         torch.cuda.synchronize()
         out[name] = {"e0": r.e0, "ritz": r.ritz, "residual": r.residual, "matvecs": r.matvecs,
                      "matvec_ms": r.matvec_ms, "wall_s": time.perf_counter() - t0}
-    out["dE0"] = abs(out["f32_matvec"]["e0"] - out["f64"]["e0"])
+    if len(modes) == 2:
+        out["dE0"] = abs(out["f32_matvec"]["e0"] - out["f64"]["e0"])
+    out["device_gb_peak"] = torch.cuda.max_memory_allocated() / 1e9
     print(json.dumps(out), flush=True)
 
 
@@ -858,6 +873,8 @@ def main():
                     help="block steps of the full FP32 batched solve behind dE0")
     ap.add_argument("--lanczos-steps", type=int, default=100,
                     help="Lanczos steps of the batched solve in --mode multi (0: skip)")
+    ap.add_argument("--solve-modes", default="f32_matvec,f64",
+                    help="Lanczos modes of --mode solve (comma-separated: f32_matvec, f64)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--mode", default="job", choices=["job", "matvec", "step", "solve", "multi", "push",
                                                       "peaks", "block"],

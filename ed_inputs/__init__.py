@@ -271,6 +271,12 @@ def workload(name: str) -> dict:
         p, c = ring_group(42, 0, parity=+1)
         return dict(name=name, n_sites=42, n_up=21, spin_inversion=+1, perms=p, chars=c,
                     op=heisenberg_ring(42), complex_=False, lanczos_steps=150)
+    if name == "ring42_pi":
+        # for n = 2 mod 4 the ground state lies at momentum pi, reflection +1,
+        # spin inversion -1 (a sector of the same dimension as k = 0, z = +1)
+        p, c = ring_group(42, 21, parity=+1)
+        return dict(name=name, n_sites=42, n_up=21, spin_inversion=-1, perms=p, chars=c,
+                    op=heisenberg_ring(42), complex_=False, lanczos_steps=150)
     if name == "torus6x6":
         p, c = torus_group(6, 6, 1, 0)
         return dict(name=name, n_sites=36, n_up=18, spin_inversion=+1, perms=p, chars=c,

@@ -119,7 +119,11 @@ ed_status ed_stream_status(void *stream);
  *
  * The call synchronises `stream` (to size its arrays) and returns with the
  * basis ready; its large arrays come from the library's memory pool (see
- * ed_release_cached_memory).  Errors:
+ * ed_release_cached_memory).  Device memory per state: 10 bytes (states and
+ * norms) plus about 1 byte of prefix table, plus the index: about 18-36 bytes
+ * for the bucketed index (sectors of 2^23 states or more; 32-byte buckets,
+ * one per 1.8 states or fewer), else 10-20 bytes for the hash index and 8 for
+ * packed (state, norm) keys.  Errors:
  * ED_ERR_INVALID_ARG, ED_ERR_NOT_A_GROUP, ED_ERR_BAD_CHARACTER, ED_ERR_OOM,
  * ED_ERR_CUDA, ED_ERR_INTERNAL.
  */
@@ -272,8 +276,9 @@ ed_status ed_matvec_multi(const ed_operator *op, const ed_sector *sectors, int n
 typedef enum {
     ED_LANCZOS_F64 = 0,        /* fp64 matvec, fp64 recurrence                     */
     ED_LANCZOS_F32_MATVEC = 1, /* fp32 matvec, fp64 recurrence and fp64 refinement */
-    ED_LANCZOS_RECOMPUTE = 16, /* flag: form the Ritz vector by a second pass even
-                                  when the Krylov vectors would fit in memory      */
+    ED_LANCZOS_RECOMPUTE = 16, /* flag: form the Ritz vector (and that of the fp64
+                                  refinement) by a second pass even when the
+                                  Krylov vectors would fit in memory              */
     ED_LANCZOS_PUSH = 32,      /* flag (ed_lanczos only): products by the transposed
                                   ("push") form -- every term added to y at its
                                   representative's index with an atomic add, the
@@ -327,8 +332,11 @@ typedef struct {
  * tridiagonal eigensolve run in fp64 on the GPU.  The Ritz vector is formed
  * from stored Krylov vectors when they fit in device memory, else by a second,
  * bit-identical pass of the recurrence.  It is then refined in fp64: a few
- * fp64 Lanczos steps started from it, whose lowest Ritz value is returned
- * together with its residual.  Takes its work vectors from the library's
+ * fp64 Lanczos steps started from it (their vectors stored, or recomputed by
+ * a second pass in the same way), whose lowest Ritz value is returned
+ * together with its residual.  Work memory beyond the caller's vectors: four
+ * fp64 vectors, plus two fp32 vectors in the fp32-matvec mode, when the
+ * Krylov vectors are not stored.  Takes its work vectors from the library's
  * memory pool (see ed_release_cached_memory); synchronises `stream` before
  * returning.
  * Errors: ED_ERR_INVALID_ARG, ED_ERR_SYMMETRY_MISMATCH, ED_ERR_UNSUPPORTED

@@ -858,13 +858,34 @@ ed_status run_lanczos(const ed_operator *op, const ed_basis *b, const void *x0, 
     // fp64 refinement from the fp32-matvec Ritz vector: a short fp64 Lanczos run
     D *u = psi;
     if (f32) {
+        // its mref + 1 vectors go into the main pass's Krylov store (no longer
+        // needed once psi is formed) or a new one if that fits in half of the
+        // free memory; else the Ritz vector comes from a second pass that
+        // starts from psi and accumulates into it (psi is read only before
+        // the first accumulation)
         D *Vr = nullptr;
-        ED_L_TRY(S.get(&Vr, (size_t)(mref + 1) * n));
+        if (store && steps >= mref) {
+            Vr = V;
+        } else if (!recompute) {
+            cudaMemGetInfo(&free_b, &total_b);
+            free_b += ws_cached_bytes();
+            if ((double)(mref + 1) * vec_bytes < 0.5 * (double)free_b)
+                ED_L_TRY(S.get(&Vr, (size_t)(mref + 1) * n));
+        }
+        const bool store_r = Vr != nullptr;
+        if (!store_r && !ring[0]) {
+            ED_L_TRY(S.get(&ring[0], n));
+            ED_L_TRY(S.get(&ring[1], n));
+        }
         ED_L_TRY(cudaMemsetAsync(beta, 0, (mmax + 2) * sizeof(double), st));
         ED_L_TRY(run(psi, mref, false, Vr, nullptr));
         ED_L_TRY(cudaMemsetAsync(y, 0, (mmax + 1) * sizeof(double), st));
         k_tridiag_lowest<<<1, 32, 0, st>>>(alpha, beta, mref, y, scal + 1, m_eff, work); count_launch();
-        k_combine<kC><<<vgrid, kRedThreads, 0, st>>>(psi, Vr, y, m_eff, n); count_launch();
+        if (store_r) {
+            k_combine<kC><<<vgrid, kRedThreads, 0, st>>>(psi, Vr, y, m_eff, n); count_launch();
+        } else {
+            ED_L_TRY(run(psi, mref, false, nullptr, y));
+        }
         ED_L_TRY(cudaGetLastError());
     }
     // fp64 Rayleigh quotient and residual of the final vector u

@@ -98,6 +98,18 @@ __device__ __forceinline__ void dd_acc(float xh, float xl, float yh, float yl, f
     s = t;
 }
 
+// dd_acc for a y that is exactly a float (low word zero): one FMA fewer
+__device__ __forceinline__ void dd_acc1(float xh, float xl, float yh, float &s, float &c)
+{
+    const float p = xh * yh;
+    float e = fmaf(xh, yh, -p);
+    e = fmaf(xl, yh, e);
+    const float t = s + p;
+    const float z = t - s;
+    c += ((s - (t - z)) + (p - z)) + e;
+    s = t;
+}
+
 __device__ __forceinline__ void dd_split(double x, float &h, float &l)
 {
     h = (float)x;
@@ -245,11 +257,18 @@ __device__ __forceinline__ void gram_tile(const float *sxh, const float *sxl, co
         const float x0h = xh[r * P + a0], x1h = xh[r * P + a0 + 1];
         const float x0l = xl[r * P + a0], x1l = xl[r * P + a0 + 1];
         const float y0h = syh[r * P + b0], y1h = syh[r * P + b0 + 1];
-        const float y0l = kYlow ? syl[r * P + b0] : 0.f, y1l = kYlow ? syl[r * P + b0 + 1] : 0.f;
-        dd_acc(x0h, x0l, y0h, y0l, s[0], c[0]);
-        dd_acc(x0h, x0l, y1h, y1l, s[1], c[1]);
-        dd_acc(x1h, x1l, y0h, y0l, s[2], c[2]);
-        dd_acc(x1h, x1l, y1h, y1l, s[3], c[3]);
+        if constexpr (kYlow) {
+            const float y0l = syl[r * P + b0], y1l = syl[r * P + b0 + 1];
+            dd_acc(x0h, x0l, y0h, y0l, s[0], c[0]);
+            dd_acc(x0h, x0l, y1h, y1l, s[1], c[1]);
+            dd_acc(x1h, x1l, y0h, y0l, s[2], c[2]);
+            dd_acc(x1h, x1l, y1h, y1l, s[3], c[3]);
+        } else {
+            dd_acc1(x0h, x0l, y0h, s[0], c[0]);
+            dd_acc1(x0h, x0l, y1h, s[1], c[1]);
+            dd_acc1(x1h, x1l, y0h, s[2], c[2]);
+            dd_acc1(x1h, x1l, y1h, s[3], c[3]);
+        }
     }
 #pragma unroll
     for (int k = 0; k < 4; ++k)
@@ -325,9 +344,151 @@ __global__ void __launch_bounds__(kBlThreads) k_dd_gram(const float *X0h, const 
     gram_finish<P, NM>(acc, red, part, ticket, out);
 }
 
+// ---- row-per-thread kernels: update and Cholesky QR ---------------------------
+// One thread per row: a row's P elements (high and low words) come straight
+// from global memory into registers, the P x P coefficient matrix is read from
+// shared memory as (high, low) pairs (broadcast, one 8-byte load per
+// double-float multiply-add), and triangular coefficient matrices cost only
+// their P (P + 1) / 2 nonzero entries.  A tile is kBlThreads rows; the Gram
+// of the rows a tile produced is taken from a padded shared-memory copy.
+
+// P floats of row `row` of a [n][P] block (16-byte aligned rows for P >= 4)
+template <int P>
+__device__ __forceinline__ void load_row(const float *g, uint64_t row, float (&v)[P])
+{
+    if constexpr (P % 4 == 0) {
+        const float4 *q = reinterpret_cast<const float4 *>(g + row * P);
+#pragma unroll
+        for (int k = 0; k < P / 4; ++k) {
+            const float4 t = q[k];
+            v[4 * k] = t.x;
+            v[4 * k + 1] = t.y;
+            v[4 * k + 2] = t.z;
+            v[4 * k + 3] = t.w;
+        }
+    } else {
+        static_assert(P == 2, "block sizes 2, 4, 8, 16");
+        const float2 t = reinterpret_cast<const float2 *>(g + row * P)[0];
+        v[0] = t.x;
+        v[1] = t.y;
+    }
+}
+
+template <int P>
+__device__ __forceinline__ void store_row(float *g, uint64_t row, const float (&v)[P])
+{
+    if constexpr (P % 4 == 0) {
+        float4 *q = reinterpret_cast<float4 *>(g + row * P);
+#pragma unroll
+        for (int k = 0; k < P / 4; ++k)
+            q[k] = make_float4(v[4 * k], v[4 * k + 1], v[4 * k + 2], v[4 * k + 3]);
+    } else {
+        reinterpret_cast<float2 *>(g + row * P)[0] = make_float2(v[0], v[1]);
+    }
+}
+
+// Row of the product output Y as a double-float start value (kind YK as in
+// stage_dd: 0 fp32, 1 fp64, 2 double-float)
+template <int P, int YK>
+__device__ __forceinline__ void load_y_row(const void *gh, const float *gl, uint64_t row, float (&s)[P],
+                                           float (&c)[P])
+{
+    if constexpr (YK == 0) {
+        load_row<P>(reinterpret_cast<const float *>(gh), row, s);
+#pragma unroll
+        for (int b = 0; b < P; ++b)
+            c[b] = 0.f;
+    } else if constexpr (YK == 1) {
+        const double *q = reinterpret_cast<const double *>(gh) + row * P;
+#pragma unroll
+        for (int b = 0; b < P; ++b)
+            dd_split(q[b], s[b], c[b]);
+    } else {
+        load_row<P>(reinterpret_cast<const float *>(gh), row, s);
+        load_row<P>(gl, row, c);
+    }
+}
+
+// Symmetric Gram of a staged tile of kBlThreads rows with row stride P + 1:
+// the 2 x 2 entry groups (ga, gb) with ga <= gb (P/2 (P/2 + 1) / 2 of them),
+// one per thread, with a slice of the tile's rows.
+template <int P>
+struct SymLayout {
+    static constexpr int kHalf = P / 2;
+    static constexpr int kGroups = kHalf * (kHalf + 1) / 2;
+    static constexpr int kSlices = kBlThreads / kGroups;
+    static constexpr int kStride = P + 1;
+    __device__ static int index(int ga, int gb) { return ga * kHalf - ga * (ga - 1) / 2 + (gb - ga); }
+    __device__ static void groups(int g, int &ga, int &gb)
+    {
+        ga = 0;
+        while (g >= kHalf - ga) {
+            g -= kHalf - ga;
+            ++ga;
+        }
+        gb = ga + g;
+    }
+};
+
+template <int P>
+__device__ __forceinline__ void gram_tile_sym(const float *sh, const float *sl, GramAcc &acc)
+{
+    using L = SymLayout<P>;
+    const int grp = threadIdx.x % L::kGroups, slc = threadIdx.x / L::kGroups;
+    if (slc >= L::kSlices)
+        return;
+    int ga, gb;
+    L::groups(grp, ga, gb);
+    const int a0 = 2 * ga, b0 = 2 * gb;
+    float s[4] = {0.f, 0.f, 0.f, 0.f}, c[4] = {0.f, 0.f, 0.f, 0.f};
+    for (int r = slc; r < kBlThreads; r += L::kSlices) {
+        const float *xh = sh + r * L::kStride, *xl = sl + r * L::kStride;
+        const float x0h = xh[a0], x1h = xh[a0 + 1], x0l = xl[a0], x1l = xl[a0 + 1];
+        const float y0h = xh[b0], y1h = xh[b0 + 1], y0l = xl[b0], y1l = xl[b0 + 1];
+        dd_acc(x0h, x0l, y0h, y0l, s[0], c[0]);
+        dd_acc(x0h, x0l, y1h, y1l, s[1], c[1]);
+        dd_acc(x1h, x1l, y0h, y0l, s[2], c[2]);
+        dd_acc(x1h, x1l, y1h, y1l, s[3], c[3]);
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+        dd_add(acc.h[k], acc.l[k], s[k], c[k]);
+    if (++acc.tiles == kFlushTiles)
+        acc.flush();
+}
+
+// As gram_finish, for the symmetric layout: entry (a, b) with a/2 > b/2 is
+// the transposed entry of group (b/2, a/2), so the result is exactly symmetric.
+template <int P>
+__device__ void gram_finish_sym(GramAcc &acc, double *red, double2 *part, unsigned int *ticket, double *out)
+{
+    using L = SymLayout<P>;
+    const int grp = threadIdx.x % L::kGroups, slc = threadIdx.x / L::kGroups;
+    acc.flush();
+    __syncthreads();
+    if (slc < L::kSlices)
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+            red[(slc * L::kGroups + grp) * 4 + k] = acc.d[k];
+    __syncthreads();
+    for (int e = threadIdx.x; e < P * P; e += blockDim.x) {
+        const int a = e / P, b = e % P;
+        const bool tr = a / 2 > b / 2;
+        const int g = tr ? L::index(b / 2, a / 2) : L::index(a / 2, b / 2);
+        const int k = tr ? (b & 1) * 2 + (a & 1) : (a & 1) * 2 + (b & 1);
+        KS t{0.0, 0.0};
+        for (int q = 0; q < L::kSlices; ++q)
+            t = ks_add(t, red[(q * L::kGroups + g) * 4 + k]);
+        part[(size_t)blockIdx.x * P * P + e] = make_double2(t.s, t.c);
+    }
+    if (last_block(ticket))
+        merge_partials(part, P * P, out, ticket);
+}
+
 // W = Y - X0 C0 - X1 C1 (C fp64, P x P row-major per matrix: W[i][b] -=
 // sum_a X[i][a] C[a][b]), written as a double-float block; W may alias X1 or
-// Y (a tile is staged completely before it is written).  With G: Gram of W.
+// Y (each row is read completely by its thread before that thread writes it).
+// With G: the Gram of W.
 template <int P, int NM, int YK>
 __global__ void __launch_bounds__(kBlThreads) k_dd_update(const float *X0h, const float *X0l, const float *X1h,
                                                           const float *X1l, const void *Yh, const float *Yl,
@@ -337,86 +498,67 @@ __global__ void __launch_bounds__(kBlThreads) k_dd_update(const float *X0h, cons
 {
     if (*stop)
         return;
-    __shared__ float sxh[NM * kTileRows * P], sxl[NM * kTileRows * P];
-    __shared__ float swh[kTileRows * P], swl[kTileRows * P];
-    __shared__ float sch[NM * P * P], scl[NM * P * P];
+    using L = SymLayout<P>;
+    __shared__ float2 sc[NM * P * P];
+    __shared__ float swh[kBlThreads * L::kStride], swl[kBlThreads * L::kStride];
     __shared__ double red[kBlThreads * 4];
-    for (int e = threadIdx.x; e < NM * P * P; e += blockDim.x)
-        dd_split(-C[e], sch[e], scl[e]);
+    for (int e = threadIdx.x; e < NM * P * P; e += blockDim.x) {
+        float h, l;
+        dd_split(-C[e], h, l);
+        sc[e] = make_float2(h, l);
+    }
+    __syncthreads();
     GramAcc acc;
     acc.init();
-    const uint64_t tiles = (n + kTileRows - 1) / kTileRows;
-    const uint64_t lim = n * P;
-    Prefetch<P, 2> p0, p1;
-    Prefetch<P, YK> py;
-    auto fetch = [&](uint64_t t) {
-        p0.load(X0h, X0l, t * kTileRows, n);
-        if (NM > 1)
-            p1.load(X1h, X1l, t * kTileRows, n);
-        py.load(Yh, Yl, t * kTileRows, n);
-    };
-    if (blockIdx.x < tiles)
-        fetch(blockIdx.x);
+    const uint64_t tiles = (n + kBlThreads - 1) / kBlThreads;
     for (uint64_t t = blockIdx.x; t < tiles; t += gridDim.x) {
-        const uint64_t r0 = t * kTileRows;
-        p0.store(sxh, sxl);
-        if (NM > 1)
-            p1.store(sxh + kTileRows * P, sxl + kTileRows * P);
-        py.store(swh, swl);
-        __syncthreads();
-        // the next tile's loads are issued now; W may alias X1 or Y, but a
-        // tile is only written by the block that staged it, after staging
-        if (t + gridDim.x < tiles)
-            fetch(t + gridDim.x);
-        {
-            constexpr int kE = (kTileRows * P + kBlThreads - 1) / kBlThreads;
-            float s[kE], c[kE];
+        const uint64_t row = t * kBlThreads + threadIdx.x;
+        float wh[P], wl[P];
+        if (row < n) {
+            float s[P], c[P];
+            load_y_row<P, YK>(Yh, Yl, row, s, c);
 #pragma unroll
-            for (int k = 0; k < kE; ++k) {
-                const int e = threadIdx.x + k * kBlThreads;
-                s[k] = e < kTileRows * P ? swh[e] : 0.f;
-                c[k] = e < kTileRows * P ? swl[e] : 0.f;
-            }
-#pragma unroll
-            for (int m = 0; m < NM; ++m)
+            for (int m = 0; m < NM; ++m) {
+                float xh[P], xl[P];
+                load_row<P>(m ? X1h : X0h, row, xh);
+                load_row<P>(m ? X1l : X0l, row, xl);
 #pragma unroll
                 for (int a = 0; a < P; ++a)
 #pragma unroll
-                    for (int k = 0; k < kE; ++k) {
-                        const int e = threadIdx.x + k * kBlThreads;
-                        if (e < kTileRows * P) {
-                            const int r = e / P, b = e % P;
-                            dd_acc(sxh[m * kTileRows * P + r * P + a], sxl[m * kTileRows * P + r * P + a],
-                                   sch[m * P * P + a * P + b], scl[m * P * P + a * P + b], s[k], c[k]);
-                        }
+                    for (int b = 0; b < P; ++b) {
+                        const float2 q = sc[m * P * P + a * P + b];
+                        dd_acc(xh[a], xl[a], q.x, q.y, s[b], c[b]);
                     }
-            __syncthreads();  // every element of the tile is read before any is overwritten
+            }
 #pragma unroll
-            for (int k = 0; k < kE; ++k) {
-                const int e = threadIdx.x + k * kBlThreads;
-                if (e < kTileRows * P)
-                    dd_norm(s[k], c[k], swh[e], swl[e]);
-            }
+            for (int b = 0; b < P; ++b)
+                dd_norm(s[b], c[b], wh[b], wl[b]);
+            store_row<P>(Wh, row, wh);
+            store_row<P>(Wl, row, wl);
+        } else {
+#pragma unroll
+            for (int b = 0; b < P; ++b)
+                wh[b] = wl[b] = 0.f;
         }
-        __syncthreads();
-        for (int e = threadIdx.x; e < kTileRows * P; e += blockDim.x) {
-            const uint64_t gi = r0 * P + (uint64_t)e;
-            if (gi < lim) {
-                Wh[gi] = swh[e];
-                Wl[gi] = swl[e];
+        if (G) {
+#pragma unroll
+            for (int b = 0; b < P; ++b) {
+                swh[threadIdx.x * L::kStride + b] = wh[b];
+                swl[threadIdx.x * L::kStride + b] = wl[b];
             }
+            __syncthreads();
+            gram_tile_sym<P>(swh, swl, acc);
+            __syncthreads();
         }
-        if (G)
-            gram_tile<P, 1, true>(swh, swl, swh, swl, acc);
-        __syncthreads();
     }
     if (G)
-        gram_finish<P, 1>(acc, red, part, ticket, G);
+        gram_finish_sym<P>(acc, red, part, ticket, G);
 }
 
-// Z = W R1i (R1i fp64 upper triangular, row-major); kApply = false: Gram of
-// Z merged into G2; kApply = true: V = Z R2i written over W.  Z is formed
-// identically in both.
+// Cholesky QR steps on the block W (double-float, in place).  kApply = false:
+// Z = W R1i (R1i fp64 upper triangular, row-major) and the Gram of Z into G2;
+// kApply = true: W = W (R1i R2i), the product of the two upper triangular
+// inverses formed in fp64 (CholQR2 applied at once).
 template <int P, bool kApply>
 __global__ void __launch_bounds__(kBlThreads) k_dd_qr(float *Wh, float *Wl, const double *R1i, const double *R2i,
                                                       uint64_t n, double2 *part, unsigned int *ticket,
@@ -424,88 +566,67 @@ __global__ void __launch_bounds__(kBlThreads) k_dd_qr(float *Wh, float *Wl, cons
 {
     if (*stop)
         return;
-    __shared__ float swh[kTileRows * P], swl[kTileRows * P];
-    __shared__ float szh[kTileRows * P], szl[kTileRows * P];
-    __shared__ float s1h[P * P], s1l[P * P], s2h[P * P], s2l[P * P];
-    __shared__ double red[kBlThreads * 4];
+    using L = SymLayout<P>;
+    constexpr int kZ = kApply ? 1 : kBlThreads * L::kStride;
+    __shared__ float2 sr[P * P];
+    __shared__ float szh[kZ], szl[kZ];
+    __shared__ double red[kApply ? 1 : kBlThreads * 4];
     for (int e = threadIdx.x; e < P * P; e += blockDim.x) {
-        dd_split(R1i[e], s1h[e], s1l[e]);
-        if (kApply)
-            dd_split(R2i[e], s2h[e], s2l[e]);
+        const int a = e / P, b = e % P;
+        double v = 0.0;
+        if (kApply) {
+            for (int k = a; k <= b; ++k)
+                v += R1i[a * P + k] * R2i[k * P + b];
+        } else if (a <= b) {
+            v = R1i[e];
+        }
+        float h, l;
+        dd_split(v, h, l);
+        sr[e] = make_float2(h, l);
     }
+    __syncthreads();
     GramAcc acc;
     acc.init();
-    const uint64_t tiles = (n + kTileRows - 1) / kTileRows;
-    const uint64_t lim = n * P;
-    Prefetch<P, 2> pw;
-    if (blockIdx.x < tiles)
-        pw.load(Wh, Wl, (uint64_t)blockIdx.x * kTileRows, n);
+    const uint64_t tiles = (n + kBlThreads - 1) / kBlThreads;
     for (uint64_t t = blockIdx.x; t < tiles; t += gridDim.x) {
-        const uint64_t r0 = t * kTileRows;
-        pw.store(swh, swl);
-        __syncthreads();
-        if (t + gridDim.x < tiles)
-            pw.load(Wh, Wl, (t + gridDim.x) * kTileRows, n);
-        // the entries of R1i / R2i below the diagonal are exact zeros, for
-        // which dd_acc is an exact no-op: full unrolled loops, no divergence
-        // between the columns b of a warp, the thread's elements interleaved
-        constexpr int kE = (kTileRows * P + kBlThreads - 1) / kBlThreads;
-        {
-            float s[kE], c[kE];
+        const uint64_t row = t * kBlThreads + threadIdx.x;
+        float zh[P], zl[P];
+        if (row < n) {
+            float wh[P], wl[P];
+            load_row<P>(Wh, row, wh);
+            load_row<P>(Wl, row, wl);
 #pragma unroll
-            for (int k = 0; k < kE; ++k)
-                s[k] = c[k] = 0.f;
+            for (int b = 0; b < P; ++b) {
+                float s = 0.f, c = 0.f;
 #pragma unroll
-            for (int a = 0; a < P; ++a)
-#pragma unroll
-                for (int k = 0; k < kE; ++k) {
-                    const int e = threadIdx.x + k * kBlThreads;
-                    if (e < kTileRows * P) {
-                        const int r = e / P, b = e % P;
-                        dd_acc(swh[r * P + a], swl[r * P + a], s1h[a * P + b], s1l[a * P + b], s[k], c[k]);
-                    }
+                for (int a = 0; a <= b; ++a) {
+                    const float2 q = sr[a * P + b];
+                    dd_acc(wh[a], wl[a], q.x, q.y, s, c);
                 }
-#pragma unroll
-            for (int k = 0; k < kE; ++k) {
-                const int e = threadIdx.x + k * kBlThreads;
-                if (e < kTileRows * P)
-                    dd_norm(s[k], c[k], szh[e], szl[e]);
+                dd_norm(s, c, zh[b], zl[b]);
             }
-        }
-        __syncthreads();
-        if (kApply) {
-            float s[kE], c[kE];
-#pragma unroll
-            for (int k = 0; k < kE; ++k)
-                s[k] = c[k] = 0.f;
-#pragma unroll
-            for (int a = 0; a < P; ++a)
-#pragma unroll
-                for (int k = 0; k < kE; ++k) {
-                    const int e = threadIdx.x + k * kBlThreads;
-                    if (e < kTileRows * P) {
-                        const int r = e / P, b = e % P;
-                        dd_acc(szh[r * P + a], szl[r * P + a], s2h[a * P + b], s2l[a * P + b], s[k], c[k]);
-                    }
-                }
-#pragma unroll
-            for (int k = 0; k < kE; ++k) {
-                const int e = threadIdx.x + k * kBlThreads;
-                const uint64_t gi = r0 * P + (uint64_t)e;
-                if (e < kTileRows * P && gi < lim) {
-                    float h, l;
-                    dd_norm(s[k], c[k], h, l);
-                    Wh[gi] = h;
-                    Wl[gi] = l;
-                }
+            if (kApply) {
+                store_row<P>(Wh, row, zh);
+                store_row<P>(Wl, row, zl);
             }
         } else {
-            gram_tile<P, 1, true>(szh, szl, szh, szl, acc);
+#pragma unroll
+            for (int b = 0; b < P; ++b)
+                zh[b] = zl[b] = 0.f;
         }
-        __syncthreads();
+        if (!kApply) {
+#pragma unroll
+            for (int b = 0; b < P; ++b) {
+                szh[threadIdx.x * L::kStride + b] = zh[b];
+                szl[threadIdx.x * L::kStride + b] = zl[b];
+            }
+            __syncthreads();
+            gram_tile_sym<P>(szh, szl, acc);
+            __syncthreads();
+        }
     }
     if (!kApply)
-        gram_finish<P, 1>(acc, red, part, ticket, G2);
+        gram_finish_sym<P>(acc, red, part, ticket, G2);
 }
 
 // psi (double-float, dim) += V_j s_j  (s_j = y[j P .. j P + P) in fp64); psi
@@ -844,6 +965,9 @@ ed_status run_block(const ed_operator *op, const ed_basis *b, const double *x0, 
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const uint64_t tiles = (n + kTileRows - 1) / kTileRows;
     const int grid = (int)std::max<uint64_t>(1, std::min<uint64_t>((uint64_t)sms * 4, tiles));
+    // the row-per-thread kernels (update, QR): tiles of kBlThreads rows
+    const uint64_t rtiles = (n + kBlThreads - 1) / kBlThreads;
+    const int rgrid = (int)std::max<uint64_t>(1, std::min<uint64_t>((uint64_t)sms * 4, rtiles));
     const int vgrid = (int)std::max<uint64_t>(1, std::min<uint64_t>((uint64_t)sms * 8, (n + 255) / 256));
     const size_t blk = (size_t)n * P;
 
@@ -901,10 +1025,10 @@ ed_status run_block(const ed_operator *op, const ed_basis *b, const double *x0, 
 
     // Cholesky QR (twice) of the block (wh, wl) in place; R1 already in sm
     auto qr = [&](float *wh, float *wl, int j) {
-        k_dd_qr<P, false><<<grid, kBlThreads, 0, st>>>(wh, wl, R1i, nullptr, n, part, tickets + 2, G2, stop);
+        k_dd_qr<P, false><<<rgrid, kBlThreads, 0, st>>>(wh, wl, R1i, nullptr, n, part, tickets + 2, G2, stop);
         count_launch();
         k_bl_small<P><<<1, 32, 0, st>>>(sm, A, B, j, 2, stop, flags + 1); count_launch();
-        k_dd_qr<P, true><<<grid, kBlThreads, 0, st>>>(wh, wl, R1i, R2i, n, part, tickets + 2, nullptr, stop);
+        k_dd_qr<P, true><<<rgrid, kBlThreads, 0, st>>>(wh, wl, R1i, R2i, n, part, tickets + 2, nullptr, stop);
         count_launch();
     };
 
@@ -942,14 +1066,14 @@ ed_status run_block(const ed_operator *op, const ed_basis *b, const double *x0, 
             const int nm = j ? 2 : 1;
             launch_gram<P>(nm, yk, Vjh, Vjl, Vph, Vpl, Yh, nullptr, n, grid, part, tickets, C, stop, st);
             k_bl_small<P><<<1, 32, 0, st>>>(sm, A, B, j, 0, stop, flags + 1); count_launch();
-            launch_update<P>(nm, yk, Vjh, Vjl, Vph, Vpl, Yh, nullptr, C, Wh, Wl, n, grid, part, tickets + 1,
+            launch_update<P>(nm, yk, Vjh, Vjl, Vph, Vpl, Yh, nullptr, C, Wh, Wl, n, rgrid, part, tickets + 1,
                              reorth ? nullptr : G, stop, st);
             if (reorth) {  // against every kept block, block modified Gram-Schmidt, twice
                 for (int rep = 0; rep < 2; ++rep)
                     for (int i = 0; i <= j; ++i) {
                         launch_gram<P>(1, 2, bh(i), bl(i), nullptr, nullptr, Wh, Wl, n, grid, part, tickets, C,
                                        stop, st);
-                        launch_update<P>(1, 2, bh(i), bl(i), nullptr, nullptr, Wh, Wl, C, Wh, Wl, n, grid, part,
+                        launch_update<P>(1, 2, bh(i), bl(i), nullptr, nullptr, Wh, Wl, C, Wh, Wl, n, rgrid, part,
                                          tickets + 1, nullptr, stop, st);
                     }
                 launch_gram<P>(1, 2, Wh, Wl, nullptr, nullptr, Wh, Wl, n, grid, part, tickets, G, stop, st);

@@ -53,6 +53,25 @@ def test_two_pass_ritz_vector_is_identical():
     assert float((hv - r1.e0 * v1).norm()) < 1e-6
 
 
+def test_two_pass_refinement_is_identical():
+    """fp32-matvec mode: with RECOMPUTE both the main Ritz vector and the
+    fp64 refinement's come from second passes (the layout used when their
+    vectors do not fit beside a sector of billions of states); energy and
+    vector equal those from stored vectors."""
+    torch, ed = gpu()
+    w = ei.workload("ring16")
+    S = build_pair(16, 8, +1, w["perms"], w["chars"], w["op"], with_oracle=False)
+    x0 = to_torch(ei.x_by_index(0, S["dim"])[:, 0], np.float64)
+    v1 = torch.empty_like(x0)
+    v2 = torch.empty_like(x0)
+    r1 = ed.lanczos(S["O"], S["B"], x0, 40, ed.ED_LANCZOS_F32_MATVEC, vec_out=v1)
+    r2 = ed.lanczos(S["O"], S["B"], x0, 40, ed.ED_LANCZOS_F32_MATVEC | ed.ED_LANCZOS_RECOMPUTE, vec_out=v2)
+    assert r1.e0 == r2.e0 and r1.residual == r2.residual
+    assert torch.equal(v1, v2)
+    assert r2.matvecs == r1.matvecs + 40 + 6
+    assert abs(r2.e0 - bethe_e0(16)) < 1e-10
+
+
 def test_complex_sector_lanczos():
     p, c = ei.torus_group(4, 4, 1, 0)
     op = ei.j1j2_torus(4, 4, 1.0, 0.5)

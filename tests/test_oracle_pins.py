@@ -232,6 +232,28 @@ def test_ground_state_sector_matches_bethe_ansatz(n):
     assert abs(e0 - bethe_e0(n)) < 1e-10
 
 
+@pytest.mark.parametrize("n", [10, 14, 18])
+def test_ground_state_of_2_mod_4_rings_lies_at_momentum_pi(n):
+    """For n = 2 mod 4 the ground state is at momentum pi with reflection +1
+    and spin inversion -1 (the 2-site singlet is odd under the swap): that
+    sector reaches the Bethe ansatz energy, the k = 0, z = +1 sector of the
+    same dimension does not."""
+    import scipy.sparse.linalg as sla
+
+    def lowest(k, p, z):
+        G, H, st, nm = ring_sector(n, n // 2, k, p, z)
+        M = oracle.sparse_matrix(G, H, st, nm)
+        if M.shape[0] < 400:
+            return len(st), np.linalg.eigvalsh(M.toarray())[0]
+        return len(st), sla.eigsh(M, k=1, which="SA", tol=1e-14)[0][0]
+
+    d_pi, e_pi = lowest(n // 2, +1, -1)
+    d_0, e_0 = lowest(0, +1, +1)
+    assert d_pi == d_0
+    assert abs(e_pi - bethe_e0(n)) < 1e-10
+    assert e_0 > bethe_e0(n) + 0.1
+
+
 def test_hermiticity_and_sz_conservation():
     # complex sector: <u, H v> = <H u, v>
     p, c = ei.ring_group(12, 5)
