@@ -52,11 +52,14 @@ L2_BYTES = 129 * 1024 * 1024
 # maximum SM clock (GB300 SM: 4 sub-partitions x 16 INT32 lanes).
 SMS = 152
 INT_LANES_PER_SM = 64
-# DRAM bytes (read + write) of one launch of the timed kernel, from one ncu
-# capture of it (--set full, which starts every replay with a cold L2); keyed by
-# workload.  Retake the capture and update the figure whenever the kernel
-# changes (the roofline reports null traffic for workloads not listed).
-KERNEL_DRAM_BYTES = {}
+# DRAM bytes (read + write) per stored nonzero of one launch of the timed
+# kernel (fp32 block product, keyed by nvec), from one ncu --set full capture of
+# the same kernel on the ring N=36 sector (nvec = 8: 161.04 + 2.02 GB for
+# 1 230 759 430 nonzeros).  A ring N=40 launch is too large for a many-pass
+# capture, so its traffic is this figure times the nonzeros it processes.
+# Retake the capture and update the figure whenever the kernel changes (the
+# roofline reports null traffic for nvec not listed).
+KERNEL_DRAM_BYTES_PER_NNZ = {8: (161.040283e9 + 2.023800e9) / 1230759430}
 
 
 def peaks():
@@ -749,7 +752,10 @@ def run_job(args, w):
     roofline = {
         "bound": "alu", "achieved": achieved_int, "peak": int_peak / 1e12, "unit": "TOP/s",
         "frac": achieved_int / (int_peak / 1e12),
-        "traffic": KERNEL_DRAM_BYTES.get((w["name"], nvec)),
+        "traffic": (KERNEL_DRAM_BYTES_PER_NNZ[nvec] * nnz_total if nvec in KERNEL_DRAM_BYTES_PER_NNZ
+                    else None),
+        "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of the ring N=36 launch, "
+                          "scaled by stored nonzeros",
         "kernel": f"k_matvec (row-per-lane, fp32, nvec={nvec}, pruned rotation search, 64-bit words, "
                   "bucketed index)",
         "peak_kind": "measured live: int32 op mix of the search (funnel shift, lop3, min, add) on every SM",

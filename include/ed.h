@@ -311,7 +311,10 @@ typedef struct {
     double e0;            /* returned energy: fp64 Rayleigh quotient of the Ritz vector */
     double residual;      /* |H psi - e0 psi| / |psi| in fp64 */
     double matvec_ms;     /* device time spent in the matvec kernels, summed over
-                             all products (CUDA events on `stream` around each) */
+                             the products launched one by one (CUDA events on
+                             `stream` around each); ed_lanczos replays the steps
+                             of sectors of at most 2^22 states from a CUDA graph
+                             and does not time those products (0)               */
 } ed_lanczos_info;
 
 /*
@@ -336,7 +339,10 @@ typedef struct {
  * a second pass in the same way), whose lowest Ritz value is returned
  * together with its residual.  Work memory beyond the caller's vectors: four
  * fp64 vectors, plus two fp32 vectors in the fp32-matvec mode, when the
- * Krylov vectors are not stored.  Takes its work vectors from the library's
+ * Krylov vectors are not stored.  Sectors of at most 2^22 states are
+ * launch-bound: there the steps after the first are replayed from a CUDA
+ * graph of two steps (same kernels, same results).  Not to be called while
+ * `stream` is being captured.  Takes its work vectors from the library's
  * memory pool (see ed_release_cached_memory); synchronises `stream` before
  * returning.
  * Errors: ED_ERR_INVALID_ARG, ED_ERR_SYMMETRY_MISMATCH, ED_ERR_UNSUPPORTED

@@ -154,12 +154,13 @@ __device__ double sum_partials_l2(const double2 *part, int nparts)
 }
 
 // partial[b] = compensated sum over this block's slice of Re<a_i, b_i>; with a
-// ticket, the last block also stores the total in *out and resets the ticket.
-// Four elements per iteration, loads first, for memory-level parallelism.
+// ticket, the last block also stores the total in out[*jp] (out[0] without a
+// step index) and resets the ticket.  Four elements per iteration, loads
+// first, for memory-level parallelism.
 template <bool kC, bool kF32>
 __global__ void __launch_bounds__(kRedThreads) k_dot_part(const typename Vec<kC>::D *a, const void *bv,
                                                            uint64_t n, double2 *part, unsigned int *ticket,
-                                                           double *out)
+                                                           double *out, const int *jp = nullptr)
 {
     using VT = Vec<kC>;
     using B = std::conditional_t<kF32, typename VT::F, typename VT::D>;
@@ -191,7 +192,7 @@ __global__ void __launch_bounds__(kRedThreads) k_dot_part(const typename Vec<kC>
     if (ticket && is_last_block(ticket)) {
         const double t = sum_partials_l2(part, gridDim.x);
         if (threadIdx.x == 0) {
-            *out = t;
+            out[jp ? *jp : 0] = t;
             *ticket = 0;
         }
     }
@@ -218,14 +219,20 @@ __global__ void __launch_bounds__(kRedThreads) k_norm_part(const typename Vec<kC
 
 // w = w_in - alpha_j v - beta_j vp (alpha_j and beta_j already stored); norm
 // partials of w; with a ticket, the last block stores sqrt(|w|^2) in *beta_out.
+// With a step index jp, alpha, beta_j and beta_out are offset by *jp.
 template <bool kC, bool kF32>
 __global__ void __launch_bounds__(kRedThreads) k_update(const void *w_in, typename Vec<kC>::D *w,
                                                          const typename Vec<kC>::D *v,
                                                          const typename Vec<kC>::D *vp, uint64_t n,
                                                          const double *alpha, const double *beta_j,
                                                          double2 *norm_part, unsigned int *ticket,
-                                                         double *beta_out)
+                                                         double *beta_out, const int *jp = nullptr)
 {
+    if (jp) {
+        alpha += *jp;
+        beta_j += *jp;
+        beta_out += *jp;
+    }
     using VT = Vec<kC>;
     using D = typename VT::D;
     using WI = std::conditional_t<kF32, typename VT::F, D>;
@@ -288,14 +295,21 @@ __global__ void __launch_bounds__(kRedThreads) k_norm_final(const double2 *part,
 }
 
 // v_out = w / beta (zero on breakdown); fp32 copy; four elements per thread
-// per iteration
+// per iteration.  With a step index jp: beta is offset by *jp, and with a
+// store, the vector is also written as stored vector *jp + 1.
 template <bool kC>
 __global__ void __launch_bounds__(kRedThreads) k_normalize(const typename Vec<kC>::D *w,
                                                             typename Vec<kC>::D *v_out,
                                                             typename Vec<kC>::F *x32, uint64_t n,
-                                                            const double *beta)
+                                                            const double *beta, const int *jp = nullptr,
+                                                            typename Vec<kC>::D *store = nullptr)
 {
     using VT = Vec<kC>;
+    if (jp) {
+        beta += *jp;
+        if (store)
+            store += (uint64_t)(*jp + 1) * n;
+    }
     const double b = *beta;
     const double s = b > 0.0 ? 1.0 / b : 0.0;
     const uint64_t G = (uint64_t)gridDim.x * blockDim.x;
@@ -310,6 +324,8 @@ __global__ void __launch_bounds__(kRedThreads) k_normalize(const typename Vec<kC
             v_out[i + u * G] = r[u];
             if (x32)
                 x32[i + u * G] = VT::down(r[u]);
+            if (jp && store)
+                store[i + u * G] = r[u];
         }
     }
     for (; i < n; i += G) {
@@ -317,20 +333,30 @@ __global__ void __launch_bounds__(kRedThreads) k_normalize(const typename Vec<kC
         v_out[i] = r;
         if (x32)
             x32[i] = VT::down(r);
+        if (jp && store)
+            store[i] = r;
     }
 }
 
-// acc += y[j] * v   (Ritz vector accumulation, second pass)
+// acc += y[j] * v   (Ritz vector accumulation, second pass); with a step
+// index jp, j = *jp and the first step (j = 0) overwrites acc
 template <bool kC>
 __global__ void k_axpy_coef(typename Vec<kC>::D *acc, const typename Vec<kC>::D *v, const double *y, int j,
-                            uint64_t n, int first)
+                            uint64_t n, int first, const int *jp = nullptr)
 {
     using VT = Vec<kC>;
+    if (jp) {
+        j = *jp;
+        first = j == 0;
+    }
     const double c = y[j];
     for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (uint64_t)gridDim.x * blockDim.x)
         acc[i] = VT::fma_acc(first ? VT::zero() : acc[i], c, v[i]);
 }
+
+__global__ void k_step_set(int *jp, int v) { *jp = v; }
+__global__ void k_step_inc(int *jp) { *jp += 1; }
 
 // psi[i] = sum_j y[j] V[j][i] over stored Krylov vectors
 template <bool kC>
@@ -647,6 +673,28 @@ struct MatvecTimer {
     }
 };
 
+// Steps replayed from a CUDA graph: -1 = for sectors of at most
+// kGraphMaxDim states (launch-bound; larger sectors spend microseconds per
+// launch against milliseconds per kernel), 0 = never, 1 = always.
+int g_lanczos_graph = -1;
+constexpr uint64_t kGraphMaxDim = 1ULL << 22;
+
+// The capture stream and the graphs of one call, released on every exit path.
+struct Graphs {
+    cudaStream_t cap = nullptr;
+    std::vector<cudaGraph_t> graphs;
+    std::vector<cudaGraphExec_t> execs;
+    ~Graphs()
+    {
+        for (auto g : execs)
+            cudaGraphExecDestroy(g);
+        for (auto g : graphs)
+            cudaGraphDestroy(g);
+        if (cap)
+            cudaStreamDestroy(cap);
+    }
+};
+
 // Work arrays of one call, from the library's stream-ordered pool.
 struct Scratch {
     cudaStream_t st;
@@ -711,7 +759,9 @@ ed_status run_lanczos(const ed_operator *op, const ed_basis *b, const void *x0, 
     if (reorth && !store)
         return ED_ERR_UNSUPPORTED;
 
+    const bool graph = !reorth && !push && (g_lanczos_graph == 1 || (g_lanczos_graph < 0 && n <= kGraphMaxDim));
     Scratch S(st);
+    Graphs GR;
     D *V = nullptr, *w = nullptr, *ring[2] = {nullptr, nullptr}, *psi = nullptr;
     F *x32 = nullptr, *w32 = nullptr;
     double *alpha = nullptr, *beta = nullptr, *y = nullptr, *work = nullptr, *scal = nullptr;
@@ -719,10 +769,13 @@ ed_status run_lanczos(const ed_operator *op, const ed_basis *b, const void *x0, 
     double2 *part_a = nullptr, *part_b = nullptr, *part_c = nullptr;
     if (store)
         ED_L_TRY(S.get(&V, (size_t)(steps + 1) * n));
-    else {
+    if (!store || graph) {  // the graph's steps run on the ring and copy into the store
         ED_L_TRY(S.get(&ring[0], n));
         ED_L_TRY(S.get(&ring[1], n));
     }
+    int *jdev = nullptr;  // the step index of graph-replayed steps
+    if (graph)
+        ED_L_TRY(S.get(&jdev, 1));
     ED_L_TRY(S.get(&w, n));
     ED_L_TRY(S.get(&psi, n));
     if (f32) {
@@ -811,8 +864,88 @@ ed_status run_lanczos(const ed_operator *op, const ed_basis *b, const void *x0, 
         return cudaGetLastError();
     };
 
+    // The same m steps as run(), for launch-bound sectors: step 0 eagerly, then
+    // a CUDA graph of two steps (v, vp alternate between the ring buffers with
+    // period two; alpha, beta and the store slot are indexed by the step index
+    // on the device) replayed, and an odd last step eagerly.  Same kernels in
+    // the same order, so the results equal run()'s bit for bit; products
+    // inside the graph are not timed one by one.
+    auto run_g = [&](const D *start, int m, bool use_f32, D *Vs, const double *acc_y) -> cudaError_t {
+        cudaError_t e;
+        k_norm_part<kC><<<nparts, kRedThreads, 0, st>>>(start, n, part_a); count_launch();
+        k_scale_by_norm<kC><<<vgrid, kRedThreads, 0, st>>>(start, ring[0], use_f32 ? x32 : nullptr, n, part_a, nparts); count_launch();
+        if (Vs && (e = cudaMemcpyAsync(Vs, ring[0], vec_bytes, cudaMemcpyDeviceToDevice, st)) != cudaSuccess)
+            return e;
+        k_step_set<<<1, 1, 0, st>>>(jdev, 0); count_launch();
+        auto step = [&](const D *v, const D *vp, D *vn, cudaStream_t s) -> cudaError_t {
+            if (acc_y) {
+                k_axpy_coef<kC><<<vgrid, kRedThreads, 0, s>>>(psi, v, acc_y, 0, n, 0, jdev); count_launch();
+            }
+            cudaError_t e2;
+            if (use_f32) {
+                if ((e2 = launch_matvec_v(ov, gv, iv, track, x32, w32, 1, dt32, tuned_variant(b, 1, dt32), s)) !=
+                    cudaSuccess)
+                    return e2;
+                k_dot_part<kC, true><<<nparts, kRedThreads, 0, s>>>(v, w32, n, part_a, tickets, alpha, jdev); count_launch();
+                k_update<kC, true><<<nparts, kRedThreads, 0, s>>>(w32, w, v, vp, n, alpha, beta, part_b,
+                                                                   tickets + 1, beta + 1, jdev); count_launch();
+            } else {
+                if ((e2 = launch_matvec_v(ov, gv, iv, track, v, w, 1, dt64, tuned_variant(b, 1, dt64), s)) !=
+                    cudaSuccess)
+                    return e2;
+                k_dot_part<kC, false><<<nparts, kRedThreads, 0, s>>>(v, w, n, part_a, tickets, alpha, jdev); count_launch();
+                k_update<kC, false><<<nparts, kRedThreads, 0, s>>>(w, w, v, vp, n, alpha, beta, part_b,
+                                                                    tickets + 1, beta + 1, jdev); count_launch();
+            }
+            k_normalize<kC><<<vgrid, kRedThreads, 0, s>>>(w, vn, use_f32 ? x32 : nullptr, n, beta + 1, jdev, Vs); count_launch();
+            k_step_inc<<<1, 1, 0, s>>>(jdev); count_launch();
+            return cudaGetLastError();
+        };
+        if ((e = step(ring[0], nullptr, ring[1], st)) != cudaSuccess)
+            return e;
+        ++matvecs;
+        int done = 1;
+        if (m - done >= 2) {
+            if (!GR.cap && (e = cudaStreamCreateWithFlags(&GR.cap, cudaStreamNonBlocking)) != cudaSuccess)
+                return e;
+            const unsigned long long c0 = launches_so_far();
+            if ((e = cudaStreamBeginCapture(GR.cap, cudaStreamCaptureModeRelaxed)) != cudaSuccess)
+                return e;
+            e = step(ring[1], ring[0], ring[0], GR.cap);
+            if (e == cudaSuccess)
+                e = step(ring[0], ring[1], ring[1], GR.cap);
+            cudaGraph_t g = nullptr;
+            const cudaError_t e2 = cudaStreamEndCapture(GR.cap, &g);
+            if (g)
+                GR.graphs.push_back(g);
+            if (e != cudaSuccess || e2 != cudaSuccess)
+                return e != cudaSuccess ? e : e2;
+            const unsigned per_graph = (unsigned)(launches_so_far() - c0);
+            uncount_launch(per_graph);  // captured, not yet run
+            cudaGraphExec_t ge = nullptr;
+            if ((e = cudaGraphInstantiate(&ge, g, 0)) != cudaSuccess)
+                return e;
+            GR.execs.push_back(ge);
+            for (; m - done >= 2; done += 2) {
+                if ((e = cudaGraphLaunch(ge, st)) != cudaSuccess)
+                    return e;
+                count_launch(per_graph);
+                matvecs += 2;
+            }
+        }
+        if (done < m) {  // odd remainder: v in ring[1]
+            if ((e = step(ring[1], ring[0], ring[0], st)) != cudaSuccess)
+                return e;
+            ++matvecs;
+        }
+        return cudaGetLastError();
+    };
+    auto run_any = [&](const D *start, int m, bool use_f32, D *Vs, const double *acc_y) -> cudaError_t {
+        return graph ? run_g(start, m, use_f32, Vs, acc_y) : run(start, m, use_f32, Vs, acc_y);
+    };
+
     // main pass
-    ED_L_TRY(run((const D *)x0, steps, f32, store ? V : nullptr, nullptr));
+    ED_L_TRY(run_any((const D *)x0, steps, f32, store ? V : nullptr, nullptr));
     ED_L_TRY(cudaMemsetAsync(y, 0, (mmax + 1) * sizeof(double), st));
     k_tridiag_lowest<<<1, 32, 0, st>>>(alpha, beta, steps, y, scal + 0, m_eff, work); count_launch();
     if (n_eig > 0) {
@@ -847,7 +980,7 @@ ed_status run_lanczos(const ed_operator *op, const ed_basis *b, const void *x0, 
     if (store) {
         k_combine<kC><<<vgrid, kRedThreads, 0, st>>>(psi, V, y, m_eff, n); count_launch();
     } else {
-        ED_L_TRY(run((const D *)x0, steps, f32, nullptr, y));  // bit-identical second pass
+        ED_L_TRY(run_any((const D *)x0, steps, f32, nullptr, y));  // bit-identical second pass
     }
     ED_L_TRY(cudaGetLastError());
     double ritz = 0.0;
@@ -878,13 +1011,13 @@ ed_status run_lanczos(const ed_operator *op, const ed_basis *b, const void *x0, 
             ED_L_TRY(S.get(&ring[1], n));
         }
         ED_L_TRY(cudaMemsetAsync(beta, 0, (mmax + 2) * sizeof(double), st));
-        ED_L_TRY(run(psi, mref, false, Vr, nullptr));
+        ED_L_TRY(run_any(psi, mref, false, Vr, nullptr));
         ED_L_TRY(cudaMemsetAsync(y, 0, (mmax + 1) * sizeof(double), st));
         k_tridiag_lowest<<<1, 32, 0, st>>>(alpha, beta, mref, y, scal + 1, m_eff, work); count_launch();
         if (store_r) {
             k_combine<kC><<<vgrid, kRedThreads, 0, st>>>(psi, Vr, y, m_eff, n); count_launch();
         } else {
-            ED_L_TRY(run(psi, mref, false, nullptr, y));
+            ED_L_TRY(run_any(psi, mref, false, nullptr, y));
         }
         ED_L_TRY(cudaGetLastError());
     }
@@ -957,6 +1090,15 @@ ed_status lanczos_entry(const ed_operator *op, const ed_basis *b, const void *x0
     return r;
 }
 }  // namespace
+
+// Test hook: steps replayed from a CUDA graph (-1 automatic, 0 never, 1
+// always); returns the previous policy.
+extern "C" int edx_lanczos_graph(int policy)
+{
+    const int old = edk::g_lanczos_graph;
+    edk::g_lanczos_graph = policy < 0 ? -1 : (policy ? 1 : 0);
+    return old;
+}
 
 extern "C" ed_status ed_lanczos(const ed_operator *op, const ed_basis *b, const void *x0, int steps,
                                 int mode_flags, double *e0_out, void *vec_out,

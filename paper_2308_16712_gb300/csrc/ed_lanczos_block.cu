@@ -246,28 +246,37 @@ __device__ __forceinline__ void gram_tile(const float *sxh, const float *sxl, co
                                           GramAcc &acc)
 {
     using L = GramLayout<P, NM>;
+    // slices beyond the tile's rows (small P) stay idle; the others take
+    // kRows rows each, unrolled with compile-time offsets
+    constexpr int kActive = L::kSlices < kTileRows ? L::kSlices : kTileRows;
+    constexpr int kRows = kTileRows / kActive;
+    static_assert(kTileRows % kActive == 0, "slices must divide the tile");
     const int grp = threadIdx.x % L::kGroups, sl = threadIdx.x / L::kGroups;
-    if (sl >= L::kSlices)
+    if (sl >= kActive)
         return;
     const int m = grp / (L::kHalf * L::kHalf), rem = grp % (L::kHalf * L::kHalf);
     const int a0 = 2 * (rem / L::kHalf), b0 = 2 * (rem % L::kHalf);
-    const float *xh = sxh + m * kXs, *xl = sxl + m * kXs;
+    // (a0, a0 + 1) and (b0, b0 + 1) are adjacent, 8-byte aligned pairs
+    const float2 *xh = reinterpret_cast<const float2 *>(sxh + m * kXs + sl * P + a0);
+    const float2 *xl = reinterpret_cast<const float2 *>(sxl + m * kXs + sl * P + a0);
+    const float2 *yh = reinterpret_cast<const float2 *>(syh + sl * P + b0);
+    const float2 *yl = reinterpret_cast<const float2 *>(syl + sl * P + b0);
+    constexpr int kStep = kActive * P / 2;  // float2 elements between a slice's rows
     float s[4] = {0.f, 0.f, 0.f, 0.f}, c[4] = {0.f, 0.f, 0.f, 0.f};
-    for (int r = sl; r < kTileRows; r += L::kSlices) {
-        const float x0h = xh[r * P + a0], x1h = xh[r * P + a0 + 1];
-        const float x0l = xl[r * P + a0], x1l = xl[r * P + a0 + 1];
-        const float y0h = syh[r * P + b0], y1h = syh[r * P + b0 + 1];
+#pragma unroll
+    for (int i = 0; i < kRows; ++i) {
+        const float2 x_h = xh[i * kStep], x_l = xl[i * kStep], y_h = yh[i * kStep];
         if constexpr (kYlow) {
-            const float y0l = syl[r * P + b0], y1l = syl[r * P + b0 + 1];
-            dd_acc(x0h, x0l, y0h, y0l, s[0], c[0]);
-            dd_acc(x0h, x0l, y1h, y1l, s[1], c[1]);
-            dd_acc(x1h, x1l, y0h, y0l, s[2], c[2]);
-            dd_acc(x1h, x1l, y1h, y1l, s[3], c[3]);
+            const float2 y_l = yl[i * kStep];
+            dd_acc(x_h.x, x_l.x, y_h.x, y_l.x, s[0], c[0]);
+            dd_acc(x_h.x, x_l.x, y_h.y, y_l.y, s[1], c[1]);
+            dd_acc(x_h.y, x_l.y, y_h.x, y_l.x, s[2], c[2]);
+            dd_acc(x_h.y, x_l.y, y_h.y, y_l.y, s[3], c[3]);
         } else {
-            dd_acc1(x0h, x0l, y0h, s[0], c[0]);
-            dd_acc1(x0h, x0l, y1h, s[1], c[1]);
-            dd_acc1(x1h, x1l, y0h, s[2], c[2]);
-            dd_acc1(x1h, x1l, y1h, s[3], c[3]);
+            dd_acc1(x_h.x, x_l.x, y_h.x, s[0], c[0]);
+            dd_acc1(x_h.x, x_l.x, y_h.y, s[1], c[1]);
+            dd_acc1(x_h.y, x_l.y, y_h.x, s[2], c[2]);
+            dd_acc1(x_h.y, x_l.y, y_h.y, s[3], c[3]);
         }
     }
 #pragma unroll
@@ -314,8 +323,8 @@ __global__ void __launch_bounds__(kBlThreads) k_dd_gram(const float *X0h, const 
 {
     if (*stop)
         return;
-    __shared__ float sxh[NM * kXStride<P>], sxl[NM * kXStride<P>];
-    __shared__ float syh[kTileRows * P], syl[kTileRows * P];
+    __shared__ __align__(16) float sxh[NM * kXStride<P>], sxl[NM * kXStride<P>];
+    __shared__ __align__(16) float syh[kTileRows * P], syl[kTileRows * P];
     __shared__ double red[kBlThreads * 4];
     GramAcc acc;
     acc.init();
@@ -416,8 +425,10 @@ template <int P>
 struct SymLayout {
     static constexpr int kHalf = P / 2;
     static constexpr int kGroups = kHalf * (kHalf + 1) / 2;
-    static constexpr int kSlices = kBlThreads / kGroups;
-    static constexpr int kStride = P + 1;
+    static constexpr int kSlices = kGroups == 1 ? 256 : kGroups <= 4 ? 64 : kGroups <= 16 ? 16 : 4;
+    static constexpr int kRows = kBlThreads / kSlices;  // rows per slice and tile
+    static constexpr int kStride = P + 2;               // even: 8-byte aligned pairs
+    static_assert(kGroups * kSlices <= kBlThreads && kBlThreads % kSlices == 0, "layout");
     __device__ static int index(int ga, int gb) { return ga * kHalf - ga * (ga - 1) / 2 + (gb - ga); }
     __device__ static void groups(int g, int &ga, int &gb)
     {
@@ -439,16 +450,19 @@ __device__ __forceinline__ void gram_tile_sym(const float *sh, const float *sl, 
         return;
     int ga, gb;
     L::groups(grp, ga, gb);
-    const int a0 = 2 * ga, b0 = 2 * gb;
+    const float2 *xh = reinterpret_cast<const float2 *>(sh + slc * L::kStride + 2 * ga);
+    const float2 *xl = reinterpret_cast<const float2 *>(sl + slc * L::kStride + 2 * ga);
+    const float2 *yh = reinterpret_cast<const float2 *>(sh + slc * L::kStride + 2 * gb);
+    const float2 *yl = reinterpret_cast<const float2 *>(sl + slc * L::kStride + 2 * gb);
+    constexpr int kStep = L::kSlices * L::kStride / 2;
     float s[4] = {0.f, 0.f, 0.f, 0.f}, c[4] = {0.f, 0.f, 0.f, 0.f};
-    for (int r = slc; r < kBlThreads; r += L::kSlices) {
-        const float *xh = sh + r * L::kStride, *xl = sl + r * L::kStride;
-        const float x0h = xh[a0], x1h = xh[a0 + 1], x0l = xl[a0], x1l = xl[a0 + 1];
-        const float y0h = xh[b0], y1h = xh[b0 + 1], y0l = xl[b0], y1l = xl[b0 + 1];
-        dd_acc(x0h, x0l, y0h, y0l, s[0], c[0]);
-        dd_acc(x0h, x0l, y1h, y1l, s[1], c[1]);
-        dd_acc(x1h, x1l, y0h, y0l, s[2], c[2]);
-        dd_acc(x1h, x1l, y1h, y1l, s[3], c[3]);
+#pragma unroll
+    for (int i = 0; i < L::kRows; ++i) {
+        const float2 x_h = xh[i * kStep], x_l = xl[i * kStep], y_h = yh[i * kStep], y_l = yl[i * kStep];
+        dd_acc(x_h.x, x_l.x, y_h.x, y_l.x, s[0], c[0]);
+        dd_acc(x_h.x, x_l.x, y_h.y, y_l.y, s[1], c[1]);
+        dd_acc(x_h.y, x_l.y, y_h.x, y_l.x, s[2], c[2]);
+        dd_acc(x_h.y, x_l.y, y_h.y, y_l.y, s[3], c[3]);
     }
 #pragma unroll
     for (int k = 0; k < 4; ++k)
@@ -499,8 +513,8 @@ __global__ void __launch_bounds__(kBlThreads) k_dd_update(const float *X0h, cons
     if (*stop)
         return;
     using L = SymLayout<P>;
-    __shared__ float2 sc[NM * P * P];
-    __shared__ float swh[kBlThreads * L::kStride], swl[kBlThreads * L::kStride];
+    __shared__ __align__(16) float2 sc[NM * P * P];
+    __shared__ __align__(16) float swh[kBlThreads * L::kStride], swl[kBlThreads * L::kStride];
     __shared__ double red[kBlThreads * 4];
     for (int e = threadIdx.x; e < NM * P * P; e += blockDim.x) {
         float h, l;
@@ -525,9 +539,10 @@ __global__ void __launch_bounds__(kBlThreads) k_dd_update(const float *X0h, cons
 #pragma unroll
                 for (int a = 0; a < P; ++a)
 #pragma unroll
-                    for (int b = 0; b < P; ++b) {
-                        const float2 q = sc[m * P * P + a * P + b];
+                    for (int b = 0; b < P; b += 2) {  // two (high, low) coefficients per load
+                        const float4 q = reinterpret_cast<const float4 *>(sc + m * P * P + a * P)[b / 2];
                         dd_acc(xh[a], xl[a], q.x, q.y, s[b], c[b]);
+                        dd_acc(xh[a], xl[a], q.z, q.w, s[b + 1], c[b + 1]);
                     }
             }
 #pragma unroll
@@ -568,8 +583,8 @@ __global__ void __launch_bounds__(kBlThreads) k_dd_qr(float *Wh, float *Wl, cons
         return;
     using L = SymLayout<P>;
     constexpr int kZ = kApply ? 1 : kBlThreads * L::kStride;
-    __shared__ float2 sr[P * P];
-    __shared__ float szh[kZ], szl[kZ];
+    __shared__ __align__(16) float2 sr[P * P];
+    __shared__ __align__(16) float szh[kZ], szl[kZ];
     __shared__ double red[kApply ? 1 : kBlThreads * 4];
     for (int e = threadIdx.x; e < P * P; e += blockDim.x) {
         const int a = e / P, b = e % P;

@@ -86,6 +86,7 @@ _SIGS = {
     "edx_index_policy": (None, [_i32]),
     "edx_inject_stall": (None, [_i32]),
     "edx_multi_policy": (None, [_i32]),
+    "edx_lanczos_graph": (_i32, [_i32]),
     "edx_peak": (_d, [_i32, _P, _u64, ctypes.POINTER(_d), _P]),
     "edx_basis_bucket": (_i32, [_P, ctypes.POINTER(_i32), ctypes.POINTER(ctypes.c_uint32)]),
     "edx_count_nnz": (_i32, [_P, _P, ctypes.POINTER(ctypes.c_ulonglong)]),
@@ -296,6 +297,13 @@ def force_all_rotations(on: bool) -> None:
     """Test hook: the factored group search visits every rotation (no pruning
     to the tops of the longest runs of equal bits)."""
     _lib.edx_force_all_rotations(1 if on else 0)
+
+
+def lanczos_graph(policy: int) -> int:
+    """Test hook: single-sector Lanczos steps replayed from a CUDA graph (-1
+    for sectors of at most 2^22 states, 0 never, 1 always); returns the
+    previous policy."""
+    return _lib.edx_lanczos_graph(policy)
 
 
 INDEX_POLICIES = {"auto": 0, "hash": 1, "bucket": 2}

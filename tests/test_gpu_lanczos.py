@@ -206,3 +206,54 @@ def test_cached_workspace_memory_is_reused_and_released():
     ed.release_cached_memory()
     r3 = ed.lanczos(S["O"], S["B"], x0, 40, ed.ED_LANCZOS_F32_MATVEC)
     assert r3.e0 == r1.e0
+
+
+@pytest.mark.parametrize("mode_name", ["f64", "f32", "f64_recompute", "f32_recompute", "values_only"])
+@pytest.mark.parametrize("steps", [1, 2, 40, 41])
+def test_graph_replayed_steps_equal_eager_steps(mode_name, steps):
+    """Steps replayed from a CUDA graph (device step index, ring buffers
+    copied into the Krylov store) give the eager launches' results bit for
+    bit: energy, residual, Ritz values and vector."""
+    torch, ed = gpu()
+    w = ei.workload("ring16")
+    S = build_pair(16, 8, +1, w["perms"], w["chars"], w["op"], with_oracle=False)
+    x0 = to_torch(ei.x_by_index(3, S["dim"])[:, 0], np.float64)
+    mode = {"f64": ed.ED_LANCZOS_F64, "f32": ed.ED_LANCZOS_F32_MATVEC,
+            "f64_recompute": ed.ED_LANCZOS_F64 | ed.ED_LANCZOS_RECOMPUTE,
+            "f32_recompute": ed.ED_LANCZOS_F32_MATVEC | ed.ED_LANCZOS_RECOMPUTE,
+            "values_only": ed.ED_LANCZOS_F64 | ed.ED_LANCZOS_VALUES_ONLY}[mode_name]
+    out = {}
+    old = ed.lanczos_graph(0)
+    try:
+        for policy in (0, 1):
+            ed.lanczos_graph(policy)
+            v = None if mode_name == "values_only" else torch.empty_like(x0)
+            n_eig = min(3, steps)
+            eigs, r = ed.lanczos_eigs(S["O"], S["B"], x0, steps, n_eig, mode, vec_out=v)
+            out[policy] = (eigs, r.e0, r.residual, r.ritz, r.matvecs, v)
+    finally:
+        ed.lanczos_graph(old)
+    e, g = out[0], out[1]
+    assert e[0] == g[0] and e[1] == g[1] and e[2] == g[2] and e[3] == g[3] and e[4] == g[4]
+    if e[5] is not None:
+        assert torch.equal(e[5], g[5])
+
+
+def test_graph_replayed_complex_sector():
+    torch, ed = gpu()
+    p, c = ei.torus_group(4, 4, 1, 0)
+    op = ei.j1j2_torus(4, 4, 1.0, 0.5)
+    S = build_pair(16, 8, +1, p, c, op, with_oracle=False)
+    x0 = to_torch(ei.x_by_index(0, S["dim"], 1, True)[:, 0], np.complex128)
+    res = []
+    old = ed.lanczos_graph(0)
+    try:
+        for policy in (0, 1):
+            ed.lanczos_graph(policy)
+            v = torch.empty_like(x0)
+            r = ed.lanczos(S["O"], S["B"], x0, 37, ed.ED_LANCZOS_F32_MATVEC, vec_out=v)
+            res.append((r.e0, r.residual, v))
+    finally:
+        ed.lanczos_graph(old)
+    assert res[0][0] == res[1][0] and res[0][1] == res[1][1]
+    assert torch.equal(res[0][2], res[1][2])
