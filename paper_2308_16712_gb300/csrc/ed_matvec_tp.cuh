@@ -139,10 +139,16 @@ __device__ __forceinline__ uint32_t ent_norm(uint2 v, int nb) { return v.y & ((1
 __device__ __forceinline__ uint32_t ent_index(ulonglong2 v, int) { return (uint32_t)v.y; }
 __device__ __forceinline__ uint32_t ent_norm(ulonglong2 v, int) { return (uint32_t)(v.y >> 32); }
 
+// Resident blocks per SM the register budget is sized for: 6 (40 registers)
+// for 32-bit words with a hash index, else 5 (48 registers), so that no
+// variant spills.
+template <typename W, int kIdx>
+constexpr int kTpMinBlocks = sizeof(W) == 4 && kIdx != 2 ? 6 : 5;
+
 // kIdx: index of the sectors -- 0 hash index with 8-byte entries, 1 with
 // 16-byte entries, 2 bucketed index (find_bucketed)
 template <typename W, typename T, bool kC, bool kTrack, bool kFact, int kIdx, int kSec, bool kPush = false>
-__global__ void __launch_bounds__(kTpThreads, 8) k_matvec_tp(const __grid_constant__ TpArgs<kSec> a)
+__global__ void __launch_bounds__(kTpThreads, kTpMinBlocks<W, kIdx>) k_matvec_tp(const __grid_constant__ TpArgs<kSec> a)
 {
     using V = typename ValT<T, kC>::type;
     using E = std::conditional_t<kIdx == 1, ulonglong2, uint2>;
