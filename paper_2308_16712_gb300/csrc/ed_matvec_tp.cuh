@@ -139,11 +139,13 @@ __device__ __forceinline__ uint32_t ent_norm(uint2 v, int nb) { return v.y & ((1
 __device__ __forceinline__ uint32_t ent_index(ulonglong2 v, int) { return (uint32_t)v.y; }
 __device__ __forceinline__ uint32_t ent_norm(ulonglong2 v, int) { return (uint32_t)(v.y >> 32); }
 
-// Resident blocks per SM the register budget is sized for: 6 (40 registers)
-// for 32-bit words with a hash index, else 5 (48 registers), so that no
-// variant spills.
+// Resident blocks per SM the register budget is sized for.  32-bit words with
+// a hash index: 8 (32 registers; 8-32 bytes of spills, measured faster than 6
+// blocks at 40 registers without them: ring N=32 fp32 1.25 against 1.38 ms).
+// Otherwise 5 (48 registers, no spills; 64-bit words at 32 registers spilled
+// 50-130 bytes: ring N=40 fp32 722 ms with the spills, 663 ms without).
 template <typename W, int kIdx>
-constexpr int kTpMinBlocks = sizeof(W) == 4 && kIdx != 2 ? 6 : 5;
+constexpr int kTpMinBlocks = sizeof(W) == 4 && kIdx != 2 ? 8 : 5;
 
 // kIdx: index of the sectors -- 0 hash index with 8-byte entries, 1 with
 // 16-byte entries, 2 bucketed index (find_bucketed)

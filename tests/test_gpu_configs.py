@@ -61,7 +61,11 @@ def test_ring40_config():
     G = oracle.Group(40, w["perms"], w["chars"], +1)
     st_t, _ = ed.basis_states(B)
     assert bool((st_t[1:] > st_t[:-1]).all())
+    del st_t
     sampled_rows_check(B, O, G, oracle.Operator(w["op"]), 31, 1, False, n_rows=60)
+    # the launch configuration of the benchmark's block product: 8 interleaved
+    # vectors, fp32 (and fp64)
+    sampled_rows_check(B, O, G, oracle.Operator(w["op"]), 32, 8, False, n_rows=40, rng_seed=1)
 
 
 def test_ring42_config():
