@@ -20,6 +20,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cstring>
 #include <type_traits>
 
 #include "ed_kernels.cuh"
@@ -61,6 +62,37 @@ __device__ __forceinline__ void store_cs(Cplx<float> *p, Cplx<float> v)
 __device__ __forceinline__ void store_cs(Cplx<double> *p, Cplx<double> v)
 {
     __stcs(reinterpret_cast<double2 *>(p), make_double2(v.re, v.im));
+}
+
+// Whole rows of an interleaved [dim][nvec] block with nvec == NV: NV values
+// by 16-byte loads and streaming 16-byte stores, for rows of a multiple of 16
+// bytes (the block starts 16-byte aligned).  One gather instruction per 16
+// bytes instead of one per value.
+template <typename V, int NV>
+constexpr bool kRowVec = (NV * sizeof(V)) % 16 == 0;
+
+template <typename V, int NV>
+__device__ __forceinline__ void load_row_v(const V *p, V (&out)[NV])
+{
+    constexpr int kW = (int)(NV * sizeof(V) / 16);
+    const uint4 *q = reinterpret_cast<const uint4 *>(p);
+    uint4 w[kW];
+#pragma unroll
+    for (int k = 0; k < kW; ++k)
+        w[k] = __ldg(q + k);
+    memcpy(out, w, sizeof(w));
+}
+
+template <typename V, int NV>
+__device__ __forceinline__ void store_row_v(V *p, const V (&in)[NV])
+{
+    constexpr int kW = (int)(NV * sizeof(V) / 16);
+    uint4 w[kW];
+    memcpy(w, in, sizeof(w));
+    uint4 *q = reinterpret_cast<uint4 *>(p);
+#pragma unroll
+    for (int k = 0; k < kW; ++k)
+        __stcs(q + k, w[k]);
 }
 
 // Shared-memory layout: masks | chi | families | matrices | offmask | coset kinds | sqrt tables
@@ -305,6 +337,12 @@ __global__ void __launch_bounds__(kMvThreads) k_matvec(const MatvecArgs a)
         }
     };
     auto store_row = [&]() {
+        if constexpr (kRowVec<V, NV>) {
+            if (nvec == NV) {
+                store_row_v<V, NV>(y + row * NV, acc);
+                return;
+            }
+        }
 #pragma unroll
         for (int v = 0; v < NV; ++v)
             if (v < nvec)
@@ -340,14 +378,26 @@ __global__ void __launch_bounds__(kMvThreads) k_matvec(const MatvecArgs a)
                         d.im += h.im * (T)cnt;
                     }
                 }
+                V xr[NV];
+                if constexpr (kRowVec<V, NV>) {
+                    if (nvec == NV)
+                        load_row_v<V, NV>(x + row * NV, xr);
+                    else
+#pragma unroll
+                        for (int v = 0; v < NV; ++v)
+                            xr[v] = v < nvec ? x[row * nvec + v] : V{};
+                } else {
+#pragma unroll
+                    for (int v = 0; v < NV; ++v)
+                        xr[v] = v < nvec ? x[row * nvec + v] : V{};
+                }
 #pragma unroll
                 for (int v = 0; v < NV; ++v) {
                     if (v < nvec) {
-                        const V xv = x[row * nvec + v];
                         if constexpr (kC)
-                            acc[v] = cmul(conjc(d), xv);
+                            acc[v] = cmul(conjc(d), xr[v]);
                         else
-                            acc[v] = d.re * xv;
+                            acc[v] = d.re * xr[v];
                     }
                 }
                 // first family
@@ -415,10 +465,23 @@ __global__ void __launch_bounds__(kMvThreads) k_matvec(const MatvecArgs a)
                 Cplx<T> coef = {h.re * ratio, -h.im * ratio};  // conj(h) sqrt(n'/n)
                 if (kTrack)
                     coef = cmul(coef, sm_chi[gbest]);
+                V xg[NV];
+                if constexpr (kRowVec<V, NV>) {
+                    if (nvec == NV)
+                        load_row_v<V, NV>(x + j * NV, xg);
+                    else
+#pragma unroll
+                        for (int v = 0; v < NV; ++v)
+                            xg[v] = v < nvec ? x[j * nvec + v] : V{};
+                } else {
+#pragma unroll
+                    for (int v = 0; v < NV; ++v)
+                        xg[v] = v < nvec ? x[j * nvec + v] : V{};
+                }
 #pragma unroll
                 for (int v = 0; v < NV; ++v) {
                     if (v < nvec) {
-                        const V xv = x[(uint64_t)j * nvec + v];
+                        const V xv = xg[v];
                         if constexpr (kC) {
                             const Cplx<T> p = cmul(coef, xv);
                             acc[v].re += p.re;

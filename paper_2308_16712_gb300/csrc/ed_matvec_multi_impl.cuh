@@ -306,6 +306,12 @@ __global__ void __launch_bounds__(kMvThreads) k_matvec_multi(const __grid_consta
     };
     auto store_row = [&]() {
         V *y = reinterpret_cast<V *>(sm_sec[sec].y);
+        if constexpr (kRowVec<V, NV>) {
+            if (nvec == NV) {
+                store_row_v<V, NV>(y + row * NV, acc);
+                return;
+            }
+        }
 #pragma unroll
         for (int v = 0; v < NV; ++v)
             if (v < nvec)
@@ -355,14 +361,26 @@ __global__ void __launch_bounds__(kMvThreads) k_matvec_multi(const __grid_consta
                             d.im += h.im * (T)pc;
                         }
                     }
+                    V xr[NV];
+                    if constexpr (kRowVec<V, NV>) {
+                        if (nvec == NV)
+                            load_row_v<V, NV>(x + row * NV, xr);
+                        else
+#pragma unroll
+                            for (int v = 0; v < NV; ++v)
+                                xr[v] = v < nvec ? x[row * nvec + v] : V{};
+                    } else {
+#pragma unroll
+                        for (int v = 0; v < NV; ++v)
+                            xr[v] = v < nvec ? x[row * nvec + v] : V{};
+                    }
 #pragma unroll
                     for (int v = 0; v < NV; ++v) {
                         if (v < nvec) {
-                            const V xv = x[row * nvec + v];
                             if constexpr (kC)
-                                acc[v] = cmul(conjc(d), xv);
+                                acc[v] = cmul(conjc(d), xr[v]);
                             else
-                                acc[v] = d.re * xv;
+                                acc[v] = d.re * xr[v];
                         }
                     }
                     f = 0;
@@ -430,10 +448,23 @@ __global__ void __launch_bounds__(kMvThreads) k_matvec_multi(const __grid_consta
                     coef = cmul(coef, ch);
                 }
                 const V *x = reinterpret_cast<const V *>(sd.x);
+                V xg[NV];
+                if constexpr (kRowVec<V, NV>) {
+                    if (nvec == NV)
+                        load_row_v<V, NV>(x + j * NV, xg);
+                    else
+#pragma unroll
+                        for (int v = 0; v < NV; ++v)
+                            xg[v] = v < nvec ? x[j * nvec + v] : V{};
+                } else {
+#pragma unroll
+                    for (int v = 0; v < NV; ++v)
+                        xg[v] = v < nvec ? x[j * nvec + v] : V{};
+                }
 #pragma unroll
                 for (int v = 0; v < NV; ++v) {
                     if (v < nvec) {
-                        const V xv = x[j * nvec + v];
+                        const V xv = xg[v];
                         if constexpr (kC) {
                             const Cplx<T> pr = cmul(coef, xv);
                             acc[v].re += pr.re;
