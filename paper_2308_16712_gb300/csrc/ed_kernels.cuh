@@ -145,6 +145,6 @@ cudaError_t launch_matvec_push(const OpView &op, const GroupView &g, const Index
 // precision (where the term-parallel kernel's fp64 segmented sums cost more
 // than they save); 1 = always row-per-lane; 2 = always term-parallel.
 extern int g_kernel_policy;
-bool use_term_parallel(int nvec, const OpView &op, ed_dtype dtype);
+bool use_term_parallel(int nvec, const OpView &op, ed_dtype dtype, int n_sites);
 
 }  // namespace edk

@@ -5,11 +5,15 @@ namespace edk {
 
 int g_kernel_policy = 0;
 
-bool use_term_parallel(int nvec, const OpView &op, ed_dtype dtype)
+// The library's kernel rule for one vector of an exchange-only operator: the
+// term-parallel kernel in single precision, and in double precision for
+// 64-bit words (ring N=36 / 40 fp64: 42.5 / 714 ms against 45.1 / 750 ms
+// row-per-lane); row-per-lane otherwise.
+bool use_term_parallel(int nvec, const OpView &op, ed_dtype dtype, int n_sites)
 {
     if (nvec != 1 || !op.exchange_only || g_kernel_policy == 1)
         return false;
-    return g_kernel_policy == 2 || dtype == ED_F32 || dtype == ED_C64;
+    return g_kernel_policy == 2 || dtype == ED_F32 || dtype == ED_C64 || n_sites > 32;
 }
 
 static TpArgs<1> single_tp_args(const OpView &op, const GroupView &g, const IndexView &ix, const void *x,
@@ -70,7 +74,7 @@ cudaError_t launch_matvec_v(const OpView &op, GroupView g, const IndexView &ix, 
     if (v.prune >= 0 && g.fact && g.rot_d == 1)
         g.prune = v.prune;
     const bool tp_ok = (ix.htab || ix.bkt) && nvec == 1 && op.exchange_only;
-    const bool tp = tp_ok && (v.kernel == 2 || (v.kernel == 0 && use_term_parallel(nvec, op, dtype)));
+    const bool tp = tp_ok && (v.kernel == 2 || (v.kernel == 0 && use_term_parallel(nvec, op, dtype, g.n_sites)));
     if (tp) {
         const TpArgs<1> t = single_tp_args(op, g, ix, x, y);
         const int k = tp_index_kind(t.sec[0]);

@@ -90,7 +90,7 @@ cudaError_t multi_launch_any(const MultiArgs &a, bool track, ed_dtype dtype, cud
     bool same_kind = true;
     for (int k = 1; k < a.n_sectors; ++k)
         same_kind = same_kind && tp_index_kind(a.sec[k]) == tp_index_kind(a.sec[0]);
-    if (same_kind && use_term_parallel(a.nvec, a.op, dtype)) {
+    if (same_kind && use_term_parallel(a.nvec, a.op, dtype, a.g.n_sites)) {
         const int kind = a.n_sectors > 0 ? tp_index_kind(a.sec[0]) : 0;
         static thread_local TpArgs<kMaxSectors> t;  // host staging (17 KB); copied at launch
         t.op = a.op;
@@ -221,7 +221,7 @@ extern "C" ed_status ed_matvec_multi(const ed_operator *op, const ed_sector *sec
         all_large = all_large && (!sectors[s].basis->dim || sectors[s].basis->dim >= (uint64_t)sms * 2048);
     cudaError_t e = cudaSuccess;
     const bool per_sector = g_multi_policy == 2 && all_large;
-    if (per_sector && use_term_parallel(nvec, args.op, dtype)) {
+    if (per_sector && use_term_parallel(nvec, args.op, dtype, args.g.n_sites)) {
         for (int s = 0; s < n_sectors && e == cudaSuccess; ++s) {
             const ed_basis *b = sectors[s].basis;
             if (b->dim)

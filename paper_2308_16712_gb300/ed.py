@@ -410,7 +410,8 @@ KERNEL_POLICIES = {"auto": 0, "rowwise": 1, "term_parallel": 2}
 
 def kernel_policy(policy: str) -> None:
     """Testing aid: which matvec kernel serves one vector of an exchange-only
-    operator: "auto" (term-parallel in single precision, row-per-lane in double),
+    operator: "auto" (term-parallel in single precision and for more than 32
+    sites, row-per-lane otherwise),
     "rowwise" or "term_parallel" (both precisions).  Affects later launches."""
     _lib.edx_kernel_policy(KERNEL_POLICIES[policy])
 
