@@ -774,8 +774,10 @@ def run_job(args, w):
     roofline["random_access"] = {"accesses_per_launch": accesses, "achieved_per_s": accesses / t_s,
                                  "peak_per_s": gather_peak, "frac": accesses / t_s / gather_peak,
                                  "peak_kind": "measured live: random 32-byte reads over 8 GiB"}
+    # the slower of the algorithmic bytes at the HBM peak and the search's
+    # integer ops at the integer peak, against the measured launch time
     roofline_time = max(alg_bytes / (hbm_peak * 1e9), int_ops / int_peak)
-    roofline["north_star_roofline_frac"] = roofline_time / t_s
+    roofline["bytes_or_ops_frac"] = roofline_time / t_s
 
     # ---- CPU oracle on sampled rows of the same sector ---------------------------
     cpu = None
