@@ -234,6 +234,14 @@ def cpu_baseline(w, budget_s=8.0, par_wall_s=4.0):
             "single_core": single, "nnz_per_row": float(nnz.mean())}
 
 
+def workload_label(w):
+    """The workload name both arms print in config.workload."""
+    if w["name"] == "ring40":
+        return ("ring40: Heisenberg ring N=40, J=1, Sz=0, k=0, p=+1, z=+1 "
+                "(the paper's Table 2 sector for 40 spins)")
+    return w["name"]
+
+
 def run_reference(args, w, budget_s=150.0):
     """The reference arm: the CPU oracle timed on the machine's host cores (rank 0
     only; other ranks exit without work), each step a bounded sample of rows
@@ -260,7 +268,10 @@ def run_reference(args, w, budget_s=150.0):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": w["name"], "rows_per_step": rows_per_step},
+            "data": "synthetic",
+            "config": {"workload": workload_label(w),
+                       "group_order": len(w["perms"]) * (2 if w["spin_inversion"] else 1), "nvec": args.nvec,
+                       "rows_per_step": rows_per_step},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                              "sample": f"{len(step_rows)} rows per step of the {w['name']} sector "
                                        f"({rows_per_step} distinct), the C oracle in {cores} spawned "
@@ -824,9 +835,7 @@ def run_job(args, w):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": per_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": f"{w['name']}: Heisenberg ring N={n}, J=1, Sz=0, k=0, p=+1, z=+1 "
-                               "(the paper's Table 2 sector for 40 spins)" if w["name"] == "ring40"
-                               else w["name"],
+        "config": {"workload": workload_label(w),
                    "dim": dim, "group_order": len(w["perms"]) * (2 if z else 1), "nvec": nvec,
                    "step": f"one block-Lanczos step: fp32 block product of {nvec} interleaved vectors + "
                            "block recurrence (double-float arithmetic, fp64 coefficients and merges)",
