@@ -270,7 +270,8 @@ def run_reference(args, w, budget_s=150.0):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
             "config": {"workload": workload_label(w),
-                       "group_order": len(w["perms"]) * (2 if w["spin_inversion"] else 1), "nvec": args.nvec,
+                       "group_order": len(w["perms"]) * (2 if w["spin_inversion"] else 1),
+                       "nvec": getattr(args, "nvec", 8),
                        "rows_per_step": rows_per_step},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                              "sample": f"{len(step_rows)} rows per step of the {w['name']} sector "
