@@ -53,13 +53,13 @@ L2_BYTES = 129 * 1024 * 1024
 SMS = 152
 INT_LANES_PER_SM = 64
 # DRAM bytes (read + write) per stored nonzero of one launch of the timed
-# kernel (fp32 block product, keyed by nvec), from one ncu --set full capture of
-# the same kernel on the ring N=36 sector (nvec = 8: 161.04 + 2.02 GB for
-# 1 230 759 430 nonzeros).  A ring N=40 launch is too large for a many-pass
-# capture, so its traffic is this figure times the nonzeros it processes.
-# Retake the capture and update the figure whenever the kernel changes (the
-# roofline reports null traffic for nvec not listed).
-KERNEL_DRAM_BYTES_PER_NNZ = {8: (161.040283e9 + 2.023800e9) / 1230759430}
+# kernel (fp32 block product, keyed by kernel and nvec), from one ncu --set
+# full capture of the same kernel on the ring N=36 sector (row-per-lane, nvec
+# = 8: 161.04 + 2.02 GB for 1 230 759 430 nonzeros).  A ring N=40 launch is too
+# large for a many-pass capture, so its traffic is this figure times the
+# nonzeros it processes.  Retake the capture and update the figure whenever the
+# kernel changes (the roofline reports null traffic for kernels not listed).
+KERNEL_DRAM_BYTES_PER_NNZ = {("row-per-lane", 8): (161.040283e9 + 2.023800e9) / 1230759430}
 
 
 def peaks():
@@ -761,15 +761,18 @@ def run_job(args, w):
     sector_bytes = dim * (8 + 2 * 4 * nvec) + terms * (32 + max(32, 4 * nvec))  # bucket + x row per term
     t_s = prod_ms * 1e-3
     achieved_int = int_ops / t_s / 1e12
+    kern_kind = "row-per-lane" if tuning.get("kernel") == 1 else "term-parallel"
     roofline = {
         "bound": "alu", "achieved": achieved_int, "peak": int_peak / 1e12, "unit": "TOP/s",
         "frac": achieved_int / (int_peak / 1e12),
-        "traffic": (KERNEL_DRAM_BYTES_PER_NNZ[nvec] * nnz_total if nvec in KERNEL_DRAM_BYTES_PER_NNZ
-                    else None),
+        "traffic": (KERNEL_DRAM_BYTES_PER_NNZ[(kern_kind, nvec)] * nnz_total
+                    if (kern_kind, nvec) in KERNEL_DRAM_BYTES_PER_NNZ else None),
         "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of the ring N=36 launch, "
                           "scaled by stored nonzeros",
-        "kernel": f"k_matvec (row-per-lane, fp32, nvec={nvec}, pruned rotation search, 64-bit words, "
-                  "bucketed index)",
+        "kernel": (("k_matvec (row-per-lane" if kern_kind == "row-per-lane" else "k_matvec_tp (term-parallel")
+                   + f", fp32, nvec={nvec}, "
+                   + ("pruned rotation search" if tuning.get("search") != 0 else "search over every rotation")
+                   + ", 64-bit words, bucketed index)"),
         "peak_kind": "measured live: int32 op mix of the search (funnel shift, lop3, min, add) on every SM",
         "int_ops_per_launch": int_ops, "int_ops_per_term": ops_term,
         "run_length_iterations_per_term": run_iters, "candidate_tops_per_term_and_coset": cands,
@@ -868,8 +871,8 @@ def run_job(args, w):
                 "d2h_bytes_per_step": 8 * nvec / args.steps,
                 "path": "pinned host start block -> device, ed_lanczos_block over the same steps, Ritz "
                         "values -> host"},
-        "autotune": {"product": tuning, "kernel_names": {"0": "library rule", "1": "row-per-lane",
-                                                          "2": "term-parallel"},
+        "autotune": {"product": tuning, "kernel_names": {"0": "library rule (term-parallel for fp32 blocks of 8)",
+                                                          "1": "row-per-lane", "2": "term-parallel"},
                      "search_names": {"-1": "n/a", "0": "every rotation", "1": "pruned to the longest runs"}},
         "gpu_launches": launches,
         "clocks": clocks,

@@ -230,14 +230,15 @@ void ed_operator_destroy(ed_operator *op);
  *
  * Two kernels: rows handed to lanes (each lane walks its row's terms), and,
  * for nvec = 1 in single precision (and in double precision above 32 sites)
- * with an operator whose off-diagonal entries only exchange antiparallel
- * spins (|01> <-> |10>), a term-parallel
+ * or an fp32 block of nvec = 8, with an operator whose off-diagonal entries
+ * only exchange antiparallel spins (|01> <-> |10>), a term-parallel
  * kernel (a warp lays a tile's terms out flat, one term per lane per round,
  * and sums each row with a segmented warp scan).  The two sum a row's terms in
  * different orders, so a column of an nvec > 1 product may differ from the
  * nvec = 1 product in the last bits.  ed_autotune replaces this rule (and the
  * choice of representative search) by measured choices for sectors of the
- * same shape.
+ * same shape.  On a real block of 8 vectors the term-parallel kernel sums
+ * every column in the order of its single-vector form.
  *
  * No allocation and no host synchronisation.  Deterministic: the same inputs
  * give bit-identical y.  Errors: ED_ERR_INVALID_ARG (including a complex

@@ -73,11 +73,21 @@ cudaError_t launch_matvec_v(const OpView &op, GroupView g, const IndexView &ix, 
 {
     if (v.prune >= 0 && g.fact && g.rot_d == 1)
         g.prune = v.prune;
-    const bool tp_ok = (ix.htab || ix.bkt) && nvec == 1 && op.exchange_only;
-    const bool tp = tp_ok && (v.kernel == 2 || (v.kernel == 0 && use_term_parallel(nvec, op, dtype, g.n_sites)));
+    // the term-parallel kernel: one vector (use_term_parallel), or a real
+    // block of 8 vectors: by default in fp32 (ring N=32 / 36 / 40: 1.69 /
+    // 43.6 / 724 ms against 2.04 / 48.4 / 788 ms row-per-lane), in fp64 when
+    // the autotuner or the test policy chooses it (its segmented scan adds on
+    // the slow fp64 pipe)
+    const bool block8 = nvec == 8 && (dtype == ED_F64 || dtype == ED_F32);
+    const bool tp_ok = (ix.htab || ix.bkt) && (nvec == 1 || block8) && op.exchange_only;
+    const bool rule = block8 ? (g_kernel_policy == 2 || (g_kernel_policy == 0 && dtype == ED_F32))
+                             : use_term_parallel(nvec, op, dtype, g.n_sites);
+    const bool tp = tp_ok && (v.kernel == 2 || (v.kernel == 0 && rule));
     if (tp) {
         const TpArgs<1> t = single_tp_args(op, g, ix, x, y);
         const int k = tp_index_kind(t.sec[0]);
+        if (block8)
+            return dtype == ED_F64 ? tp_single_f64_nv8(t, track, k, stream) : tp_single_f32_nv8(t, track, k, stream);
         switch (dtype) {
         case ED_F64: return tp_single_f64(t, track, k, stream);
         case ED_F32: return tp_single_f32(t, track, k, stream);

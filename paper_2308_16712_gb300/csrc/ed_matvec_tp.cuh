@@ -122,6 +122,89 @@ template <typename T> __device__ __forceinline__ Cplx<T> vshfl_up(Cplx<T> v, int
     return {__shfl_up_sync(0xffffffffu, v.re, o), __shfl_up_sync(0xffffffffu, v.im, o)};
 }
 
+// NV interleaved vectors of a real block as one value: a row of the block.
+// The segmented scan and the accumulators work on it componentwise; loads and
+// stores move it 16 bytes at a time.
+template <typename T, int NV>
+struct __align__(16) VecN {
+    T v[NV];
+};
+template <typename T, int NV>
+__device__ __forceinline__ VecN<T, NV> vadd(const VecN<T, NV> &a, const VecN<T, NV> &b)
+{
+    VecN<T, NV> r;
+#pragma unroll
+    for (int k = 0; k < NV; ++k)
+        r.v[k] = a.v[k] + b.v[k];
+    return r;
+}
+template <typename T, int NV>
+__device__ __forceinline__ VecN<T, NV> vshfl_up(const VecN<T, NV> &a, int o)
+{
+    VecN<T, NV> r;
+#pragma unroll
+    for (int k = 0; k < NV; ++k)
+        r.v[k] = __shfl_up_sync(0xffffffffu, a.v[k], o);
+    return r;
+}
+template <typename T, int NV>
+__device__ __forceinline__ VecN<T, NV> operator*(T s, const VecN<T, NV> &a)
+{
+    VecN<T, NV> r;
+#pragma unroll
+    for (int k = 0; k < NV; ++k)
+        r.v[k] = s * a.v[k];
+    return r;
+}
+template <typename V> struct IsVecN : std::false_type {};
+template <typename T, int NV> struct IsVecN<VecN<T, NV>> : std::true_type {};
+template <typename V>
+__device__ __forceinline__ V vzero_any()
+{
+    if constexpr (IsVecN<V>::value) {
+        V r;
+#pragma unroll
+        for (int k = 0; k < (int)(sizeof(V) / sizeof(r.v[0])); ++k)
+            r.v[k] = 0;
+        return r;
+    } else {
+        return vzero<V>();
+    }
+}
+template <typename V>
+__device__ __forceinline__ V vload(const V *p)
+{
+    if constexpr (IsVecN<V>::value) {
+        constexpr int kW = (int)(sizeof(V) / 16);
+        uint4 w[kW];
+        const uint4 *q = reinterpret_cast<const uint4 *>(p);
+#pragma unroll
+        for (int k = 0; k < kW; ++k)
+            w[k] = __ldg(q + k);
+        V r;
+        memcpy(&r, w, sizeof(V));
+        return r;
+    } else {
+        return *p;
+    }
+}
+template <typename T, int NV>
+__device__ __forceinline__ void store_cs(VecN<T, NV> *p, const VecN<T, NV> &a)
+{
+    constexpr int kW = (int)(sizeof(VecN<T, NV>) / 16);
+    uint4 w[kW];
+    memcpy(w, &a, sizeof(w));
+    uint4 *q = reinterpret_cast<uint4 *>(p);
+#pragma unroll
+    for (int k = 0; k < kW; ++k)
+        __stcs(q + k, w[k]);
+}
+
+// The row value of the term-parallel kernel: one scalar or complex number, or
+// NV > 1 interleaved real vectors
+template <typename T, bool kC, int NV>
+using TpVal = std::conditional_t<(NV > 1), VecN<T, NV>, typename ValT<T, kC>::type>;
+
 __device__ __forceinline__ void atomic_add(float *p, float v) { atomicAdd(p, v); }
 __device__ __forceinline__ void atomic_add(double *p, double v) { atomicAdd(p, v); }
 template <typename T> __device__ __forceinline__ void atomic_add(Cplx<T> *p, Cplx<T> v)
@@ -144,15 +227,19 @@ __device__ __forceinline__ uint32_t ent_norm(ulonglong2 v, int) { return (uint32
 // blocks at 40 registers without them: ring N=32 fp32 1.25 against 1.38 ms).
 // Otherwise 5 (48 registers, no spills; 64-bit words at 32 registers spilled
 // 50-130 bytes: ring N=40 fp32 722 ms with the spills, 663 ms without).
-template <typename W, int kIdx>
-constexpr int kTpMinBlocks = sizeof(W) == 4 && kIdx != 2 ? 8 : 5;
+template <typename W, int kIdx, int NV = 1>
+constexpr int kTpMinBlocks = NV > 1 ? 4 : (sizeof(W) == 4 && kIdx != 2 ? 8 : 5);
 
 // kIdx: index of the sectors -- 0 hash index with 8-byte entries, 1 with
-// 16-byte entries, 2 bucketed index (find_bucketed)
-template <typename W, typename T, bool kC, bool kTrack, bool kFact, int kIdx, int kSec, bool kPush = false>
-__global__ void __launch_bounds__(kTpThreads, kTpMinBlocks<W, kIdx>) k_matvec_tp(const __grid_constant__ TpArgs<kSec> a)
+// 16-byte entries, 2 bucketed index (find_bucketed).  NV > 1: a real block of
+// NV interleaved vectors (one search and lookup per term serves them all).
+template <typename W, typename T, bool kC, bool kTrack, bool kFact, int kIdx, int kSec, bool kPush = false,
+          int NV = 1>
+__global__ void __launch_bounds__(kTpThreads, kTpMinBlocks<W, kIdx, NV>)
+    k_matvec_tp(const __grid_constant__ TpArgs<kSec> a)
 {
-    using V = typename ValT<T, kC>::type;
+    static_assert(NV == 1 || (!kC && !kPush), "blocks: real, pull form");
+    using V = TpVal<T, kC, NV>;
     using E = std::conditional_t<kIdx == 1, ulonglong2, uint2>;
     extern __shared__ __align__(16) unsigned char smem[];
     size_t off[8];
@@ -234,7 +321,7 @@ __global__ void __launch_bounds__(kTpThreads, kTpMinBlocks<W, kIdx>) k_matvec_tp
         W r = 0;
         T rinv = T(0);
         uint32_t nt = 0;
-        V acc = vzero<V>();
+        V acc = vzero_any<V>();
         if (valid) {
             if (sd.keys) {
                 const uint64_t k = __ldcs(sd.keys + row);  // streamed once: evict first
@@ -258,7 +345,7 @@ __global__ void __launch_bounds__(kTpThreads, kTpMinBlocks<W, kIdx>) k_matvec_tp
                         nt += (uint32_t)cnt;
                 }
             }
-            const V xv = x[row];
+            const V xv = vload(x + row);
             if constexpr (kPush) {
                 // push form: the row's x is scattered, not gathered; the
                 // diagonal goes to y like every other contribution
@@ -384,7 +471,7 @@ __global__ void __launch_bounds__(kTpThreads, kTpMinBlocks<W, kIdx>) k_matvec_tp
             }
 
             // stateToIndex through the bucket of the hash index, gather, scale
-            V val = vzero<V>();
+            V val = vzero_any<V>();
             if (act) {
                 uint32_t jidx = 0, jnorm = 0;
                 bool found = false;
@@ -428,7 +515,7 @@ __global__ void __launch_bounds__(kTpThreads, kTpMinBlocks<W, kIdx>) k_matvec_tp
                                 pv = coef.re * xr;
                             atomic_add(reinterpret_cast<V *>(sd.y) + jidx, pv);
                         } else {
-                            const V xv = x[jidx];
+                            const V xv = vload(x + jidx);
                             if constexpr (kC)
                                 val = cmul(coef, xv);
                             else
@@ -457,11 +544,12 @@ __global__ void __launch_bounds__(kTpThreads, kTpMinBlocks<W, kIdx>) k_matvec_tp
     }
 }
 
-template <typename W, typename T, bool kC, bool kTrack, bool kFact, int kIdx, int kSec, bool kPush = false>
+template <typename W, typename T, bool kC, bool kTrack, bool kFact, int kIdx, int kSec, bool kPush = false,
+          int NV = 1>
 cudaError_t tp_launch(const TpArgs<kSec> &a, cudaStream_t stream)
 {
-    using V = typename ValT<T, kC>::type;
-    auto kern = k_matvec_tp<W, T, kC, kTrack, kFact, kIdx, kSec, kPush>;
+    using V = TpVal<T, kC, NV>;
+    auto kern = k_matvec_tp<W, T, kC, kTrack, kFact, kIdx, kSec, kPush, NV>;
     const size_t smem = tp_smem_bytes<W, T, V, kFact>(a.g, a.op, a.n_sectors, a.max_order);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess)
@@ -481,15 +569,15 @@ cudaError_t tp_launch(const TpArgs<kSec> &a, cudaStream_t stream)
 // idx: index kind of every sector of the batch (they must agree): 0 hash
 // index with 8-byte entries, 1 with 16-byte entries, 2 bucketed index; kPush:
 // the transposed (push) form with atomic scatter into y, which must be zero
-template <typename T, bool kC, int kSec, bool kPush = false>
+template <typename T, bool kC, int kSec, bool kPush = false, int NV = 1>
 cudaError_t tp_dispatch(const TpArgs<kSec> &a, bool track, int idx, cudaStream_t stream)
 {
     const bool w32 = a.g.n_sites <= 32;
     const bool fact = a.g.fact != 0;
-#define ED_TP_FA(W, TR, IX)                                                             \
-    do {                                                                                \
-        if (fact) return tp_launch<W, T, kC, TR, true, IX, kSec, kPush>(a, stream);     \
-        return tp_launch<W, T, kC, TR, false, IX, kSec, kPush>(a, stream);              \
+#define ED_TP_FA(W, TR, IX)                                                                 \
+    do {                                                                                    \
+        if (fact) return tp_launch<W, T, kC, TR, true, IX, kSec, kPush, NV>(a, stream);     \
+        return tp_launch<W, T, kC, TR, false, IX, kSec, kPush, NV>(a, stream);              \
     } while (0)
 #define ED_TP_TR(W, IX)                  \
     do {                                 \
@@ -527,5 +615,8 @@ cudaError_t tp_multi_c128(const TpArgs<kMaxSectors> &a, bool track, int idx, cud
 cudaError_t tp_multi_c64(const TpArgs<kMaxSectors> &a, bool track, int idx, cudaStream_t s);
 // push form (ablation), one sector, y zeroed by the caller
 cudaError_t tp_push(const TpArgs<1> &a, bool track, int idx, ed_dtype dtype, cudaStream_t s);
+// one sector, a real block of 8 interleaved vectors
+cudaError_t tp_single_f64_nv8(const TpArgs<1> &a, bool track, int idx, cudaStream_t s);
+cudaError_t tp_single_f32_nv8(const TpArgs<1> &a, bool track, int idx, cudaStream_t s);
 
 }  // namespace edk

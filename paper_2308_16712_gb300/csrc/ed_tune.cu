@@ -166,11 +166,13 @@ int tuned_index_kind(int n_sites, int order, int flip, uint64_t dim)
 }
 
 // candidate variants of the product for this basis (the default first)
-static std::vector<MatvecVariant> product_variants(const ed_operator *op, const ed_basis *b, int nvec)
+static std::vector<MatvecVariant> product_variants(const ed_operator *op, const ed_basis *b, int nvec,
+                                                   ed_dtype dtype)
 {
     const OpView ov = make_op_view(op);
     const GroupView gv = b->group_view();
-    const bool tp_ok = (b->d_htab || b->d_bkt) && nvec == 1 && ov.exchange_only;
+    const bool tp_ok = (b->d_htab || b->d_bkt) && (nvec == 1 || (nvec == 8 && (dtype == ED_F64 || dtype == ED_F32))) &&
+                       ov.exchange_only;
     const bool prune_ok = gv.fact && gv.rot_d == 1;
     std::vector<MatvecVariant> v{MatvecVariant{0, -1}};
     for (int k : {1, 2}) {
@@ -204,7 +206,7 @@ extern "C" ed_status ed_autotune(const ed_operator *op, const ed_basis *b, const
     if (!b->dim)
         return ED_ERR_INVALID_ARG;
     cudaStream_t st = (cudaStream_t)stream;
-    const std::vector<MatvecVariant> cand = product_variants(op, b, nvec);
+    const std::vector<MatvecVariant> cand = product_variants(op, b, nvec, dtype);
     double ms_default = 0.0, ms_best = 1e300;
     MatvecVariant best{};
     for (size_t i = 0; i < cand.size(); ++i) {

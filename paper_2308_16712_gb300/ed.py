@@ -409,10 +409,11 @@ KERNEL_POLICIES = {"auto": 0, "rowwise": 1, "term_parallel": 2}
 
 
 def kernel_policy(policy: str) -> None:
-    """Testing aid: which matvec kernel serves one vector of an exchange-only
-    operator: "auto" (term-parallel in single precision and for more than 32
-    sites, row-per-lane otherwise),
-    "rowwise" or "term_parallel" (both precisions).  Affects later launches."""
+    """Testing aid: which matvec kernel serves one vector (or a real block of 8)
+    of an exchange-only operator: "auto" (one vector: term-parallel in single
+    precision and for more than 32 sites, row-per-lane otherwise; blocks of 8
+    vectors: term-parallel in fp32, row-per-lane in fp64), "rowwise" or
+    "term_parallel" (both precisions).  Affects later launches."""
     _lib.edx_kernel_policy(KERNEL_POLICIES[policy])
 
 

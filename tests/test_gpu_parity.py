@@ -96,10 +96,11 @@ def search_mode(request):
     generic Benes search over every element with the hash index; factored
     search with the prefix-table binary search (the row-per-lane kernel);
     factored search and hash index with the row-per-lane kernel forced; and
-    with the term-parallel kernel forced in both precisions (it otherwise
-    serves single vectors of exchange-only operators in single precision
-    only); and with the bucketed index (one 64-byte bucket per lookup) built
-    for every sector whose key fits its entry."""
+    with the term-parallel kernel forced in both precisions and for real
+    8-vector blocks (by default it serves single vectors of exchange-only
+    operators in single precision, and in double above 32 sites); and with
+    the bucketed index (one 32-byte bucket per lookup) built for every sector
+    whose key fits its entry."""
     torch, ed = gpu()
     ed.index_policy("bucket" if request.param == "bucket" else "hash")
     ed.force_generic(request.param == "generic")
@@ -152,7 +153,7 @@ def test_index_bit_exact(case):
 
 
 @pytest.mark.parametrize("case", SECTORS, ids=[s[0] for s in SECTORS])
-@pytest.mark.parametrize("nvec", [1, 3])
+@pytest.mark.parametrize("nvec", [1, 3, 8])
 def test_matvec_f64_parity(case, nvec):
     torch, ed = gpu()
     S = make(case)
@@ -189,6 +190,27 @@ def test_matvec_f32_error_bounded(case, nvec):
     ed.matvec(S["O"], S["B"], xt, yt, nvec)
     err = rel_err(yt.cpu().numpy().astype(np.complex128), want if cplx else want.real)
     assert err < F32_TOL, err
+
+
+@pytest.mark.parametrize("name", ["ring16_k0_p+_z+", "ring20_k0_p-_z-", "ring40_nup2_k0_p+"])
+def test_term_parallel_block_columns_equal_single_products(name, search_mode):
+    """The term-parallel kernel on a real block of 8 vectors sums every
+    column in the order of its single-vector form: columns equal the
+    term-parallel single products bit for bit, in fp64 and fp32."""
+    if search_mode != "term_parallel":
+        pytest.skip("runs once, with the term-parallel kernel forced")
+    torch, ed = gpu()
+    case = [c for c in SECTORS if c[0] == name][0]
+    S = make(case, with_oracle=False)
+    for np_dt in (np.float64, np.float32):
+        x = to_torch(ei.x_by_index(23, S["dim"], 8, False).real, np_dt)
+        y = torch.empty_like(x)
+        ed.matvec(S["O"], S["B"], x, y, 8)
+        for v in range(8):
+            xv = x[:, v].contiguous()
+            yv = torch.empty_like(xv)
+            ed.matvec(S["O"], S["B"], xv, yv, 1)
+            assert torch.equal(yv, y[:, v])
 
 
 def test_matvec_nvec_columns_equal_single_products(search_mode):
