@@ -54,12 +54,14 @@ SMS = 152
 INT_LANES_PER_SM = 64
 # DRAM bytes (read + write) per stored nonzero of one launch of the timed
 # kernel (fp32 block product, keyed by kernel and nvec), from one ncu --set
-# full capture of the same kernel on the ring N=36 sector (row-per-lane, nvec
-# = 8: 161.04 + 2.02 GB for 1 230 759 430 nonzeros).  A ring N=40 launch is too
-# large for a many-pass capture, so its traffic is this figure times the
-# nonzeros it processes.  Retake the capture and update the figure whenever the
-# kernel changes (the roofline reports null traffic for kernels not listed).
-KERNEL_DRAM_BYTES_PER_NNZ = {("row-per-lane", 8): (161.040283e9 + 2.023800e9) / 1230759430}
+# full capture of the same kernel on the ring N=36 sector with 1 230 759 430
+# nonzeros (term-parallel, nvec = 8: 162.13 + 2.02 GB; row-per-lane: 161.04 +
+# 2.02 GB).  A ring N=40 launch is too large for a many-pass capture, so its
+# traffic is this figure times the nonzeros it processes.  Retake the capture
+# and update the figure whenever the kernel changes (the roofline reports null
+# traffic for kernels not listed).
+KERNEL_DRAM_BYTES_PER_NNZ = {("term-parallel", 8): (162.133806e9 + 2.022193e9) / 1230759430,
+                             ("row-per-lane", 8): (161.040283e9 + 2.023800e9) / 1230759430}
 
 
 def peaks():
@@ -315,6 +317,7 @@ def run_matvec_only(args, w):
     dim = ed.basis_size(B)
     cplx = not ed.basis_is_real(B)
     nvec = args.nvec
+    ed.kernel_policy(args.kernel_policy)
     states, _ = ed.basis_states(B)
     nnz = ed.count_nnz(O, B)
     out = {"mode": "matvec", "workload": w["name"], "dim": dim, "nvec": nvec, "basis_build_ms": build_ms,
@@ -894,6 +897,8 @@ def main():
                     help="block steps of the full FP32 batched solve behind dE0")
     ap.add_argument("--lanczos-steps", type=int, default=100,
                     help="Lanczos steps of the batched solve in --mode multi (0: skip)")
+    ap.add_argument("--kernel-policy", default="auto", choices=["auto", "rowwise", "term_parallel"],
+                    help="product kernel in --mode matvec (default: the library's rule)")
     ap.add_argument("--solve-modes", default="f32_matvec,f64",
                     help="Lanczos modes of --mode solve (comma-separated: f32_matvec, f64)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
