@@ -134,34 +134,11 @@ __device__ __forceinline__ void dd_norm(float s, float c, float &h, float &l)
     l = c - (h - s);
 }
 
-// Tile staging.  Kind 0: fp32 array (low word 0); 1: fp64 array (split);
-// 2: double-float block (separate high and low float arrays).
-template <int P, int K>
-__device__ __forceinline__ void stage_dd(float *sh, float *sl, const void *gh, const float *gl, uint64_t r0,
-                                         uint64_t n)
-{
-    const uint64_t lim = n * P;
-    for (int e = threadIdx.x; e < kTileRows * P; e += blockDim.x) {
-        const uint64_t gi = r0 * P + (uint64_t)e;
-        float h = 0.f, l = 0.f;
-        if (gi < lim) {
-            if (K == 0) {
-                h = reinterpret_cast<const float *>(gh)[gi];
-            } else if (K == 1) {
-                dd_split(reinterpret_cast<const double *>(gh)[gi], h, l);
-            } else {
-                h = reinterpret_cast<const float *>(gh)[gi];
-                l = gl[gi];
-            }
-        }
-        sh[e] = h;
-        sl[e] = l;
-    }
-}
-
 // A tile's elements held in registers between the load of tile t + grid and
 // the shared-memory store at the top of the next iteration, so that the
-// global loads overlap the current tile's arithmetic.
+// global loads overlap the current tile's arithmetic.  Kind K: 0 fp32 array
+// (low word 0), 1 fp64 array (split), 2 double-float block (separate high and
+// low float arrays).
 template <int P, int K>
 struct Prefetch {
     static constexpr int kN = (kTileRows * P + kBlThreads - 1) / kBlThreads;
@@ -313,7 +290,7 @@ __device__ void gram_finish(GramAcc &acc, double *red, double2 *part, unsigned i
         merge_partials(part, L::E, out, ticket);
 }
 
-// Gram of NM double-float blocks X_m against Y (kind YK, see stage_dd):
+// Gram of NM double-float blocks X_m against Y (kind YK as in Prefetch):
 // out[m][a][b] = sum_i X_m[i][a] Y[i][b].
 template <int P, int NM, int YK>
 __global__ void __launch_bounds__(kBlThreads) k_dd_gram(const float *X0h, const float *X0l, const float *X1h,
@@ -397,7 +374,7 @@ __device__ __forceinline__ void store_row(float *g, uint64_t row, const float (&
 }
 
 // Row of the product output Y as a double-float start value (kind YK as in
-// stage_dd: 0 fp32, 1 fp64, 2 double-float)
+// Prefetch: 0 fp32, 1 fp64, 2 double-float)
 template <int P, int YK>
 __device__ __forceinline__ void load_y_row(const void *gh, const float *gl, uint64_t row, float (&s)[P],
                                            float (&c)[P])
