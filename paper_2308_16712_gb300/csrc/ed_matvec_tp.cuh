@@ -2,7 +2,9 @@
 // product": y_i = sum_j H_ij x_j through getRow and stateToIndex), for
 // operators whose two-site terms only exchange antiparallel spins (every
 // off-diagonal entry of each 4x4 matrix couples |01> and |10>: Heisenberg, XXZ,
-// J1-J2 and any U(1)-conserving two-site coupling), one vector per product.
+// J1-J2 and any U(1)-conserving two-site coupling), for one vector per
+// product or a real block of 8 interleaved vectors (the row value is then the
+// block's row, and every step below works on it componentwise).
 //
 // Work decomposition.  The grid is persistent; a warp takes a tile of 32
 // consecutive rows of one sector (tiles dealt round-robin over the warps).
