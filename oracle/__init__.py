@@ -15,7 +15,9 @@ Layers:
 * this module: ctypes marshalling, spin-inversion expansion of the group,
   the character-formula sector dimension, the sector matrix as a scipy sparse
   matrix, dense diagonalisation (numpy ``eigvalsh``) and a plain fp64 Lanczos
-  whose tridiagonal problem is solved by ``scipy.linalg.eigh_tridiagonal``.
+  whose tridiagonal problem is solved by ``scipy.linalg.eigh_tridiagonal``;
+  the Ritz values of a block Krylov space by Rayleigh-Ritz (the definition
+  block Lanczos computes).
 
 Functions without an independent pin are marked "parity unpinned" in their
 docstring.  (At present every function has at least one pin in
@@ -312,3 +314,36 @@ def lanczos(apply_h, v0, steps: int, reorth: bool = False):
     b = np.array(betas[: len(alphas) - 1])
     e0 = eigh_tridiagonal(a, b, eigvals_only=True)[0]
     return a, b, float(e0)
+
+
+def block_krylov_ritz(apply_h, X0, m: int, rank_tol: float = 1e-12):
+    """Ritz values, ascending, of the block Krylov space
+    K_m(H, X0) = span{X0, H X0, ..., H^(m-1) X0}: the eigenvalues of Q^T H Q
+    for an orthonormal basis Q of the space (Rayleigh-Ritz).  These are the
+    values block Lanczos with m steps produces in exact arithmetic (Krylov
+    methods consume products, Background).  apply_h maps an (n, k) array to
+    H times it; H real symmetric.
+
+    Q is built block by block: the newest block times H, orthogonalised
+    against every earlier block (block Gram-Schmidt, twice), then numpy's
+    Householder QR; directions whose R diagonal falls below rank_tol of the
+    block's size before the projections are dropped (the space stops
+    growing)."""
+    blocks = []
+    V = np.array(X0, dtype=np.float64, copy=True)
+    for _ in range(m):
+        scale = max(float(np.abs(V).max()) if V.size else 0.0, 1e-300)  # before the projections
+        for _pass in range(2):
+            for Bk in blocks:
+                V = V - Bk @ (Bk.T @ V)
+        Qj, R = np.linalg.qr(V)
+        d = np.abs(np.diag(R))
+        keep = d > rank_tol * scale * np.sqrt(V.shape[0])
+        Qj = Qj[:, keep]
+        if Qj.shape[1] == 0:
+            break
+        blocks.append(Qj)
+        V = apply_h(Qj)
+    Q = np.hstack(blocks)
+    T = Q.T @ apply_h(Q)
+    return np.linalg.eigvalsh(0.5 * (T + T.T))

@@ -46,6 +46,29 @@ def test_ring16_block_eigenvalues_match_dense(nvec, steps):
     assert abs(ev[0] - bethe_e0(16)) < 1e-10
 
 
+@pytest.mark.parametrize("nvec,steps", [(2, 5), (4, 3), (8, 3), (16, 2)])
+def test_unconverged_ritz_values_equal_the_block_krylov_definition(nvec, steps):
+    """After a few steps, far from convergence, the Ritz values of the block
+    tridiagonal matrix equal the oracle's Rayleigh-Ritz values of the block
+    Krylov space span{X0, H X0, ..., H^(steps-1) X0}: the recurrence (block
+    Gram and update, Cholesky QR, the coupling blocks) is checked entry by
+    entry through the whole spectrum of T, not only its converged end."""
+    torch, ed = gpu()
+    for name, p, c, op, z in (("ring16", *ei.ring_group(16, 0, +1), ei.heisenberg_ring(16), +1),
+                              ("torus4x4", *ei.torus_group(4, 4, 0, 0), ei.j1j2_torus(4, 4, 1.0, 0.5), +1)):
+        S = build_pair(16, 8, z, p, c, op)
+        if not ed.basis_is_real(S["B"]):
+            continue
+        M = oracle.sparse_matrix(S["G"], S["H"], S["st"], S["nm"]).real
+        x0 = start_block(S["dim"], nvec, seed=11)
+        want = oracle.block_krylov_ritz(lambda V: M @ V, x0.cpu().numpy(), steps)
+        k = nvec * steps
+        eigs, _ = ed.lanczos_block(S["O"], S["B"], x0, nvec, steps, ed.ED_LANCZOS_F64 | ed.ED_LANCZOS_VALUES_ONLY,
+                                   n_eig=k)
+        assert len(want) == k
+        assert np.max(np.abs(np.array(eigs) - want)) < 1e-9 * np.max(np.abs(want)), (name, eigs, want)
+
+
 @pytest.mark.parametrize("nvec", [4, 8])
 def test_ring16_block_f32_products_refined(nvec):
     torch, ed = gpu()

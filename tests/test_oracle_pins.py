@@ -254,6 +254,40 @@ def test_ground_state_of_2_mod_4_rings_lies_at_momentum_pi(n):
     assert e_0 > bethe_e0(n) + 0.1
 
 
+def test_block_krylov_ritz_full_space_is_the_spectrum():
+    """Once the block Krylov space fills the whole space its Ritz values are
+    the eigenvalues (random symmetric matrix, blocks of 4 and of 1)."""
+    rng = np.random.default_rng(5)
+    A = rng.standard_normal((40, 40))
+    A = A + A.T
+    ev = np.linalg.eigvalsh(A)
+    for p, m in ((4, 10), (1, 40), (8, 6)):
+        X0 = rng.standard_normal((40, p))
+        r = oracle.block_krylov_ritz(lambda V: A @ V, X0, m)
+        assert len(r) == 40
+        assert np.max(np.abs(r - ev)) < 1e-10 * np.max(np.abs(ev))
+
+
+def test_block_krylov_ritz_of_one_vector_is_lanczos():
+    """Block size 1: the Ritz values equal those of the oracle's plain
+    Lanczos (with full reorthogonalisation) after the same number of steps,
+    and the lowest one decreases with the steps towards the lowest eigenvalue
+    without passing it."""
+    from scipy.linalg import eigh_tridiagonal
+    G, H, st, nm = ring_sector(12, 6, 0, +1, +1)
+    M = oracle.sparse_matrix(G, H, st, nm).real
+    x0 = np.random.default_rng(3).standard_normal(len(st))
+    lam0 = np.linalg.eigvalsh(M.toarray())[0]
+    prev = np.inf
+    for m in (3, 6, 9):
+        a, b, _ = oracle.lanczos(lambda v: M @ v, x0, m, reorth=True)
+        want = eigh_tridiagonal(a, b[: len(a) - 1], eigvals_only=True)
+        got = oracle.block_krylov_ritz(lambda V: M @ V, x0[:, None], m)
+        assert np.max(np.abs(got - want)) < 1e-10
+        assert lam0 - 1e-12 <= got[0] <= prev
+        prev = got[0]
+
+
 def test_hermiticity_and_sz_conservation():
     # complex sector: <u, H v> = <H u, v>
     p, c = ei.ring_group(12, 5)
